@@ -1,0 +1,159 @@
+"""FP64 CPU oracle for ray casting against animated sparse voxel octrees.
+
+TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package.  The CUDA library never calls it and
+shares no code with it (see svo_oracle.c for the definition it computes).
+
+Python side: argument marshalling with ctypes plus a convenience wrapper that
+runs the per-frame pose pipeline (compose, invert) and the tracer for a scene
+built by ``synthetic``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        up32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+        up64 = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+        L.oracle_compose.argtypes = [C.c_int, ip, dp, dp]
+        L.oracle_compose.restype = C.c_int
+        L.oracle_invert.argtypes = [C.c_int, dp, dp]
+        L.oracle_invert.restype = C.c_int
+        L.oracle_part_sphere.argtypes = [C.c_int, dp, dp]
+        L.oracle_part_sphere.restype = None
+        L.oracle_ray_sphere.argtypes = [dp, dp, dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.oracle_ray_sphere.restype = C.c_int
+        L.oracle_slab.argtypes = [dp, dp, dp, dp, C.c_double, C.c_double, dp]
+        L.oracle_slab.restype = C.c_int
+        L.oracle_asset_new.argtypes = [C.c_int, C.c_int64, up64]
+        L.oracle_asset_new.restype = C.c_void_p
+        L.oracle_asset_free.argtypes = [C.c_void_p]
+        L.oracle_asset_free.restype = None
+        L.oracle_asset_leaves.argtypes = [C.c_void_p]
+        L.oracle_asset_leaves.restype = C.c_int64
+        L.oracle_trace.argtypes = [C.c_int, C.POINTER(C.c_void_p), dp, C.c_int64, dp, dp, up32, up64, dp, C.c_int,
+                                   C.c_int]
+        L.oracle_trace.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+MISS_PART = 0xFFFFFFFF
+MISS_VOXEL = 0xFFFFFFFFFFFFFFFF
+
+
+def compose(parent, local) -> np.ndarray:
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    local = np.ascontiguousarray(local, dtype=np.float64).reshape(-1, 12)
+    world = np.zeros_like(local)
+    if lib().oracle_compose(len(parent), parent, local, world) != 0:
+        raise ValueError("parent[i] must be < i")
+    return world
+
+
+def invert(world) -> np.ndarray:
+    world = np.ascontiguousarray(world, dtype=np.float64).reshape(-1, 12)
+    inv = np.zeros_like(world)
+    if lib().oracle_invert(world.shape[0], world, inv) != 0:
+        raise ValueError("singular pose")
+    return inv
+
+
+def part_spheres(world) -> np.ndarray:
+    world = np.ascontiguousarray(world, dtype=np.float64).reshape(-1, 12)
+    out = np.zeros((world.shape[0], 4))
+    lib().oracle_part_sphere(world.shape[0], world, out)
+    return out
+
+
+def ray_sphere(o, d, sphere4):
+    """Eq. 4 (general direction length).  Returns (hit, t_in, t_out)."""
+    ti, to = C.c_double(0), C.c_double(0)
+    h = lib().oracle_ray_sphere(np.ascontiguousarray(o, np.float64), np.ascontiguousarray(d, np.float64),
+                                np.ascontiguousarray(sphere4, np.float64), C.byref(ti), C.byref(to))
+    return bool(h), ti.value, to.value
+
+
+def slab(o, d, lo, hi, t_lo=0.0, t_hi=float("inf")):
+    """Closed-box slab test.  Returns (hit, t0, t1)."""
+    out = np.zeros(2)
+    h = lib().oracle_slab(*(np.ascontiguousarray(v, np.float64) for v in (o, d, lo, hi)), float(t_lo), float(t_hi),
+                          out)
+    return bool(h), float(out[0]), float(out[1])
+
+
+class OracleAsset:
+    """The oracle's own octree of one asset (sorted Morton codes of its leaves)."""
+
+    def __init__(self, depth: int, leaf_ids):
+        ids = np.ascontiguousarray(leaf_ids, dtype=np.uint64)
+        self.depth = depth
+        self.handle = lib().oracle_asset_new(depth, ids.shape[0], ids)
+        if not self.handle:
+            raise ValueError("bad asset")
+
+    @property
+    def n_leaves(self) -> int:
+        return int(lib().oracle_asset_leaves(self.handle))
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.oracle_asset_free(h)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def trace(part_assets, inv, rays, mode: int = 1, threads: int | None = None) -> dict:
+    """Closest hit of every ray.  ``part_assets``: one OracleAsset per part;
+    ``inv``: [P,12] FP64 world->local poses; ``rays``: [n,8] (any float dtype,
+    converted exactly to FP64)."""
+    rays = np.ascontiguousarray(np.asarray(rays).astype(np.float64)).reshape(-1, 8)
+    inv = np.ascontiguousarray(inv, dtype=np.float64).reshape(-1, 12)
+    n = rays.shape[0]
+    P = len(part_assets)
+    handles = (C.c_void_p * max(P, 1))(*[a.handle for a in part_assets])
+    out_t = np.zeros(n)
+    out_s = np.zeros(n)
+    out_p = np.zeros(n, dtype=np.uint32)
+    out_v = np.zeros(n, dtype=np.uint64)
+    rc = lib().oracle_trace(P, handles, inv, n, rays, out_t, out_p, out_v, out_s, int(mode),
+                            int(threads or default_threads()))
+    if rc != 0:
+        raise ValueError("oracle_trace failed")
+    return {"t": out_t, "part": out_p, "voxel": out_v, "second": out_s}
+
+
+class SceneOracle:
+    """Oracle view of a ``synthetic.Scene``: assets built once, poses per frame."""
+
+    def __init__(self, scene):
+        self.scene = scene
+        self.assets = [OracleAsset(a.depth, a.leaf_ids) for a in scene.assets]
+
+    def poses(self, local=None):
+        local = self.scene.local if local is None else local
+        world = compose(self.scene.parent, local)
+        return world, invert(world)
+
+    def trace(self, rays, local=None, mode: int = 1, threads: int | None = None) -> dict:
+        world, inv = self.poses(local)
+        parts = [self.assets[int(a)] for a in self.scene.part_asset]
+        return trace(parts, inv, rays, mode=mode, threads=threads)
