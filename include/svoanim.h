@@ -1,0 +1,230 @@
+/*
+ * svoanim.h -- C ABI of the GB300 (sm_103a) library for ray casting against
+ * scenes of animated sparse voxel octrees.
+ *
+ * Method (Espe, Gjermundnes, Hendseth, "Efficient Animation of Sparse Voxel
+ * Octrees for Real-Time Ray Tracing"): a scene is a set of static SVOs, each
+ * with a pose that changes per frame (Sec. III); instead of moving voxels,
+ * every ray is moved into a part's local frame by the inverse pose (Eq. 2-3);
+ * parts are culled by bounding spheres (Sec. IV-A, Eq. 4) and traced front to
+ * back with an early exit once the closest hit lies before the next part
+ * (Sec. IV-B).
+ *
+ * Conventions used by every call:
+ *  - Status: every call returns svo_status (0 = success, < 0 = error) and never
+ *    aborts.  svo_last_error() gives a thread-local message for the last error.
+ *  - Pointers are host pointers unless the comment says "device".  Host arrays
+ *    are copied before the call returns; the caller keeps ownership of every
+ *    array it passes.  Device buffers passed in (rays, hits, flags, stats)
+ *    belong to the caller and must stay valid until the work on `stream`
+ *    completes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls marked "async" only enqueue work on it.
+ *  - An asset's local frame is the unit cube [0,1]^3 with the octree origin at
+ *    a corner (Fig. 2).  A leaf cell (x,y,z) of a depth-D asset has voxel id
+ *    x | y<<D | z<<2D.
+ *  - A pose is an affine map stored row-major as 3x4 doubles [A | b]
+ *    (y = A x + b).  A part's pose is relative to its parent part;
+ *    parent[i] < i, or -1 for a root.  World pose = parent's world pose o local.
+ *  - A ray is 8 floats: ox oy oz tmin dx dy dz tmax (Eq. 1; t in
+ *    [tmin, tmax]); d need not be unit length and is never renormalised, so
+ *    t means the same point in world and local space.
+ *  - Device memory: the library allocates device memory for assets, scene
+ *    tables and its own scratch (cudaMalloc) in svo_upload, scene_create and,
+ *    when a larger ray count than before is traced, in trace_rays /
+ *    trace_batch (outside any stream capture; see trace_rays).
+ */
+#ifndef SVOANIM_H
+#define SVOANIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t svo_status;
+
+#define SVO_OK 0
+#define SVO_ERR_ARG (-1)      /* bad argument (null pointer, size, depth, parent order) */
+#define SVO_ERR_OOM (-2)      /* device or host allocation failed */
+#define SVO_ERR_HANDLE (-3)   /* unknown or released asset handle / scene */
+#define SVO_ERR_CUDA (-4)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define SVO_ERR_TIMEOUT (-5)  /* a bounded device wait gave up */
+#define SVO_ERR_ADMIT (-6)    /* request does not fit the memory budget */
+#define SVO_ERR_NAN (-7)      /* NaN or infinity in a pose */
+#define SVO_ERR_SINGULAR (-8) /* a composed pose is not invertible */
+#define SVO_ERR_LIMIT (-9)    /* a size exceeds a documented library limit */
+#define SVO_ERR_DEVICE (-10)  /* a kernel reported an internal check failure */
+
+/* Limits. */
+#define SVO_MAX_DEPTH 16        /* octree depth of an asset (leaf level) */
+#define SVO_MAX_PARTS 1024      /* parts per scene */
+
+/* trace flags (bitmask).  With none set the call is the plain trace: every
+ * part in index order, no sphere culling, no cross-part early exit. */
+#define SVO_TRACE_CULL 1u     /* bounding-sphere culling of parts (Sec. IV-A, Eq. 4) */
+#define SVO_TRACE_SORT 2u     /* visit parts by sphere entry t, stop once the hit is nearer (Sec. IV-B) */
+#define SVO_TRACE_FP64_FIX 4u /* re-intersect flagged rays in FP64 and overwrite their hits */
+#define SVO_TRACE_STATS 8u    /* accumulate counters into *stats (device) */
+#define SVO_TRACE_DEFER_FIX 16u /* with FP64_FIX: collect flagged rays but leave the FP64 pass to
+                                   trace_fix_pending (lets a caller time the two passes apart) */
+#define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
+
+/* per-ray flags written when ray_flags != NULL */
+#define SVO_RAY_UNCERTAIN 1u /* FP32 could not certify the closest hit (near tie / grazing) */
+#define SVO_RAY_FIXED 2u     /* the hit was recomputed in FP64 */
+
+typedef struct svo_ctx svo_ctx;
+typedef struct svo_scene svo_scene;
+typedef uint32_t svo_handle;
+
+/* One static SVO given by its occupied finest-level cells. */
+typedef struct {
+  int32_t depth;              /* 1..SVO_MAX_DEPTH */
+  uint64_t n_leaves;          /* number of entries in leaf_ids (duplicates allowed) */
+  const uint64_t *leaf_ids;   /* host; voxel ids x | y<<D | z<<2D */
+  const uint32_t *leaf_rgb;   /* host, may be NULL; 0x00RRGGBB per entry of leaf_ids */
+} svo_desc;
+
+/* Closest hit of one ray: 16 bytes.  Miss: t = +inf, part = 0xFFFFFFFF,
+ * voxel = UINT64_MAX.  Equal t is broken by smaller part, then smaller voxel. */
+typedef struct {
+  float t;
+  uint32_t part;
+  uint64_t voxel;
+} svo_hit;
+
+/* Counters accumulated (atomically, on the device) when SVO_TRACE_STATS is set. */
+typedef struct {
+  unsigned long long rays;          /* rays traced */
+  unsigned long long flagged;       /* rays flagged SVO_RAY_UNCERTAIN */
+  unsigned long long fixed;         /* rays recomputed in FP64 */
+  unsigned long long parts_tested;  /* (ray, part) sphere tests */
+  unsigned long long parts_entered; /* (ray, part) traversals started */
+  unsigned long long nodes_visited; /* interior node descriptors fetched (8 B each) */
+  unsigned long long leaves_tested; /* leaf cells slab-tested */
+  unsigned long long passes;        /* candidate-list passes (> rays when lists overflow) */
+} svo_trace_stats;
+
+/* One entry of a batched trace (trace_batch). */
+typedef struct {
+  svo_scene *scene;
+  const float *rays;   /* device, 8 floats per ray */
+  uint64_t n;          /* number of rays */
+  svo_hit *hits;       /* device, n entries */
+  uint32_t *ray_flags; /* device, n entries, or NULL */
+} svo_batch_item;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (makes it current for the calling
+ * thread).  *out receives the context; destroy it with svo_ctx_destroy. */
+svo_status svo_ctx_create(int32_t device, svo_ctx **out);
+/* Release every asset, scene and buffer of the context.  NULL is allowed. */
+svo_status svo_ctx_destroy(svo_ctx *ctx);
+/* Thread-local message of the last failing call of this thread ("" if none). */
+const char *svo_last_error(void);
+/* Static name of a status code. */
+const char *svo_status_string(svo_status s);
+/* Read and clear the context's device error word (synchronises the device).
+ * Returns SVO_OK, or SVO_ERR_DEVICE with the failing check in the message. */
+svo_status svo_check_device(svo_ctx *ctx);
+
+/* ----------------------------------------------------------------- assets */
+
+/* Host-only octree build of the node layout, for inspection (no GPU needed).
+ * Node layout (a simplified Laine-Karras child descriptor, Sec. II-B, V):
+ * 8 bytes per interior node, nodes in breadth-first order, root first:
+ *   uint32 first_child; uint8 child_mask; uint8 leaf_mask; uint16 zero.
+ * Bit k of child_mask is octant k (bit0 = +x half, bit1 = +y, bit2 = +z).
+ * The children of a node are stored contiguously in ascending octant order;
+ * child k is at first_child + popcount(child_mask & ((1<<k)-1)).  At level
+ * D-1 the children are leaves: leaf_mask == child_mask and first_child indexes
+ * the leaf payload array (one 0x00RRGGBB per leaf, same order).
+ * Call with nodes == NULL to get *n_nodes and *n_leaves; then call again with
+ * nodes (n_nodes * 8 bytes) and rgb (n_leaves entries, may be NULL). */
+svo_status svo_build_host(const svo_desc *desc, uint64_t *n_nodes, uint64_t *n_leaves, void *nodes,
+                          uint32_t *rgb);
+/* Build an asset from a leaf list and upload it (synchronous).  The library
+ * owns the device copy until svo_release.  *out receives the handle. */
+svo_status svo_upload(svo_ctx *ctx, const svo_desc *desc, svo_handle *out);
+/* Free an asset.  Scenes that still reference it must be destroyed first
+ * (SVO_ERR_ARG otherwise). */
+svo_status svo_release(svo_ctx *ctx, svo_handle h);
+/* Depth, interior node count and leaf count of an asset (any pointer may be NULL). */
+svo_status svo_asset_info(svo_ctx *ctx, svo_handle h, int32_t *depth, uint64_t *n_nodes, uint64_t *n_leaves);
+
+/* ----------------------------------------------------------------- scenes */
+
+/* A scene of n_parts parts; part i instances asset[i] and hangs below
+ * parent[i] (< i, or -1).  Poses start as identities. */
+svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, const int32_t *parent,
+                        svo_scene **out);
+svo_status scene_destroy(svo_scene *scene);
+/* Set every part's local pose (host, n_parts*12 doubles, parent <- part).
+ * Async: the array is copied to pinned staging before return, then to the
+ * device on `stream`.  SVO_ERR_NAN if any entry is NaN/inf. */
+svo_status scene_set_transforms(svo_scene *scene, const double *local_3x4, void *stream);
+/* Same from a device array (n_parts*12 doubles); no check for NaN. */
+svo_status scene_set_transforms_device(svo_scene *scene, const double *local_3x4_dev, void *stream);
+/* Per-frame pose pipeline (async, one small kernel): compose the transform
+ * tree in FP64 (W_i = W_parent o L_i), invert in FP64 (Eq. 3; adjugate /
+ * determinant, which reduces to transpose-and-negate for a rigid pose), emit
+ * the FP32 world->local rows used by tracing, refit the part bounding spheres
+ * (centre = image of the cube centre, radius = farthest image corner,
+ * Sec. IV-A) and rebuild the cluster level of the sphere hierarchy.  A
+ * singular pose sets the device error word (svo_check_device). */
+svo_status scene_refit(svo_scene *scene, void *stream);
+/* Copy the last refit's per-part data to host arrays (any may be NULL) and
+ * synchronise `stream`: world and inverse poses (n_parts*12 doubles each),
+ * FP32 inverse rows (n_parts*12 floats), FP32 spheres (n_parts*4 floats:
+ * cx cy cz r). */
+svo_status scene_read_poses(svo_scene *scene, double *world, double *inv, float *inv_f32, float *sphere,
+                            void *stream);
+/* Number of clusters of the sphere hierarchy and, if the arrays are not NULL,
+ * the cluster spheres (n_clusters*4 floats) and the part order
+ * (n_parts ints; cluster c holds order[8c .. 8c+7]).  Synchronises `stream`. */
+svo_status scene_read_clusters(svo_scene *scene, int32_t *n_clusters, float *sphere, int32_t *order,
+                               void *stream);
+
+/* ------------------------------------------------------------------ trace */
+
+/* Closest hit (t, part, voxel) of n rays (async).  rays: device, 8 floats per
+ * ray; hits: device, n svo_hit; ray_flags: device, n uint32 or NULL;
+ * stats: device svo_trace_stats or NULL (used with SVO_TRACE_STATS; the caller
+ * zeroes it).  Traversal runs in FP32; a ray whose closest hit FP32 cannot
+ * certify (the error-bounded intervals of two candidates overlap, or the
+ * winner's own interval is wider than 2^-17 of its t) is flagged, and with
+ * SVO_TRACE_FP64_FIX re-intersected in FP64.  The scene must have been
+ * refitted since its last scene_set_transforms.  If n exceeds the largest n
+ * traced so far on this context the call grows the context's scratch with
+ * cudaMalloc, so call it once at full size before capturing a CUDA graph. */
+svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits, uint32_t *ray_flags,
+                      uint32_t flags, svo_trace_stats *stats, void *stream);
+/* Batched trace: every item's rays against its own scene, in one persistent
+ * launch whose thread blocks take fixed-size tiles of rays from a device work
+ * counter (async).  Items may reference different scenes of the context. */
+svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_items, uint32_t flags,
+                       svo_trace_stats *stats, void *stream);
+
+/* trace_rays for rays and hits in HOST memory (async on `stream`): the library
+ * copies rays to its per-stream device staging, traces, and copies hits (and
+ * ray_flags, if not NULL) back.  With pinned (page-locked) host buffers the
+ * copies overlap other streams and the call returns before they finish:
+ * synchronise `stream` before reading hits.  Pageable buffers are allowed
+ * (the copies then block the host).  Grows the staging with cudaMalloc when n
+ * exceeds the largest n traced so far on this stream. */
+svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n, svo_hit *hits_host,
+                           uint32_t *ray_flags_host, uint32_t flags, void *stream);
+
+/* Run the FP64 re-intersection pass left pending by the last trace_rays /
+ * trace_batch issued on `stream` with SVO_TRACE_FP64_FIX | SVO_TRACE_DEFER_FIX
+ * (async).  No-op (SVO_OK) if nothing is pending on that stream. */
+svo_status trace_fix_pending(svo_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVOANIM_H */

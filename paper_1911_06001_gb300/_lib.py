@@ -1,0 +1,108 @@
+"""ctypes declarations of the C ABI in include/svoanim.h (marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsvoanim.so")
+
+SVO_OK = 0
+STATUS_NAMES = {
+    0: "SVO_OK", -1: "SVO_ERR_ARG", -2: "SVO_ERR_OOM", -3: "SVO_ERR_HANDLE", -4: "SVO_ERR_CUDA",
+    -5: "SVO_ERR_TIMEOUT", -6: "SVO_ERR_ADMIT", -7: "SVO_ERR_NAN", -8: "SVO_ERR_SINGULAR", -9: "SVO_ERR_LIMIT",
+    -10: "SVO_ERR_DEVICE",
+}
+
+TRACE_CULL = 1
+TRACE_SORT = 2
+TRACE_FP64_FIX = 4
+TRACE_STATS = 8
+TRACE_DEFER_FIX = 16
+TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
+
+RAY_UNCERTAIN = 1
+RAY_FIXED = 2
+
+MAX_DEPTH = 16
+MAX_PARTS = 1024
+
+# every symbol include/svoanim.h declares
+EXPORTS = [
+    "svo_ctx_create", "svo_ctx_destroy", "svo_last_error", "svo_status_string", "svo_check_device",
+    "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
+    "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
+    "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
+    "trace_rays_host",
+]
+
+
+class SvoDesc(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("n_leaves", C.c_uint64), ("leaf_ids", C.c_void_p), ("leaf_rgb", C.c_void_p)]
+
+
+class SvoTraceStats(C.Structure):
+    _fields_ = [(n, C.c_ulonglong) for n in ("rays", "flagged", "fixed", "parts_tested", "parts_entered",
+                                             "nodes_visited", "leaves_tested", "passes")]
+
+
+class SvoBatchItem(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("rays", C.c_void_p), ("n", C.c_uint64), ("hits", C.c_void_p),
+                ("ray_flags", C.c_void_p)]
+
+
+class SvoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the compiled library; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libsvoanim.so not built at {p}; run __graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(p)
+    vp, i32, u32, u64 = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64
+    pvp = C.POINTER(C.c_void_p)
+    sig = {
+        "svo_ctx_create": ([i32, pvp], i32),
+        "svo_ctx_destroy": ([vp], i32),
+        "svo_last_error": ([], C.c_char_p),
+        "svo_status_string": ([i32], C.c_char_p),
+        "svo_check_device": ([vp], i32),
+        "svo_build_host": ([C.POINTER(SvoDesc), C.POINTER(u64), C.POINTER(u64), vp, vp], i32),
+        "svo_upload": ([vp, C.POINTER(SvoDesc), C.POINTER(u32)], i32),
+        "svo_release": ([vp, u32], i32),
+        "svo_asset_info": ([vp, u32, C.POINTER(i32), C.POINTER(u64), C.POINTER(u64)], i32),
+        "scene_create": ([vp, i32, vp, vp, pvp], i32),
+        "scene_destroy": ([vp], i32),
+        "scene_set_transforms": ([vp, vp, vp], i32),
+        "scene_set_transforms_device": ([vp, vp, vp], i32),
+        "scene_refit": ([vp, vp], i32),
+        "scene_read_poses": ([vp, vp, vp, vp, vp, vp], i32),
+        "scene_read_clusters": ([vp, C.POINTER(i32), vp, vp, vp], i32),
+        "trace_rays": ([vp, vp, u64, vp, vp, u32, vp, vp], i32),
+        "trace_batch": ([vp, C.POINTER(SvoBatchItem), i32, u32, vp, vp], i32),
+        "trace_fix_pending": ([vp, vp], i32),
+        "trace_rays_host": ([vp, vp, u64, vp, vp, u32, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def check(status: int) -> None:
+    if status != SVO_OK:
+        msg = load().svo_last_error()
+        raise SvoError(status, msg.decode() if msg else "")

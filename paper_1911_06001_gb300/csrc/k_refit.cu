@@ -1,0 +1,262 @@
+// k_refit.cu -- per-frame pose pipeline of a scene, one thread block.
+//
+//  1. compose the transform tree in FP64, parents first: W_i = W_parent(i) o L_i
+//     (the paper gives one transform per SVO, Sec. III; the tree is a
+//     generalisation in which a root part has W_i = L_i);
+//  2. invert each W_i in FP64 (Eq. 3): A^-1 = adj(A)/det(A), b' = -A^-1 b,
+//     which for a rigid pose equals the transposed rotation and the negated,
+//     rotated translation (Sec. III-A);
+//  3. emit the FP32 world->local rows the trace kernel uses, plus bounds on
+//     their norms for the trace kernel's rounding-error bound;
+//  4. refit the part bounding spheres (Sec. IV-A: centre and radius follow
+//     from the pose): centre = image of the cube centre, radius = farthest
+//     image corner, rounded outward to FP32;
+//  5. rebuild the cluster level of the sphere hierarchy: parts sorted by the
+//     Morton code of their sphere centres, runs of 8 enclosed by one sphere
+//     (the scene-level structure the paper proposes for many parts, Sec. V-E).
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+
+#include "svo_internal.h"
+
+namespace svo {
+
+namespace {
+
+constexpr int kRefitThreads = 256;
+
+__device__ __forceinline__ void compose_affine(const double *p, const double *q, double *out) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double r0 = p[i * 4 + 0] * q[0] + p[i * 4 + 1] * q[4] + p[i * 4 + 2] * q[8];
+    double r1 = p[i * 4 + 0] * q[1] + p[i * 4 + 1] * q[5] + p[i * 4 + 2] * q[9];
+    double r2 = p[i * 4 + 0] * q[2] + p[i * 4 + 1] * q[6] + p[i * 4 + 2] * q[10];
+    double r3 = p[i * 4 + 0] * q[3] + p[i * 4 + 1] * q[7] + p[i * 4 + 2] * q[11] + p[i * 4 + 3];
+    out[i * 4 + 0] = r0;
+    out[i * 4 + 1] = r1;
+    out[i * 4 + 2] = r2;
+    out[i * 4 + 3] = r3;
+  }
+}
+
+__device__ __forceinline__ unsigned int spread10(unsigned int v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
+  const int P = a.n_parts;
+  const int tid = threadIdx.x;
+  __shared__ unsigned long long s_key[kMaxParts];
+  __shared__ float s_red[6][kRefitThreads];
+
+  // 1. compose, level by level (parents are on earlier levels)
+  for (int L = 0; L < a.n_levels; ++L) {
+    const int b = a.level_start[L], e = a.level_start[L + 1];
+    for (int j = b + tid; j < e; j += kRefitThreads) {
+      const int i = a.level_order[j];
+      const int p = a.stat[i].parent;
+      const double *Li = a.local + 12 * i;
+      double *Wi = a.world + 12 * i;
+      if (p < 0) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Wi[k] = Li[k];
+      } else {
+        double Wp[12], L12[12], out[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          Wp[k] = a.world[12 * p + k];
+          L12[k] = Li[k];
+        }
+        compose_affine(Wp, L12, out);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Wi[k] = out[k];
+      }
+    }
+    __syncthreads();
+  }
+
+  // 2-4. per part: invert, FP32 rows, norms, sphere
+  float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+  for (int i = tid; i < P; i += kRefitThreads) {
+    double m[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m[k] = a.world[12 * i + k];
+    const double A0 = m[0], A1 = m[1], A2 = m[2], A3 = m[4], A4 = m[5], A5 = m[6], A6 = m[8], A7 = m[9],
+                 A8 = m[10];
+    const double c00 = A4 * A8 - A5 * A7, c01 = A5 * A6 - A3 * A8, c02 = A3 * A7 - A4 * A6;
+    const double det = A0 * c00 + A1 * c01 + A2 * c02;
+    double inv[12];
+    bool ok = isfinite(det) && fabs(det) > 0.0;
+    if (ok) {
+      const double rd = 1.0 / det;
+      inv[0] = c00 * rd;
+      inv[1] = (A2 * A7 - A1 * A8) * rd;
+      inv[2] = (A1 * A5 - A2 * A4) * rd;
+      inv[4] = c01 * rd;
+      inv[5] = (A0 * A8 - A2 * A6) * rd;
+      inv[6] = (A2 * A3 - A0 * A5) * rd;
+      inv[8] = c02 * rd;
+      inv[9] = (A1 * A6 - A0 * A7) * rd;
+      inv[10] = (A0 * A4 - A1 * A3) * rd;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        inv[r * 4 + 3] = -(inv[r * 4 + 0] * m[3] + inv[r * 4 + 1] * m[7] + inv[r * 4 + 2] * m[11]);
+      for (int k = 0; k < 12; ++k) ok = ok && isfinite(inv[k]);
+    }
+    if (!ok) {
+      atomicOr(a.err, kErrSingular);
+      for (int k = 0; k < 12; ++k) inv[k] = 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a.inv64[12 * i + k] = inv[k];
+
+    float f[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) f[k] = (float)inv[k];
+    double rowsum = 0.0, bmax = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      double s = fabs((double)f[r * 4]) + fabs((double)f[r * 4 + 1]) + fabs((double)f[r * 4 + 2]);
+      rowsum = fmax(rowsum, s);
+      bmax = fmax(bmax, fabs((double)f[r * 4 + 3]));
+    }
+    double fro = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fro += m[r * 4 + c] * m[r * 4 + c];
+    // sphere: centre = W (1/2,1/2,1/2), radius = farthest image corner
+    double c[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) c[r] = 0.5 * (m[r * 4] + m[r * 4 + 1] + m[r * 4 + 2]) + m[r * 4 + 3];
+    double r2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double qx = (k & 1) ? 0.5 : -0.5, qy = (k & 2) ? 0.5 : -0.5, qz = (k & 4) ? 0.5 : -0.5;
+      double s = 0.0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double v = m[r * 4] * qx + m[r * 4 + 1] * qy + m[r * 4 + 2] * qz;
+        s += v * v;
+      }
+      r2 = fmax(r2, s);
+    }
+    const float cfx = (float)c[0], cfy = (float)c[1], cfz = (float)c[2];
+    const double dcx = c[0] - cfx, dcy = c[1] - cfy, dcz = c[2] - cfz;
+    const double rr = (sqrt(r2) + sqrt(dcx * dcx + dcy * dcy + dcz * dcz)) * (1.0 + 1e-12);
+    PartHot h;
+    h.r0 = make_float4(f[0], f[1], f[2], f[3]);
+    h.r1 = make_float4(f[4], f[5], f[6], f[7]);
+    h.r2 = make_float4(f[8], f[9], f[10], f[11]);
+    h.sphere = make_float4(cfx, cfy, cfz, ok ? __double2float_ru(rr) : -1.0f);
+    a.hot[i] = h;
+    PartAux x;
+    x.nodes = a.stat[i].nodes;
+    x.n_nodes = a.stat[i].n_nodes;
+    x.depth = a.stat[i].depth;
+    x.n_ainv = __double2float_ru(rowsum * (1.0 + 1e-12));
+    x.n_binv = __double2float_ru(bmax * (1.0 + 1e-12));
+    x.cull_scale = __double2float_ru(2.0 * 1.7320508075688772 * sqrt(fro) * (1.0 + 1e-12));
+    x.pad = 0;
+    a.aux[i] = x;
+    mn[0] = fminf(mn[0], cfx);
+    mn[1] = fminf(mn[1], cfy);
+    mn[2] = fminf(mn[2], cfz);
+    mx[0] = fmaxf(mx[0], cfx);
+    mx[1] = fmaxf(mx[1], cfy);
+    mx[2] = fmaxf(mx[2], cfz);
+  }
+  // bounding box of the sphere centres (block reduction)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s_red[k][tid] = mn[k];
+    s_red[3 + k][tid] = mx[k];
+  }
+  __syncthreads();
+  for (int w = kRefitThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        s_red[k][tid] = fminf(s_red[k][tid], s_red[k][tid + w]);
+        s_red[3 + k][tid] = fmaxf(s_red[3 + k][tid], s_red[3 + k][tid + w]);
+      }
+    }
+    __syncthreads();
+  }
+  const float bx0 = s_red[0][0], by0 = s_red[1][0], bz0 = s_red[2][0];
+  const float ex = fmaxf(s_red[3][0] - bx0, 1e-30f), ey = fmaxf(s_red[4][0] - by0, 1e-30f),
+              ez = fmaxf(s_red[5][0] - bz0, 1e-30f);
+  // 5. Morton keys and a rank sort (P <= kMaxParts)
+  for (int i = tid; i < P; i += kRefitThreads) {
+    const float4 s = a.hot[i].sphere;
+    const unsigned int qx = (unsigned int)fminf(fmaxf((s.x - bx0) / ex * 1023.0f, 0.0f), 1023.0f);
+    const unsigned int qy = (unsigned int)fminf(fmaxf((s.y - by0) / ey * 1023.0f, 0.0f), 1023.0f);
+    const unsigned int qz = (unsigned int)fminf(fmaxf((s.z - bz0) / ez * 1023.0f, 0.0f), 1023.0f);
+    const unsigned int mc = spread10(qx) | (spread10(qy) << 1) | (spread10(qz) << 2);
+    s_key[i] = ((unsigned long long)mc << 11) | (unsigned long long)i;
+  }
+  __syncthreads();
+  for (int i = tid; i < P; i += kRefitThreads) {
+    const unsigned long long k = s_key[i];
+    int rank = 0;
+    for (int j = 0; j < P; ++j) rank += (s_key[j] < k) ? 1 : 0;
+    a.order[rank] = i;
+  }
+  __syncthreads();
+  for (int cidx = tid; cidx < a.n_clusters; cidx += kRefitThreads) {
+    const int first = cidx * kClusterSize;
+    const int cnt = min(kClusterSize, P - first);
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    float na = 0.f, nb = 0.f, cs = 0.f;
+    bool any = false;
+    for (int k = 0; k < cnt; ++k) {
+      const int p = a.order[first + k];
+      const float4 s = a.hot[p].sphere;
+      if (s.w < 0.f) continue;
+      any = true;
+      lo[0] = fmin(lo[0], (double)s.x - s.w);
+      lo[1] = fmin(lo[1], (double)s.y - s.w);
+      lo[2] = fmin(lo[2], (double)s.z - s.w);
+      hi[0] = fmax(hi[0], (double)s.x + s.w);
+      hi[1] = fmax(hi[1], (double)s.y + s.w);
+      hi[2] = fmax(hi[2], (double)s.z + s.w);
+      na = fmaxf(na, a.aux[p].n_ainv);
+      nb = fmaxf(nb, a.aux[p].n_binv);
+      cs = fmaxf(cs, a.aux[p].cull_scale);
+    }
+    Cluster cl;
+    if (any) {
+      double C[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+      const float Cx = (float)C[0], Cy = (float)C[1], Cz = (float)C[2];
+      double R = 0.0;
+      for (int k = 0; k < cnt; ++k) {
+        const int p = a.order[first + k];
+        const float4 s = a.hot[p].sphere;
+        if (s.w < 0.f) continue;
+        const double dx = (double)s.x - Cx, dy = (double)s.y - Cy, dz = (double)s.z - Cz;
+        R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz) + (double)s.w);
+      }
+      cl.sphere = make_float4(Cx, Cy, Cz, __double2float_ru(R * (1.0 + 1e-12)));
+    } else {
+      cl.sphere = make_float4(0.f, 0.f, 0.f, -1.0f);
+    }
+    cl.aux = make_float4(na, nb, cs, __uint_as_float((unsigned int)first | ((unsigned int)cnt << 16)));
+    a.clusters[cidx] = cl;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_refit(const RefitArgs &a, cudaStream_t stream) {
+  k_refit<<<1, kRefitThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace svo

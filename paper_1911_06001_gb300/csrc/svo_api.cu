@@ -1,0 +1,666 @@
+// svo_api.cu -- C ABI of the library (declared in include/svoanim.h).
+//
+// Host-side responsibilities: argument checks, asset and scene tables,
+// device memory, staging of per-frame poses, and kernel launches.  Every
+// per-ray step runs in the kernels of k_trace.cu; the per-frame pose
+// pipeline runs in k_refit.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "svo_build.h"
+#include "svo_internal.h"
+
+namespace svo {
+unsigned long long trace_tile_rays();
+}
+
+using namespace svo;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+svo_status fail(svo_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+svo_status ok() { return SVO_OK; }
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(SVO_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                        \
+  } while (0)
+
+struct AssetRec {
+  bool live = false;
+  int depth = 0;
+  uint64_t n_nodes = 0, n_leaves = 0;
+  uint2 *d_nodes = nullptr;
+  uint32_t *d_rgb = nullptr;
+  int refs = 0;
+};
+
+// Scratch of one stream: launch counters and the FP64 re-intersection list.
+struct Slot {
+  unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
+  unsigned long long *d_fix = nullptr;
+  unsigned long long cap = 0;
+  TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
+  char *d_stage = nullptr;                   // rays | hits | flags staging of trace_rays_host
+  unsigned long long stage_rays = 0;
+};
+
+}  // namespace
+
+struct svo_ctx {
+  int device = 0;
+  int n_sm = 1;
+  std::mutex mu;
+  std::vector<AssetRec> assets;
+  std::unordered_set<svo_scene *> scenes;
+  std::unordered_map<void *, Slot> slots;
+  unsigned int *d_err = nullptr;
+};
+
+struct svo_scene {
+  svo_ctx *ctx = nullptr;
+  int P = 0, L = 0, NC = 0;
+  std::vector<int32_t> parent;
+  std::vector<svo_handle> asset;
+  char *d_mem = nullptr;
+  double *d_local = nullptr, *d_world = nullptr, *d_inv64 = nullptr;
+  PartHot *d_hot = nullptr;
+  PartAux *d_aux = nullptr;
+  Cluster *d_cl = nullptr;
+  int32_t *d_order = nullptr;
+  PartStatic *d_stat = nullptr;
+  int32_t *d_level_order = nullptr, *d_level_start = nullptr;
+  double *h_stage = nullptr;
+  cudaEvent_t ev_stage = nullptr;
+  bool stage_pending = false;
+};
+
+namespace {
+
+AssetRec *find_asset(svo_ctx *ctx, svo_handle h) {
+  if (h == 0 || h > ctx->assets.size()) return nullptr;
+  AssetRec *a = &ctx->assets[h - 1];
+  return a->live ? a : nullptr;
+}
+
+svo_status get_slot(svo_ctx *ctx, void *stream, unsigned long long need, Slot **out) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  Slot &s = ctx->slots[stream];
+  if (!s.d_counters) CK(cudaMalloc(&s.d_counters, 4 * sizeof(unsigned long long)));
+  if (need > s.cap) {
+    unsigned long long cap = need < 65536 ? 65536 : need;
+    unsigned long long *p = nullptr;
+    if (s.d_fix) {
+      // the old list may still be read by queued work on this stream
+      CK(cudaStreamSynchronize((cudaStream_t)stream));
+      CK(cudaFree(s.d_fix));
+      s.d_fix = nullptr;
+      s.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&p, cap * sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(SVO_ERR_OOM, "scratch for %llu rays: %s", cap, cudaGetErrorString(e));
+    s.d_fix = p;
+    s.cap = cap;
+  }
+  *out = &s;
+  return SVO_OK;
+}
+
+TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *flags) {
+  TraceItem it;
+  it.hot = s->d_hot;
+  it.aux = s->d_aux;
+  it.clusters = s->d_cl;
+  it.order = s->d_order;
+  it.inv64 = s->d_inv64;
+  it.rays = reinterpret_cast<const float4 *>(rays);
+  it.hits = reinterpret_cast<uint4 *>(hits);
+  it.ray_flags = flags;
+  it.n = n;
+  it.tile_begin = 0;
+  it.n_parts = s->P;
+  it.n_clusters = s->NC;
+  return it;
+}
+
+svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Slot *slot = nullptr;
+  svo_status rc = get_slot(ctx, stream, total_rays, &slot);
+  if (rc != SVO_OK) return rc;
+  L.tile_counter = slot->d_counters;
+  L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
+  L.fix_list = slot->d_fix;
+  L.fix_capacity = slot->cap;
+  L.err = ctx->d_err;
+  CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
+  CK(launch_trace(L, ctx->n_sm, st));
+  delete slot->pending;
+  slot->pending = nullptr;
+  if (L.flags & SVO_TRACE_FP64_FIX) {
+    if (L.flags & SVO_TRACE_DEFER_FIX)
+      slot->pending = new TraceLaunch(L);
+    else
+      CK(launch_fix(L, ctx->n_sm, st));
+  }
+  return SVO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *svo_last_error(void) { return g_last_error.c_str(); }
+
+const char *svo_status_string(svo_status s) {
+  switch (s) {
+    case SVO_OK: return "SVO_OK";
+    case SVO_ERR_ARG: return "SVO_ERR_ARG";
+    case SVO_ERR_OOM: return "SVO_ERR_OOM";
+    case SVO_ERR_HANDLE: return "SVO_ERR_HANDLE";
+    case SVO_ERR_CUDA: return "SVO_ERR_CUDA";
+    case SVO_ERR_TIMEOUT: return "SVO_ERR_TIMEOUT";
+    case SVO_ERR_ADMIT: return "SVO_ERR_ADMIT";
+    case SVO_ERR_NAN: return "SVO_ERR_NAN";
+    case SVO_ERR_SINGULAR: return "SVO_ERR_SINGULAR";
+    case SVO_ERR_LIMIT: return "SVO_ERR_LIMIT";
+    case SVO_ERR_DEVICE: return "SVO_ERR_DEVICE";
+    default: return "SVO_ERR_UNKNOWN";
+  }
+}
+
+svo_status svo_ctx_create(int32_t device, svo_ctx **out) {
+  if (!out) return fail(SVO_ERR_ARG, "svo_ctx_create: out is NULL");
+  *out = nullptr;
+  int n_dev = 0;
+  CK(cudaGetDeviceCount(&n_dev));
+  if (device < 0 || device >= n_dev) return fail(SVO_ERR_ARG, "svo_ctx_create: device %d of %d", device, n_dev);
+  CK(cudaSetDevice(device));
+  svo_ctx *c = new svo_ctx();
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    if (c->d_err) cudaFree(c->d_err);
+    delete c;
+    return fail(SVO_ERR_CUDA, "svo_ctx_create: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return ok();
+}
+
+svo_status scene_destroy(svo_scene *s);
+
+svo_status svo_ctx_destroy(svo_ctx *ctx) {
+  if (!ctx) return ok();
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  std::vector<svo_scene *> sc(ctx->scenes.begin(), ctx->scenes.end());
+  for (svo_scene *s : sc) scene_destroy(s);
+  for (AssetRec &a : ctx->assets) {
+    if (a.d_nodes) cudaFree(a.d_nodes);
+    if (a.d_rgb) cudaFree(a.d_rgb);
+  }
+  for (auto &kv : ctx->slots) {
+    if (kv.second.d_counters) cudaFree(kv.second.d_counters);
+    if (kv.second.d_fix) cudaFree(kv.second.d_fix);
+    if (kv.second.d_stage) cudaFree(kv.second.d_stage);
+    delete kv.second.pending;
+  }
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return ok();
+}
+
+svo_status svo_check_device(svo_ctx *ctx) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_check_device: ctx is NULL");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaDeviceSynchronize());
+  unsigned int e = 0;
+  CK(cudaMemcpy(&e, ctx->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+  if (e == 0) return ok();
+  return fail(SVO_ERR_DEVICE, "device checks failed: 0x%x%s%s%s%s", e, (e & kErrNodeIndex) ? " node-index" : "",
+              (e & kErrFixOverflow) ? " fix-list-overflow" : "", (e & kErrSingular) ? " singular-pose" : "",
+              (e & kErrStack) ? " stack" : "");
+}
+
+svo_status svo_build_host(const svo_desc *d, uint64_t *n_nodes, uint64_t *n_leaves, void *nodes, uint32_t *rgb) {
+  if (!d) return fail(SVO_ERR_ARG, "svo_build_host: desc is NULL");
+  BuiltOctree b;
+  int rc = build_octree(d->depth, d->n_leaves, d->leaf_ids, d->leaf_rgb, &b);
+  if (rc != SVO_OK) return fail(rc, "svo_build_host: bad leaf list (depth %d, %llu leaves)", d->depth,
+                                (unsigned long long)d->n_leaves);
+  if (n_nodes) *n_nodes = b.n_nodes;
+  if (n_leaves) *n_leaves = b.n_leaves;
+  if (nodes && b.n_nodes) memcpy(nodes, b.nodes.data(), b.n_nodes * 8);
+  if (rgb && b.n_leaves) memcpy(rgb, b.rgb.data(), b.n_leaves * 4);
+  return ok();
+}
+
+svo_status svo_upload(svo_ctx *ctx, const svo_desc *d, svo_handle *out) {
+  if (!ctx || !d || !out) return fail(SVO_ERR_ARG, "svo_upload: NULL argument");
+  BuiltOctree b;
+  int rc = build_octree(d->depth, d->n_leaves, d->leaf_ids, d->leaf_rgb, &b);
+  if (rc != SVO_OK) return fail(rc, "svo_upload: bad leaf list (depth %d)", d->depth);
+  CK(cudaSetDevice(ctx->device));
+  AssetRec a;
+  a.depth = b.depth;
+  a.n_nodes = b.n_nodes;
+  a.n_leaves = b.n_leaves;
+  if (b.n_nodes) {
+    cudaError_t e = cudaMalloc(&a.d_nodes, b.n_nodes * 8);
+    if (e != cudaSuccess) return fail(SVO_ERR_OOM, "svo_upload: %llu nodes: %s", (unsigned long long)b.n_nodes,
+                                      cudaGetErrorString(e));
+    e = cudaMalloc(&a.d_rgb, b.n_leaves * 4);
+    if (e != cudaSuccess) {
+      cudaFree(a.d_nodes);
+      return fail(SVO_ERR_OOM, "svo_upload: leaf payload: %s", cudaGetErrorString(e));
+    }
+    CK(cudaMemcpy(a.d_nodes, b.nodes.data(), b.n_nodes * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(a.d_rgb, b.rgb.data(), b.n_leaves * 4, cudaMemcpyHostToDevice));
+  }
+  a.live = true;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->assets.push_back(a);
+  *out = (svo_handle)ctx->assets.size();
+  return ok();
+}
+
+svo_status svo_release(svo_ctx *ctx, svo_handle h) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_release: ctx is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  AssetRec *a = find_asset(ctx, h);
+  if (!a) return fail(SVO_ERR_HANDLE, "svo_release: unknown handle %u", h);
+  if (a->refs > 0) return fail(SVO_ERR_ARG, "svo_release: asset %u is used by %d scene part(s)", h, a->refs);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (a->d_nodes) cudaFree(a->d_nodes);
+  if (a->d_rgb) cudaFree(a->d_rgb);
+  *a = AssetRec();
+  return ok();
+}
+
+svo_status svo_asset_info(svo_ctx *ctx, svo_handle h, int32_t *depth, uint64_t *n_nodes, uint64_t *n_leaves) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_asset_info: ctx is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  AssetRec *a = find_asset(ctx, h);
+  if (!a) return fail(SVO_ERR_HANDLE, "svo_asset_info: unknown handle %u", h);
+  if (depth) *depth = a->depth;
+  if (n_nodes) *n_nodes = a->n_nodes;
+  if (n_leaves) *n_leaves = a->n_leaves;
+  return ok();
+}
+
+svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, const int32_t *parent,
+                        svo_scene **out) {
+  if (!ctx || !asset || !parent || !out) return fail(SVO_ERR_ARG, "scene_create: NULL argument");
+  *out = nullptr;
+  if (n_parts < 1 || n_parts > kMaxParts)
+    return fail(SVO_ERR_LIMIT, "scene_create: %d parts (1..%d)", n_parts, kMaxParts);
+  std::vector<int32_t> level(n_parts, 0);
+  for (int i = 0; i < n_parts; ++i) {
+    if (parent[i] >= i || parent[i] < -1)
+      return fail(SVO_ERR_ARG, "scene_create: parent[%d] = %d (must be -1 or < %d)", i, parent[i], i);
+    level[i] = parent[i] < 0 ? 0 : level[parent[i]] + 1;
+  }
+  std::vector<PartStatic> stat(n_parts);
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (int i = 0; i < n_parts; ++i) {
+      AssetRec *a = find_asset(ctx, asset[i]);
+      if (!a) return fail(SVO_ERR_HANDLE, "scene_create: part %d: unknown asset %u", i, asset[i]);
+      stat[i].nodes = a->d_nodes;
+      stat[i].n_nodes = (uint32_t)a->n_nodes;
+      stat[i].depth = a->depth;
+      stat[i].parent = parent[i];
+      stat[i].pad = 0;
+    }
+  }
+  int L = 0;
+  for (int i = 0; i < n_parts; ++i) L = level[i] + 1 > L ? level[i] + 1 : L;
+  std::vector<int32_t> lorder, lstart(L + 1, 0);
+  for (int l = 0; l < L; ++l) {
+    lstart[l] = (int32_t)lorder.size();
+    for (int i = 0; i < n_parts; ++i)
+      if (level[i] == l) lorder.push_back(i);
+  }
+  lstart[L] = n_parts;
+  const int P = n_parts;
+  const int NC = (P + kClusterSize - 1) / kClusterSize;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off_local = 0;
+  size_t off_world = al(off_local + P * 12 * sizeof(double));
+  size_t off_inv = al(off_world + P * 12 * sizeof(double));
+  size_t off_hot = al(off_inv + P * 12 * sizeof(double));
+  size_t off_aux = al(off_hot + P * sizeof(PartHot));
+  size_t off_cl = al(off_aux + P * sizeof(PartAux));
+  size_t off_order = al(off_cl + NC * sizeof(Cluster));
+  size_t off_stat = al(off_order + P * sizeof(int32_t));
+  size_t off_lo = al(off_stat + P * sizeof(PartStatic));
+  size_t off_ls = al(off_lo + P * sizeof(int32_t));
+  size_t total = al(off_ls + (L + 1) * sizeof(int32_t));
+  CK(cudaSetDevice(ctx->device));
+  svo_scene *s = new svo_scene();
+  s->ctx = ctx;
+  s->P = P;
+  s->L = L;
+  s->NC = NC;
+  s->parent.assign(parent, parent + P);
+  s->asset.assign(asset, asset + P);
+  cudaError_t e = cudaMalloc(&s->d_mem, total);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(SVO_ERR_OOM, "scene_create: %zu bytes: %s", total, cudaGetErrorString(e));
+  }
+  s->d_local = reinterpret_cast<double *>(s->d_mem + off_local);
+  s->d_world = reinterpret_cast<double *>(s->d_mem + off_world);
+  s->d_inv64 = reinterpret_cast<double *>(s->d_mem + off_inv);
+  s->d_hot = reinterpret_cast<PartHot *>(s->d_mem + off_hot);
+  s->d_aux = reinterpret_cast<PartAux *>(s->d_mem + off_aux);
+  s->d_cl = reinterpret_cast<Cluster *>(s->d_mem + off_cl);
+  s->d_order = reinterpret_cast<int32_t *>(s->d_mem + off_order);
+  s->d_stat = reinterpret_cast<PartStatic *>(s->d_mem + off_stat);
+  s->d_level_order = reinterpret_cast<int32_t *>(s->d_mem + off_lo);
+  s->d_level_start = reinterpret_cast<int32_t *>(s->d_mem + off_ls);
+  std::vector<double> ident(P * 12, 0.0);
+  for (int i = 0; i < P; ++i) ident[12 * i + 0] = ident[12 * i + 5] = ident[12 * i + 10] = 1.0;
+  e = cudaMallocHost(&s->h_stage, P * 12 * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_stage, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_local, ident.data(), P * 12 * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_stat, stat.data(), P * sizeof(PartStatic), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_level_order, lorder.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_level_start, lstart.data(), (L + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    if (s->ev_stage) cudaEventDestroy(s->ev_stage);
+    cudaFree(s->d_mem);
+    delete s;
+    return fail(SVO_ERR_CUDA, "scene_create: %s", cudaGetErrorString(e));
+  }
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (int i = 0; i < P; ++i) find_asset(ctx, asset[i])->refs++;
+    ctx->scenes.insert(s);
+  }
+  svo_status rc = scene_refit(s, nullptr);
+  if (rc == SVO_OK) {
+    cudaError_t e2 = cudaStreamSynchronize(nullptr);
+    if (e2 != cudaSuccess) rc = fail(SVO_ERR_CUDA, "scene_create: %s", cudaGetErrorString(e2));
+  }
+  if (rc != SVO_OK) {
+    scene_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return ok();
+}
+
+svo_status scene_destroy(svo_scene *s) {
+  if (!s) return ok();
+  svo_ctx *ctx = s->ctx;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->scenes.count(s)) return fail(SVO_ERR_HANDLE, "scene_destroy: unknown scene");
+    ctx->scenes.erase(s);
+    for (svo_handle h : s->asset) {
+      AssetRec *a = find_asset(ctx, h);
+      if (a && a->refs > 0) a->refs--;
+    }
+  }
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->ev_stage) cudaEventDestroy(s->ev_stage);
+  if (s->d_mem) cudaFree(s->d_mem);
+  delete s;
+  return ok();
+}
+
+svo_status scene_set_transforms(svo_scene *s, const double *local, void *stream) {
+  if (!s || !local) return fail(SVO_ERR_ARG, "scene_set_transforms: NULL argument");
+  const int n = s->P * 12;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(local[i])) return fail(SVO_ERR_NAN, "scene_set_transforms: entry %d is not finite", i);
+  CK(cudaSetDevice(s->ctx->device));
+  if (s->stage_pending) CK(cudaEventSynchronize(s->ev_stage));  // previous copy out of the staging buffer
+  memcpy(s->h_stage, local, n * sizeof(double));
+  CK(cudaMemcpyAsync(s->d_local, s->h_stage, n * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  CK(cudaEventRecord(s->ev_stage, (cudaStream_t)stream));
+  s->stage_pending = true;
+  return ok();
+}
+
+svo_status scene_set_transforms_device(svo_scene *s, const double *local_dev, void *stream) {
+  if (!s || !local_dev) return fail(SVO_ERR_ARG, "scene_set_transforms_device: NULL argument");
+  CK(cudaSetDevice(s->ctx->device));
+  CK(cudaMemcpyAsync(s->d_local, local_dev, s->P * 12 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return ok();
+}
+
+svo_status scene_refit(svo_scene *s, void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "scene_refit: scene is NULL");
+  CK(cudaSetDevice(s->ctx->device));
+  RefitArgs a;
+  a.n_parts = s->P;
+  a.n_levels = s->L;
+  a.level_order = s->d_level_order;
+  a.level_start = s->d_level_start;
+  a.stat = s->d_stat;
+  a.local = s->d_local;
+  a.world = s->d_world;
+  a.inv64 = s->d_inv64;
+  a.hot = s->d_hot;
+  a.aux = s->d_aux;
+  a.clusters = s->d_cl;
+  a.order = s->d_order;
+  a.n_clusters = s->NC;
+  a.err = s->ctx->d_err;
+  CK(launch_refit(a, (cudaStream_t)stream));
+  return ok();
+}
+
+svo_status scene_read_poses(svo_scene *s, double *world, double *inv, float *inv_f32, float *sphere, void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "scene_read_poses: scene is NULL");
+  CK(cudaSetDevice(s->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int P = s->P;
+  if (world) CK(cudaMemcpyAsync(world, s->d_world, P * 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (inv) CK(cudaMemcpyAsync(inv, s->d_inv64, P * 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<PartHot> hot;
+  if (inv_f32 || sphere) {
+    hot.resize(P);
+    CK(cudaMemcpyAsync(hot.data(), s->d_hot, P * sizeof(PartHot), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < P && (inv_f32 || sphere); ++i) {
+    if (inv_f32) {
+      const float4 r[3] = {hot[i].r0, hot[i].r1, hot[i].r2};
+      for (int k = 0; k < 3; ++k) {
+        inv_f32[12 * i + 4 * k + 0] = r[k].x;
+        inv_f32[12 * i + 4 * k + 1] = r[k].y;
+        inv_f32[12 * i + 4 * k + 2] = r[k].z;
+        inv_f32[12 * i + 4 * k + 3] = r[k].w;
+      }
+    }
+    if (sphere) {
+      sphere[4 * i + 0] = hot[i].sphere.x;
+      sphere[4 * i + 1] = hot[i].sphere.y;
+      sphere[4 * i + 2] = hot[i].sphere.z;
+      sphere[4 * i + 3] = hot[i].sphere.w;
+    }
+  }
+  return ok();
+}
+
+svo_status scene_read_clusters(svo_scene *s, int32_t *n_clusters, float *sphere, int32_t *order, void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "scene_read_clusters: scene is NULL");
+  CK(cudaSetDevice(s->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_clusters) *n_clusters = s->NC;
+  std::vector<Cluster> cl;
+  if (sphere) {
+    cl.resize(s->NC);
+    CK(cudaMemcpyAsync(cl.data(), s->d_cl, s->NC * sizeof(Cluster), cudaMemcpyDeviceToHost, st));
+  }
+  if (order) CK(cudaMemcpyAsync(order, s->d_order, s->P * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int c = 0; c < s->NC && sphere; ++c) {
+    sphere[4 * c + 0] = cl[c].sphere.x;
+    sphere[4 * c + 1] = cl[c].sphere.y;
+    sphere[4 * c + 2] = cl[c].sphere.z;
+    sphere[4 * c + 3] = cl[c].sphere.w;
+  }
+  return ok();
+}
+
+svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *ray_flags,
+                      uint32_t flags, svo_trace_stats *stats, void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "trace_rays: scene is NULL");
+  if (n == 0) return ok();
+  if (!rays || !hits) return fail(SVO_ERR_ARG, "trace_rays: rays/hits is NULL");
+  if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
+    return fail(SVO_ERR_ARG, "trace_rays: rays and hits must be 16-byte aligned");
+  if (n >= (1ull << 40)) return fail(SVO_ERR_LIMIT, "trace_rays: %llu rays", (unsigned long long)n);
+  if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_rays: STATS without stats buffer");
+  CK(cudaSetDevice(s->ctx->device));
+  TraceLaunch *L = new TraceLaunch();
+  L->items[0] = make_item(s, rays, n, hits, ray_flags);
+  L->n_items = 1;
+  L->flags = flags;
+  L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
+  const unsigned long long tile = trace_tile_rays();
+  L->n_tiles = (n + tile - 1) / tile;
+  svo_status rc = run_trace(s->ctx, *L, n, stream);
+  delete L;
+  return rc;
+}
+
+svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_items, uint32_t flags,
+                       svo_trace_stats *stats, void *stream) {
+  if (!ctx || (n_items > 0 && !items)) return fail(SVO_ERR_ARG, "trace_batch: NULL argument");
+  if (n_items < 0) return fail(SVO_ERR_ARG, "trace_batch: n_items < 0");
+  if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_batch: STATS without stats buffer");
+  CK(cudaSetDevice(ctx->device));
+  const unsigned long long tile = trace_tile_rays();
+  for (int b = 0; b < n_items; b += kMaxBatchItems) {
+    const int cnt = (n_items - b) < kMaxBatchItems ? (n_items - b) : kMaxBatchItems;
+    TraceLaunch *L = new TraceLaunch();
+    L->n_items = 0;
+    unsigned long long tiles = 0, total = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const svo_batch_item &it = items[b + i];
+      if (!it.scene) {
+        delete L;
+        return fail(SVO_ERR_ARG, "trace_batch: item %d has no scene", b + i);
+      }
+      if (it.scene->ctx != ctx) {
+        delete L;
+        return fail(SVO_ERR_ARG, "trace_batch: item %d belongs to another context", b + i);
+      }
+      if (it.n == 0) continue;
+      if (!it.rays || !it.hits || (reinterpret_cast<uintptr_t>(it.rays) & 15) ||
+          (reinterpret_cast<uintptr_t>(it.hits) & 15)) {
+        delete L;
+        return fail(SVO_ERR_ARG, "trace_batch: item %d rays/hits NULL or not 16-byte aligned", b + i);
+      }
+      TraceItem ti = make_item(it.scene, it.rays, it.n, it.hits, it.ray_flags);
+      ti.tile_begin = tiles;
+      tiles += (it.n + tile - 1) / tile;
+      total += it.n;
+      L->items[L->n_items++] = ti;
+    }
+    if (L->n_items > 0) {
+      L->flags = flags;
+      L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
+      L->n_tiles = tiles;
+      svo_status rc = run_trace(ctx, *L, total, stream);
+      if (rc != SVO_OK) {
+        delete L;
+        return rc;
+      }
+    }
+    delete L;
+  }
+  return ok();
+}
+
+svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo_hit *hits_host,
+                           uint32_t *ray_flags_host, uint32_t flags, void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "trace_rays_host: scene is NULL");
+  if (n == 0) return ok();
+  if (!rays_host || !hits_host) return fail(SVO_ERR_ARG, "trace_rays_host: rays/hits is NULL");
+  if (flags & SVO_TRACE_STATS) return fail(SVO_ERR_ARG, "trace_rays_host: STATS needs a device stats buffer");
+  CK(cudaSetDevice(s->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  char *stage = nullptr;
+  {
+    std::lock_guard<std::mutex> g(s->ctx->mu);
+    Slot &sl = s->ctx->slots[stream];
+    if (n > sl.stage_rays) {
+      if (sl.d_stage) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaFree(sl.d_stage));
+        sl.d_stage = nullptr;
+        sl.stage_rays = 0;
+      }
+      cudaError_t e = cudaMalloc(&sl.d_stage, n * (32 + 16 + 4));
+      if (e != cudaSuccess) return fail(SVO_ERR_OOM, "trace_rays_host: staging: %s", cudaGetErrorString(e));
+      sl.stage_rays = n;
+    }
+    stage = sl.d_stage;
+  }
+  const unsigned long long cap = s->ctx->slots[stream].stage_rays;
+  float *d_rays = reinterpret_cast<float *>(stage);
+  svo_hit *d_hits = reinterpret_cast<svo_hit *>(stage + cap * 32);
+  uint32_t *d_flags = ray_flags_host ? reinterpret_cast<uint32_t *>(stage + cap * 48) : nullptr;
+  CK(cudaMemcpyAsync(d_rays, rays_host, n * 32, cudaMemcpyHostToDevice, st));
+  svo_status rc = trace_rays(s, d_rays, n, d_hits, d_flags, flags & ~SVO_TRACE_DEFER_FIX, nullptr, stream);
+  if (rc != SVO_OK) return rc;
+  CK(cudaMemcpyAsync(hits_host, d_hits, n * 16, cudaMemcpyDeviceToHost, st));
+  if (d_flags) CK(cudaMemcpyAsync(ray_flags_host, d_flags, n * 4, cudaMemcpyDeviceToHost, st));
+  return ok();
+}
+
+svo_status trace_fix_pending(svo_ctx *ctx, void *stream) {
+  if (!ctx) return fail(SVO_ERR_ARG, "trace_fix_pending: ctx is NULL");
+  CK(cudaSetDevice(ctx->device));
+  TraceLaunch *L = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->slots.find(stream);
+    if (it == ctx->slots.end() || !it->second.pending) return ok();
+    L = it->second.pending;
+    it->second.pending = nullptr;
+  }
+  cudaError_t e = launch_fix(*L, ctx->n_sm, (cudaStream_t)stream);
+  delete L;
+  if (e != cudaSuccess) return fail(SVO_ERR_CUDA, "trace_fix_pending: %s", cudaGetErrorString(e));
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// svo_internal.h -- device data layouts shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "svoanim.h"
+
+namespace svo {
+
+constexpr uint32_t kMissPart = 0xFFFFFFFFu;
+constexpr unsigned long long kMissVoxel = 0xFFFFFFFFFFFFFFFFull;
+constexpr int kMaxDepth = SVO_MAX_DEPTH;
+constexpr int kMaxParts = SVO_MAX_PARTS;
+constexpr int kClusterSize = 8;                 // parts per sphere-hierarchy cluster
+constexpr int kMaxClusters = kMaxParts / kClusterSize;
+constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
+
+// Device error word bits (svo_check_device reports them).
+constexpr unsigned int kErrNodeIndex = 1u;      // a child index fell outside the node array
+constexpr unsigned int kErrFixOverflow = 2u;    // the FP64 re-intersection list overflowed
+constexpr unsigned int kErrSingular = 4u;       // a composed pose was not invertible
+constexpr unsigned int kErrStack = 8u;          // traversal stack exceeded kMaxDepth
+
+// Static per-part data written at scene_create.
+struct PartStatic {
+  const uint2 *nodes;   // asset's interior nodes (8 B each, breadth-first)
+  uint32_t n_nodes;
+  int32_t depth;
+  int32_t parent;
+  int32_t pad;
+};
+
+// Per-frame FP32 data of a part used by the trace kernel (64 B, staged in
+// shared memory).  rows: world->local [Ainv | binv]; sphere: conservative
+// bounding sphere in world space.
+struct PartHot {
+  float4 r0, r1, r2;
+  float4 sphere;
+};
+
+// Per-frame scalars of a part (32 B).
+struct PartAux {
+  const uint2 *nodes;
+  uint32_t n_nodes;
+  int32_t depth;
+  float n_ainv;      // upper bound of ||Ainv||_inf (max abs row sum of the FP32 rows)
+  float n_binv;      // upper bound of ||binv||_inf
+  float cull_scale;  // upper bound of 2*sqrt(3)*||A||_F (local -> world length)
+  uint32_t pad;
+};
+
+// Cluster of up to kClusterSize parts (consecutive in `order`).
+struct Cluster {
+  float4 sphere;  // encloses the member spheres
+  float4 aux;     // max n_ainv, max n_binv, max cull_scale, bits: first | count << 16
+};
+
+// One item of a trace launch (by value in the kernel parameters).
+struct TraceItem {
+  const PartHot *hot;
+  const PartAux *aux;
+  const Cluster *clusters;
+  const int32_t *order;
+  const double *inv64;  // FP64 world->local rows (12 per part)
+  const float4 *rays;   // 2 float4 per ray
+  uint4 *hits;          // svo_hit per ray
+  uint32_t *ray_flags;  // or nullptr
+  unsigned long long n;
+  unsigned long long tile_begin;
+  int32_t n_parts;
+  int32_t n_clusters;
+};
+
+struct TraceLaunch {
+  TraceItem items[kMaxBatchItems];
+  int32_t n_items;
+  uint32_t flags;
+  unsigned long long n_tiles;
+  unsigned long long *tile_counter;   // zeroed before the launch
+  unsigned long long *fix_list;       // (item << 40) | ray, capacity fix_capacity
+  unsigned int *fix_count;            // zeroed before the launch
+  unsigned long long fix_capacity;
+  svo_trace_stats *stats;
+  unsigned int *err;
+};
+
+// Kernel launchers (k_trace.cu, k_refit.cu).
+cudaError_t launch_trace(const TraceLaunch &L, int n_sm, cudaStream_t stream);
+cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream);
+
+struct RefitArgs {
+  int32_t n_parts;
+  int32_t n_levels;
+  const int32_t *level_order;  // parts grouped by tree level
+  const int32_t *level_start;  // n_levels + 1
+  const PartStatic *stat;
+  const double *local;         // parent <- part, 12 per part
+  double *world;
+  double *inv64;
+  PartHot *hot;
+  PartAux *aux;
+  Cluster *clusters;
+  int32_t *order;
+  int32_t n_clusters;
+  unsigned int *err;
+};
+cudaError_t launch_refit(const RefitArgs &a, cudaStream_t stream);
+
+}  // namespace svo

@@ -442,13 +442,16 @@ def articulated_figure(seed: int | None = None, depth: int = 9) -> ArticulatedFi
     phase = rng.uniform(0.0, 2 * math.pi, P)
     view = np.array([0.35, 0.45, 1.0]) + 0.1 * rng.standard_normal(3)
     view /= np.linalg.norm(view)
+    # camera framing chosen for this topology: the figure spans about 6 x 4.5
+    # cube widths around (0.25, 0.28, -0.1); 5.2 widths away it fills the frame
+    target = np.array([0.25, 0.28, -0.1])
     scene = Scene(
         name="ART",
         assets=assets,
         part_asset=np.arange(P, dtype=np.int32),
         parent=parent,
         local=np.zeros((P, 12)),
-        meta={"eye": view * 7.5, "target": np.zeros(3), "frames": 60},
+        meta={"eye": target + view * 5.2, "target": target, "frames": 60},
     )
     fig = ArticulatedFigure(scene=scene, attach=attach, joint=joint, rest=rest, axis=axis, freq=freq, phase=phase)
     scene.local = fig.pose(0)

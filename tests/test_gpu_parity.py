@@ -1,0 +1,314 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bar: part and voxel ids bit-exact on every ray the FP32 path does not flag;
+hit t within 1e-5 * max(|t|, leaf diagonal); flagged rays re-intersected in
+FP64 and compared the same way (mismatches counted, expected zero).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from golden_cases import case_scene, load_hand_cases
+from gpu_helpers import GpuScene, compare
+
+pytestmark = pytest.mark.gpu
+
+FLAG_SETS = {
+    "plain": 0,
+    "cull": 1,
+    "cull_sort": 3,
+    "fix": 4,
+    "cull_fix": 5,
+    "default": 7,
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1911_06001_gb300 as g
+
+    c = g.Context(0)
+    yield c
+    c.check_device()
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pr1(ctx):
+    s = synthetic.pr1_scene()
+    return s, GpuScene(ctx, s), oracle.SceneOracle(s)
+
+
+def test_refit_matches_oracle(ctx, pr1):
+    scene, gs, so = pr1
+    got = gs.sc.read_poses()
+    world, inv = so.poses(gs.local)
+    assert np.allclose(got["world"], world, rtol=0, atol=1e-13 * np.abs(world).max())
+    assert np.allclose(got["inv"], inv, rtol=0, atol=1e-12 * max(1.0, np.abs(inv).max()))
+    assert np.array_equal(got["inv_f32"], got["inv"].astype(np.float32))
+    sph = oracle.part_spheres(world)
+    dc = np.linalg.norm(got["sphere"][:, :3].astype(np.float64) - sph[:, :3], axis=1)
+    r = got["sphere"][:, 3].astype(np.float64)
+    assert np.all(dc + sph[:, 3] <= r)  # the FP32 sphere encloses the exact one
+    assert np.all(r <= sph[:, 3] * (1 + 1e-6) + 2 * dc + 1e-30)
+    cl = gs.sc.read_clusters()
+    assert sorted(cl["order"].tolist()) == list(range(scene.n_parts))
+    for c in range(cl["sphere"].shape[0]):
+        C = cl["sphere"][c].astype(np.float64)
+        for p in cl["order"][8 * c: 8 * c + 8]:
+            s = got["sphere"][p].astype(np.float64)
+            assert np.linalg.norm(s[:3] - C[:3]) + s[3] <= C[3] * (1 + 1e-12)
+
+
+def test_five_level_chain_compose(ctx):
+    """Long transform chains composed in FP64 on the device match the oracle."""
+    rng = np.random.default_rng(5)
+    asset = synthetic.make_asset(4, (np.array([1, 2]), np.array([3, 3]), np.array([0, 15])))
+    P = 6
+    parent = np.array([-1, 0, 1, 2, 3, 4], np.int32)
+    local = np.array([synthetic.affine12(synthetic.euler_xyz(*rng.uniform(-3, 3, 3)), rng.uniform(-1e4, 1e4, 3) / 8192)
+                      for _ in range(P)])
+    scene = synthetic.Scene("chain", [asset], np.zeros(P, np.int32), parent, local)
+    gs = GpuScene(ctx, scene)
+    got = gs.sc.read_poses()
+    world = oracle.compose(parent, local)
+    inv = oracle.invert(world)
+    assert np.allclose(got["world"], world, rtol=0, atol=1e-12)
+    assert np.allclose(got["inv"], inv, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("case", load_hand_cases(), ids=lambda c: c["name"])
+def test_hand_cases_gpu(ctx, case):
+    scene, rays = case_scene(case)
+    gs = GpuScene(ctx, scene)
+    for flags in (0, 4, 7):
+        res = gs.trace(rays.astype(np.float32), flags)
+        for i, exp in enumerate(case["hits"]):
+            uncertain = (res["flags"][i] & 1) != 0
+            if exp is None:
+                if not uncertain or flags & 4:
+                    assert math.isinf(res["t"][i]) and res["part"][i] == oracle.MISS_PART, (flags, res)
+            else:
+                if not uncertain or flags & 4:
+                    assert abs(res["t"][i] - exp[0]) <= 1e-6 * max(1.0, exp[0]), (flags, res)
+                    assert int(res["part"][i]) == exp[1] and int(res["voxel"][i]) == exp[2], (flags, res)
+
+
+@pytest.mark.parametrize("flags", list(FLAG_SETS.values()), ids=list(FLAG_SETS.keys()))
+def test_pr1_parity(ctx, pr1, flags):
+    scene, gs, so = pr1
+    rays = synthetic.pr1_rays(scene)[: 16384 - 77]  # ragged tail
+    ora = so.trace(rays)
+    res = gs.trace(rays, flags)
+    rep = compare(scene, gs.local, rays, res, ora)
+    assert rep["hits"] > 1000
+    assert rep["flagged"] <= 0.05 * rep["rays"], rep
+    print("PR1", flags, rep)
+
+
+def test_flags_do_not_change_results(ctx, pr1):
+    """Culling and depth sorting only save work (Sec. IV; the optimised and
+    unoptimised animations are identical): with FP64 re-intersection the hits
+    are bit-identical under every flag combination."""
+    scene, gs, so = pr1
+    rays = synthetic.pr1_rays(scene)
+    ref = gs.trace(rays, 4)
+    for f in (5, 6, 7):
+        res = gs.trace(rays, f)
+        for k in ("t", "part", "voxel", "flags"):
+            assert np.array_equal(res[k], ref[k]), (f, k)
+
+
+def test_articulated_reduced_parity(ctx):
+    fig = synthetic.articulated_figure(depth=7)
+    gs = GpuScene(ctx, fig.scene)
+    so = oracle.SceneOracle(fig.scene)
+    rays = fig.rays(320, 180)
+    for frame in (0, 17, 45):
+        local = fig.pose(frame)
+        gs.set_pose(local)
+        ora = so.trace(rays, local=local)
+        res = gs.trace(rays, 7)
+        rep = compare(fig.scene, local, rays, res, ora)
+        assert rep["hits"] > 5000
+        print("ART-reduced frame", frame, rep)
+
+
+def test_incoherent_affine_many_parts(ctx):
+    """Random affine poses (scale 0.5-2, shear <= 0.1), directions uniform on
+    the sphere, 300 parts (beyond the shared-memory part table), mixed depths."""
+    rng = np.random.default_rng(2024)
+    assets = []
+    for depth in (3, 4, 5, 6):
+        n = 1 << depth
+        occ = rng.random(n ** 3) < 0.04
+        idx = np.nonzero(occ)[0]
+        assets.append(synthetic.make_asset(depth, (idx % n, (idx // n) % n, idx // (n * n))))
+    P = 300
+    local = []
+    for _ in range(P):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        S = np.diag(rng.uniform(0.5, 2.0, 3))
+        H = np.eye(3)
+        H[0, 1], H[0, 2], H[1, 2] = rng.uniform(-0.1, 0.1, 3)
+        local.append(synthetic.affine12(R @ S @ H, rng.uniform(-8, 8, 3)))
+    scene = synthetic.Scene("bat-like", assets, rng.integers(0, 4, P).astype(np.int32),
+                            np.full(P, -1, np.int32), np.array(local))
+    gs = GpuScene(ctx, scene)
+    so = oracle.SceneOracle(scene)
+    rays = synthetic.random_rays(20000 - 3, rng, (-9,) * 3, (9,) * 3)
+    ora = so.trace(rays)
+    for flags in (7, 4):
+        res = gs.trace(rays, flags)
+        rep = compare(scene, scene.local, rays, res, ora)
+        assert rep["hits"] > 2000
+        print("incoherent", flags, rep)
+
+
+def test_edge_rays(ctx, pr1):
+    scene, gs, so = pr1
+    base = synthetic.pr1_rays(scene)[8000:8064].copy()
+    rays = base.copy()
+    rays[0, 3], rays[0, 7] = 5.0, 1.0          # tmin > tmax: empty segment
+    rays[1, 4:7] = 0.0                          # zero direction
+    rays[2, 0] = np.nan                         # NaN origin
+    rays[3, 7] = 0.0                            # tmax = 0 with origin outside everything
+    rays[4, 4:7] = [1.0, 0.0, 0.0]              # axis-aligned
+    rays[5, 4:7] = [0.0, -1.0, 0.0]
+    rays[6, 4:7] *= 1000.0                      # long direction (t scales)
+    rays[7, 4:7] *= 1e-3                        # short direction
+    res = gs.trace(rays, 7)
+    for i in (0, 1, 2, 3):
+        assert res["part"][i] == oracle.MISS_PART and math.isinf(res["t"][i])
+    ok = np.ones(len(rays), bool)
+    ok[[0, 1, 2, 3]] = False
+    ora = so.trace(rays[ok])
+    sub = {k: v[ok] for k, v in res.items()}
+    compare(scene, gs.local, rays[ok], sub, ora)
+    # scaling d by s divides t by s
+    r6 = gs.trace(base[6:7], 7)
+    assert abs(res["t"][6] * 1000.0 - r6["t"][0]) <= 1e-5 * r6["t"][0] or not np.isfinite(r6["t"][0])
+
+
+def test_empty_and_degenerate_assets(ctx):
+    rng = np.random.default_rng(12)
+    empty = synthetic.Asset(5, np.zeros(0, np.uint64), np.zeros(0, np.uint32))
+    one = synthetic.make_asset(1, (np.array([1]), np.array([0]), np.array([1])))
+    deep = synthetic.make_asset(16, (np.array([1, 40000, 65535]), np.array([2, 30000, 65535]),
+                                     np.array([3, 20000, 0])))
+    dense_n = 8
+    g3 = np.arange(dense_n)
+    xx, yy, zz = np.meshgrid(g3, g3, g3, indexing="ij")
+    full = synthetic.make_asset(3, (xx.ravel(), yy.ravel(), zz.ravel()))
+    assets = [empty, one, deep, full]
+    local = np.array([synthetic.affine12(synthetic.euler_xyz(*rng.uniform(-1, 1, 3)), rng.uniform(-2, 2, 3))
+                      for _ in range(4)])
+    scene = synthetic.Scene("degenerate", assets, np.arange(4, dtype=np.int32), np.array([-1, 0, -1, 2], np.int32),
+                            local)
+    gs = GpuScene(ctx, scene)
+    so = oracle.SceneOracle(scene)
+    rays = synthetic.random_rays(8192, rng, (-3,) * 3, (3,) * 3)
+    ora = so.trace(rays)
+    res = gs.trace(rays, 7)
+    rep = compare(scene, local, rays, res, ora)
+    assert rep["hits"] > 500
+    # the deep asset is reachable: rays aimed at its leaf centres hit it
+    world = oracle.compose(scene.parent, local)
+    W = world[2].reshape(3, 4)
+    tgt = np.array([[1.5, 2.5, 3.5], [40000.5, 30000.5, 20000.5], [65535.5, 65535.5, 0.5]]) / 65536.0
+    pts = tgt @ W[:, :3].T + W[:, 3]
+    org = pts + np.array([5.0, 4.0, 3.0])
+    r2 = np.zeros((3, 8), np.float32)
+    r2[:, 0:3] = org
+    r2[:, 4:7] = pts - org
+    r2[:, 7] = np.inf
+    ora2 = so.trace(r2)
+    res2 = gs.trace(r2, 7)
+    compare(scene, local, r2, res2, ora2)
+    assert (ora2["part"] == 2).sum() >= 2
+
+
+def test_batch_equals_individual(ctx, pr1):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    fig = synthetic.articulated_figure(depth=6)
+    ga = GpuScene(ctx, fig.scene)
+    r1 = synthetic.pr1_rays(scene)
+    r2 = fig.rays(200, 120)
+    r3 = r1[::7].copy()
+    items, outs = [], []
+    for sc, r in ((gs, r1), (ga, r2), (gs, r3)):
+        rt = torch.from_numpy(np.ascontiguousarray(r)).cuda()
+        ht = torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda")
+        ft = torch.empty(r.shape[0], dtype=torch.int32, device="cuda")
+        items.append((sc.sc, rt, ht, ft))
+        outs.append((sc, r, ht, ft))
+    ctx.trace_batch(items, flags=7)
+    torch.cuda.synchronize()
+    for sc, r, ht, ft in outs:
+        ref = sc.trace(r, 7)
+        got = g.decode_hits(ht)
+        for k in ("t", "part", "voxel"):
+            assert np.array_equal(got[k], ref[k]), k
+        assert np.array_equal(ft.cpu().numpy().astype(np.uint32), ref["flags"])
+
+
+def test_stats_counters(ctx, pr1):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    rays = torch.from_numpy(synthetic.pr1_rays(scene)).cuda()
+    st = g.new_stats()
+    rf = torch.zeros(rays.shape[0], dtype=torch.int32, device="cuda")
+    gs.sc.trace(rays, flags=7 | g.TRACE_STATS, ray_flags=rf, stats=st)
+    torch.cuda.synchronize()
+    s = g.read_stats(st)
+    flags = rf.cpu().numpy()
+    assert s["rays"] == rays.shape[0]
+    assert s["flagged"] == int(((flags & 1) != 0).sum())
+    assert s["fixed"] == s["flagged"]
+    assert s["nodes_visited"] > 0 and s["parts_entered"] <= s["parts_tested"]
+    assert s["passes"] >= s["rays"]
+
+
+def test_articulated_full_size_sampled(ctx):
+    """The bench workload (1920x1080 rays, depth-9 parts) in the bench's launch
+    configuration; the oracle checks a random sample of 20000 rays."""
+    fig = synthetic.articulated_figure()
+    gs = GpuScene(ctx, fig.scene)
+    so = oracle.SceneOracle(fig.scene)
+    rays = fig.rays()
+    rng = np.random.default_rng(99)
+    for frame in (0, 31):
+        local = fig.pose(frame)
+        gs.set_pose(local)
+        res = gs.trace(rays, 7)
+        idx = rng.choice(rays.shape[0], 20000, replace=False)
+        ora = so.trace(rays[idx], local=local)
+        sub = {k: v[idx] for k, v in res.items()}
+        rep = compare(fig.scene, local, rays[idx], sub, ora)
+        assert rep["hits"] > 4000
+        print("ART full sampled frame", frame, rep, "flag rate full frame",
+              float(((res["flags"] & 1) != 0).mean()))
