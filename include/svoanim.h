@@ -105,6 +105,9 @@ typedef struct {
   unsigned long long nodes_visited; /* interior node descriptors fetched (8 B each) */
   unsigned long long leaves_tested; /* leaf cells slab-tested */
   unsigned long long passes;        /* candidate-list passes (> rays when lists overflow) */
+  unsigned long long flag_winner;   /* flagged because the nearest candidate was not certainly hit */
+  unsigned long long flag_overlap;  /* flagged because another candidate's entry bound reached it */
+  unsigned long long flag_width;    /* flagged because the winner's t interval was too wide */
 } svo_trace_stats;
 
 /* One entry of a batched trace (trace_batch). */
@@ -177,8 +180,10 @@ svo_status scene_set_transforms_device(svo_scene *scene, const double *local_3x4
  * singular pose sets the device error word (svo_check_device). */
 svo_status scene_refit(svo_scene *scene, void *stream);
 /* Copy the last refit's per-part data to host arrays (any may be NULL) and
- * synchronise `stream`: world and inverse poses (n_parts*12 doubles each),
- * FP32 inverse rows (n_parts*12 floats), FP32 spheres (n_parts*4 floats:
+ * synchronise `stream`: world and inverse poses (n_parts*12 doubles each,
+ * [A | b] rows), the FP32 rows used by tracing (n_parts*12 floats: the
+ * inverse matrix rounded to FP32 in columns 0-2 and, in column 3, the local
+ * coordinates of the FP32 sphere centre), FP32 spheres (n_parts*4 floats:
  * cx cy cz r). */
 svo_status scene_read_poses(svo_scene *scene, double *world, double *inv, float *inv_f32, float *sphere,
                             void *stream);
@@ -194,8 +199,9 @@ svo_status scene_read_clusters(svo_scene *scene, int32_t *n_clusters, float *sph
  * ray; hits: device, n svo_hit; ray_flags: device, n uint32 or NULL;
  * stats: device svo_trace_stats or NULL (used with SVO_TRACE_STATS; the caller
  * zeroes it).  Traversal runs in FP32; a ray whose closest hit FP32 cannot
- * certify (the error-bounded intervals of two candidates overlap, or the
- * winner's own interval is wider than 2^-17 of its t) is flagged, and with
+ * certify (the error-bounded intervals of two candidates overlap, or half
+ * the winner's own interval exceeds 2^-17 of max(t, leaf diagonal / |d|))
+ * is flagged, and with
  * SVO_TRACE_FP64_FIX re-intersected in FP64.  The scene must have been
  * refitted since its last scene_set_transforms.  If n exceeds the largest n
  * traced so far on this context the call grows the context's scratch with

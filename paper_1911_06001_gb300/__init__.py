@@ -199,10 +199,11 @@ def decode_hits(hits) -> dict:
 def new_stats(device="cuda"):
     import torch
 
-    return torch.zeros(8, dtype=torch.int64, device=device)
+    return torch.zeros(11, dtype=torch.int64, device=device)
 
 
 def read_stats(stats) -> dict:
-    names = ("rays", "flagged", "fixed", "parts_tested", "parts_entered", "nodes_visited", "leaves_tested", "passes")
+    names = ("rays", "flagged", "fixed", "parts_tested", "parts_entered", "nodes_visited", "leaves_tested", "passes",
+             "flag_winner", "flag_overlap", "flag_width")
     v = stats.detach().cpu().numpy().astype(np.uint64)
     return {n: int(x) for n, x in zip(names, v)}

@@ -44,7 +44,8 @@ class SvoDesc(C.Structure):
 
 class SvoTraceStats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("rays", "flagged", "fixed", "parts_tested", "parts_entered",
-                                             "nodes_visited", "leaves_tested", "passes")]
+                                             "nodes_visited", "leaves_tested", "passes", "flag_winner",
+                                             "flag_overlap", "flag_width")]
 
 
 class SvoBatchItem(C.Structure):

@@ -6,8 +6,9 @@
 //  2. invert each W_i in FP64 (Eq. 3): A^-1 = adj(A)/det(A), b' = -A^-1 b,
 //     which for a rigid pose equals the transposed rotation and the negated,
 //     rotated translation (Sec. III-A);
-//  3. emit the FP32 world->local rows the trace kernel uses, plus bounds on
-//     their norms for the trace kernel's rounding-error bound;
+//  3. emit the FP32 world->local matrix the trace kernel uses, the local
+//     coordinates of the FP32 sphere centre (FP64-accurate), and bounds on
+//     norms for the trace kernel's rounding-error bound;
 //  4. refit the part bounding spheres (Sec. IV-A: centre and radius follow
 //     from the pose): centre = image of the cube centre, radius = farthest
 //     image corner, rounded outward to FP32;
@@ -120,18 +121,12 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     float f[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) f[k] = (float)inv[k];
-    double rowsum = 0.0, bmax = 0.0;
+    double rowsum = 0.0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       double s = fabs((double)f[r * 4]) + fabs((double)f[r * 4 + 1]) + fabs((double)f[r * 4 + 2]);
       rowsum = fmax(rowsum, s);
-      bmax = fmax(bmax, fabs((double)f[r * 4 + 3]));
     }
-    double fro = 0.0;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) fro += m[r * 4 + c] * m[r * 4 + c];
     // sphere: centre = W (1/2,1/2,1/2), radius = farthest image corner
     double c[3];
 #pragma unroll
@@ -151,10 +146,16 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     const float cfx = (float)c[0], cfy = (float)c[1], cfz = (float)c[2];
     const double dcx = c[0] - cfx, dcy = c[1] - cfy, dcz = c[2] - cfz;
     const double rr = (sqrt(r2) + sqrt(dcx * dcx + dcy * dcy + dcz * dcz)) * (1.0 + 1e-12);
+    // local coordinates of the FP32 centre (close to (1/2, 1/2, 1/2))
+    float lc[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      lc[q] = (float)(inv[q * 4] * (double)cfx + inv[q * 4 + 1] * (double)cfy + inv[q * 4 + 2] * (double)cfz +
+                      inv[q * 4 + 3]);
     PartHot h;
-    h.r0 = make_float4(f[0], f[1], f[2], f[3]);
-    h.r1 = make_float4(f[4], f[5], f[6], f[7]);
-    h.r2 = make_float4(f[8], f[9], f[10], f[11]);
+    h.r0 = make_float4(f[0], f[1], f[2], lc[0]);
+    h.r1 = make_float4(f[4], f[5], f[6], lc[1]);
+    h.r2 = make_float4(f[8], f[9], f[10], lc[2]);
     h.sphere = make_float4(cfx, cfy, cfz, ok ? __double2float_ru(rr) : -1.0f);
     a.hot[i] = h;
     PartAux x;
@@ -162,9 +163,17 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     x.n_nodes = a.stat[i].n_nodes;
     x.depth = a.stat[i].depth;
     x.n_ainv = __double2float_ru(rowsum * (1.0 + 1e-12));
-    x.n_binv = __double2float_ru(bmax * (1.0 + 1e-12));
-    x.cull_scale = __double2float_ru(2.0 * 1.7320508075688772 * sqrt(fro) * (1.0 + 1e-12));
-    x.pad = 0;
+    x.spare0 = 0.f;
+    x.spare1 = 0.f;
+    {
+      double dg = 0.0;
+#pragma unroll
+      for (int rr2 = 0; rr2 < 3; ++rr2) {
+        const double v = m[rr2 * 4] + m[rr2 * 4 + 1] + m[rr2 * 4 + 2];
+        dg += v * v;
+      }
+      x.hdiag = (float)(sqrt(dg) * ldexp(1.0, -a.stat[i].depth));
+    }
     a.aux[i] = x;
     mn[0] = fminf(mn[0], cfx);
     mn[1] = fminf(mn[1], cfy);
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     const int first = cidx * kClusterSize;
     const int cnt = min(kClusterSize, P - first);
     double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    float na = 0.f, nb = 0.f, cs = 0.f;
+    float na = 0.f;
     bool any = false;
     for (int k = 0; k < cnt; ++k) {
       const int p = a.order[first + k];
@@ -228,8 +237,6 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
       hi[1] = fmax(hi[1], (double)s.y + s.w);
       hi[2] = fmax(hi[2], (double)s.z + s.w);
       na = fmaxf(na, a.aux[p].n_ainv);
-      nb = fmaxf(nb, a.aux[p].n_binv);
-      cs = fmaxf(cs, a.aux[p].cull_scale);
     }
     Cluster cl;
     if (any) {
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     } else {
       cl.sphere = make_float4(0.f, 0.f, 0.f, -1.0f);
     }
-    cl.aux = make_float4(na, nb, cs, __uint_as_float((unsigned int)first | ((unsigned int)cnt << 16)));
+    cl.aux = make_float4(na, 0.f, 0.f, __uint_as_float((unsigned int)first | ((unsigned int)cnt << 16)));
     a.clusters[cidx] = cl;
   }
 }

@@ -49,8 +49,11 @@ struct TraceLaunchT {
   unsigned long long *fix_list;
   unsigned int *fix_count;
   unsigned long long fix_capacity;
+  uint4 *fix_cand;
+  unsigned long long cand_capacity;
   svo_trace_stats *stats;
   unsigned int *err;
+  int32_t one_scene;  // every item traces the same scene: stage its tables in shared memory
 };
 
 namespace {
@@ -60,8 +63,8 @@ constexpr float kTau = 7.62939453125e-6f;      // 2^-17
 constexpr int kCap = 8;                         // candidate parts per pass
 constexpr int kSmemParts = 256;                 // parts staged in shared memory
 constexpr int kBlock = 128;
-constexpr int kRaysPerThread = 4;               // rays per thread per tile
-constexpr int kTile = kBlock * kRaysPerThread;
+constexpr int kRaysPerLane = 4;                 // rays per lane per warp tile
+constexpr int kTile = 32 * kRaysPerLane;        // rays per warp tile
 constexpr unsigned long long kRayBits = 40;
 
 struct Tables {
@@ -103,6 +106,19 @@ __device__ void build_tables(Tables *t) {
     const int m = ((q & 1) << a0) | (((q >> 1) & 1) << a1) | (((q >> 2) & 1) << a2);
     t->k[mir][p][q] = (uint8_t)(m ^ mir);
   }
+}
+
+// The tables are built once per device (svo_ctx_create) and copied into
+// shared memory by every block.
+__device__ __align__(16) Tables g_tables;
+
+__global__ void k_init_tables() { build_tables(&g_tables); }
+
+__device__ __forceinline__ void load_tables(Tables *t) {
+  static_assert(sizeof(Tables) % 16 == 0, "Tables must be a whole number of 16-byte words");
+  const uint4 *src = reinterpret_cast<const uint4 *>(&g_tables);
+  uint4 *dst = reinterpret_cast<uint4 *>(t);
+  for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
 template <typename R>
@@ -154,9 +170,43 @@ struct ExactState {
   unsigned long long vox;
 };
 
-__device__ __forceinline__ void offer(CertState &s, float lo, float hi, float te, bool cert, uint32_t part,
-                                      unsigned long long vox) {
+// Leaves that may still be the closest hit: every candidate whose entry lower
+// bound lo does not exceed hi_min (the best upper bound of a certainly hit
+// leaf).  The true winner is always among them, so a flagged ray can be
+// resolved by intersecting only these leaves in FP64.
+struct Contenders {
+  float lo[kContenders];
+  uint32_t part[kContenders];
+  unsigned long long vox[kContenders];
+  int n;
+  bool overflow;
+};
+
+__device__ __forceinline__ void keep_contender(Contenders &c, float hi_min, float lo, uint32_t part,
+                                               unsigned long long vox) {
+  if (!(lo <= hi_min)) return;
+  if (c.n < kContenders) {
+    c.lo[c.n] = lo;
+    c.part[c.n] = part;
+    c.vox[c.n] = vox;
+    ++c.n;
+    return;
+  }
+  for (int i = 0; i < kContenders; ++i) {
+    if (!(c.lo[i] <= hi_min)) {  // no longer a contender: reuse its slot
+      c.lo[i] = lo;
+      c.part[i] = part;
+      c.vox[i] = vox;
+      return;
+    }
+  }
+  c.overflow = true;
+}
+
+__device__ __forceinline__ void offer(CertState &s, Contenders &c, float lo, float hi, float te, bool cert,
+                                      uint32_t part, unsigned long long vox) {
   if (cert) s.hi_min = fminf(s.hi_min, hi);
+  keep_contender(c, s.hi_min, lo, part, vox);
   const bool better = lo < s.lo1 || (lo == s.lo1 && (part < s.part1 || (part == s.part1 && vox < s.vox1)));
   if (better) {
     s.lo2 = fminf(s.lo2, s.lo1);
@@ -180,20 +230,27 @@ __device__ __forceinline__ void offer(ExactState &s, double t, uint32_t part, un
 }
 
 __device__ __forceinline__ float prune_bound(const CertState &s, float tmax) { return fminf(tmax, s.hi_min); }
-__device__ __forceinline__ double prune_bound(const ExactState &s, double tmax) { return fmin(tmax, s.t); }
+// The same bound in a part's shifted parameter t_rel = t - tshift, rounded up
+// so that pruning stays conservative.
+__device__ __forceinline__ float rel_bound(const CertState &s, float tmax_rel, float tshift) {
+  return fminf(tmax_rel, __fsub_ru(s.hi_min, tshift));
+}
+__device__ __forceinline__ double rel_bound(const ExactState &s, double tmax, double) { return fmin(tmax, s.t); }
 
 struct Counters {
   uint32_t parts_tested, parts_entered, nodes, leaves, passes;
+  uint32_t f_winner, f_overlap, f_width;
 };
 
-// Front-to-back descent of one part in its local frame.  (o, d): local ray;
-// eta: inflation (0 for the exact FP64 search).  State S is CertState (R =
-// float, certified) or ExactState (R = double).
+// Front-to-back descent of one part in its local frame.  (o, d): local ray
+// whose parameter is t - tshift; tmin/tmax are in that shifted parameter;
+// eta: inflation (0 for the exact FP64 search, whose tshift is 0).  State S is
+// CertState (R = float, certified) or ExactState (R = double).
 template <typename R, typename S, bool STATS>
 __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, uint32_t n_nodes, int D, R ox, R oy,
-                                             R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, uint32_t part,
-                                             const Tables *__restrict__ tab, S &st, unsigned int &err,
-                                             Counters &cnt) {
+                                             R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, R tshift, uint32_t part,
+                                             const Tables *__restrict__ tab, S &st, Contenders *con,
+                                             unsigned int &err, Counters &cnt) {
   if (n_nodes == 0) return;
   constexpr bool CERT = sizeof(R) == 4;
   uint32_t mir = 0;
@@ -236,7 +293,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
     if (down) {
       const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
       const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
-      const R tl = prune_bound(st, tmax);
+      const R tl = rel_bound(st, tmax, tshift);
       const R Ax = Slab<R>::t(lx - eta, ix, ox, bx), Ay = Slab<R>::t(ly - eta, iy, oy, by), Az = Slab<R>::t(lz - eta, iz, oz, bz);
       const R Bx = Slab<R>::t((lx + h) - eta, ix, ox, bx), By = Slab<R>::t((ly + h) - eta, iy, oy, by), Bz = Slab<R>::t((lz + h) - eta, iz, oz, bz);
       const R Cx = CERT ? Slab<R>::t((lx + h) + eta, ix, ox, bx) : Bx;
@@ -282,7 +339,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
           if (m & 1u) lo = fmax(lo, Bx);
           if (m & 2u) lo = fmax(lo, By);
           if (m & 4u) lo = fmax(lo, Bz);
-          if (lo > prune_bound(st, tmax)) break;  // later leaves start even later
+          if (lo > rel_bound(st, tmax, tshift)) break;  // later leaves start even later
           if (STATS) ++cnt.leaves;
           const uint32_t vx = 2u * px + (m & 1u), vy = 2u * py + ((m >> 1) & 1u), vz = 2u * pz + ((m >> 2) & 1u);
           const unsigned long long gx = (mir & 1u) ? (side - 1u - vx) : vx;
@@ -296,7 +353,9 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
                                fmin(Slab<R>::t((clz + h) - eta, iz, oz, bz), tmax));
             const R te = fmax(fmax(Slab<R>::t(clx, ix, ox, bx), Slab<R>::t(cly, iy, oy, by)), fmax(Slab<R>::t(clz, iz, oz, bz), tmin));
             const bool cert = dlo <= dhi;
-            offer(st, lo, cert ? dlo : Num<R>::inf(), te, cert, part, vox);
+            // back to the ray's own parameter, rounding the bounds outward
+            offer(st, *con, __fadd_rd(tshift, lo), cert ? __fadd_ru(tshift, dlo) : Num<R>::inf(), tshift + te, cert,
+                  part, vox);
           } else {
             offer(st, lo, part, vox);
           }
@@ -342,7 +401,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
       const int ax = rank == 0 ? a0 : (rank == 1 ? a1 : a2);
       const R Bsel = ax == 0 ? Slab<R>::t((lx + h) - eta, ix, ox, bx) : (ax == 1 ? Slab<R>::t((ly + h) - eta, iy, oy, by) : Slab<R>::t((lz + h) - eta, iz, oz, bz));
       const R en = fmax(T0, Bsel);
-      if (en > prune_bound(st, tmax)) continue;  // this and all later siblings are too far
+      if (en > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
       stk[level].y = (e.y & ~0xFF00u) | (rest << 8);
       const uint32_t k = kt[p * 8 + q];
       const uint32_t cmask = e.y & 0xFFu;
@@ -366,14 +425,16 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
 struct RayW {
   float ox, oy, oz, tmin, dx, dy, dz, tmax;
   float inv_dd;
-  float onorm;  // ||o||_inf
+  float inv_len;  // 1/|d|
+  float onorm;    // ||o||_inf
 };
 
 // Conservative ray / sphere test: sphere (c, R) is hit by the segment.  Eq. 4
 // with a direction of any length: l = c - o, tc = (l.d)/|d|^2, the squared
 // distance of the centre to the line is |l - tc d|^2.
-__device__ __forceinline__ bool sphere_test(const RayW &r, float lx, float ly, float lz, float R, float &tin) {
-  const float tc = (lx * r.dx + ly * r.dy + lz * r.dz) * r.inv_dd;
+__device__ __forceinline__ bool sphere_test(const RayW &r, float lx, float ly, float lz, float R, float &tin,
+                                            float &tc) {
+  tc = (lx * r.dx + ly * r.dy + lz * r.dz) * r.inv_dd;
   const float qx = fmaf(-tc, r.dx, lx), qy = fmaf(-tc, r.dy, ly), qz = fmaf(-tc, r.dz, lz);
   const float p2 = qx * qx + qy * qy + qz * qz;
   const float R2 = R * R;
@@ -384,15 +445,21 @@ __device__ __forceinline__ bool sphere_test(const RayW &r, float lx, float ly, f
   return tout >= r.tmin && tin <= r.tmax;
 }
 
-// Part test with the error slack of this ray; returns the eta for its descent.
-__device__ __forceinline__ bool part_cull(const RayW &r, const PartHot &ph, const PartAux &pa, float &tin, float &eta) {
+// Part test.  The part's cube lies in its exact bounding sphere, so a ray that
+// truly meets the cube passes once the FP32 test's own rounding is covered
+// (16 u (|l|_1 + r) of slack).  tref: the reference parameter for the part's
+// descent -- the sphere entry (or the closest approach on a miss), not before
+// tmin.
+__device__ __forceinline__ bool part_cull(const RayW &r, const PartHot &ph, float &tin, float &tref) {
   const float4 s = ph.sphere;
   if (s.w < 0.f) return false;
   const float lx = s.x - r.ox, ly = s.y - r.oy, lz = s.z - r.oz;
   const float ln = fabsf(lx) + fabsf(ly) + fabsf(lz);
-  eta = kU * (16.0f * fmaf(pa.n_ainv, r.onorm, pa.n_binv) + 8.0f * pa.n_ainv * (ln + 2.0f * s.w) + 8.0f);
-  const float Rt = s.w * (1.0f + 9.5367431640625e-7f) + eta * pa.cull_scale + 16.0f * kU * (ln + s.w);
-  return sphere_test(r, lx, ly, lz, Rt, tin);
+  const float Rt = s.w * (1.0f + 9.5367431640625e-7f) + 16.0f * kU * (ln + s.w);
+  float tc;
+  const bool hit = sphere_test(r, lx, ly, lz, Rt, tin, tc);
+  tref = fmaxf(hit ? tin : tc, r.tmin);
+  return hit;
 }
 
 __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
@@ -400,27 +467,47 @@ __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
   if (s.w < 0.f) return false;
   const float lx = s.x - r.ox, ly = s.y - r.oy, lz = s.z - r.oz;
   const float ln = fabsf(lx) + fabsf(ly) + fabsf(lz);
-  const float lm = ln + 1.7320508f * s.w;
-  const float eta = kU * (16.0f * fmaf(c.aux.x, r.onorm, c.aux.y) + 8.0f * c.aux.x * (lm + 2.0f * s.w) + 8.0f);
-  const float Rt = s.w * (1.0f + 9.5367431640625e-7f) + eta * c.aux.z + 16.0f * kU * (2.0f * ln + 3.7320508f * s.w);
-  float tin;
-  return sphere_test(r, lx, ly, lz, Rt, tin);
+  // covers every member test's slack 16 u (|l_m|_1 + r_m), |l_m|_1 <= |l|_1 + sqrt(3) R
+  const float Rt = s.w * (1.0f + 9.5367431640625e-7f) + 48.0f * kU * (2.0f * ln + 3.8f * s.w);
+  float tin, tc;
+  return sphere_test(r, lx, ly, lz, Rt, tin, tc);
 }
 
+// Ray -> part frame (Eq. 3) and descent.  The origin is first moved along the
+// ray to q = o + tref d (tref: sphere entry), and q is mapped relative to the
+// sphere centre c, o' = Ainv (q - c) + c', with c' the FP64-accurate local
+// coordinates of c: all FP32 arithmetic then works on numbers of order one.
+// The descent's parameter is t - tref.  eta bounds the position error of the
+// FP32 local ray over the part (in local units), doubled for safety:
+//   q rounding            u ||Ainv||_inf ||q||_inf
+//   q - c and Ainv (q-c)   5u ||Ainv||_inf ||q - c||_inf, c' rounding u |c'|
+//   mirroring, slabs      u (4 |o'| + 3)
+//   FP32 direction        4u ||Ainv||_inf (|c - q|_1 + r)
 template <bool STATS>
-__device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float eta,
-                                               uint32_t part, const Tables *tab, CertState &st, unsigned int &err,
-                                               Counters &cnt) {
+__device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
+                                               uint32_t part, const Tables *tab, CertState &st, Contenders &con,
+                                               unsigned int &err, Counters &cnt) {
   const float4 a = ph.r0, b = ph.r1, c = ph.r2;
-  const float ox = fmaf(a.x, r.ox, fmaf(a.y, r.oy, fmaf(a.z, r.oz, a.w)));
-  const float oy = fmaf(b.x, r.ox, fmaf(b.y, r.oy, fmaf(b.z, r.oz, b.w)));
-  const float oz = fmaf(c.x, r.ox, fmaf(c.y, r.oy, fmaf(c.z, r.oz, c.w)));
+  const float4 s = ph.sphere;
+  const float qx = fmaf(tref, r.dx, r.ox), qy = fmaf(tref, r.dy, r.oy), qz = fmaf(tref, r.dz, r.oz);
+  const float vx = qx - s.x, vy = qy - s.y, vz = qz - s.z;
+  const float ox = fmaf(a.x, vx, fmaf(a.y, vy, fmaf(a.z, vz, a.w)));
+  const float oy = fmaf(b.x, vx, fmaf(b.y, vy, fmaf(b.z, vz, b.w)));
+  const float oz = fmaf(c.x, vx, fmaf(c.y, vy, fmaf(c.z, vz, c.w)));
   const float dx = fmaf(a.x, r.dx, fmaf(a.y, r.dy, a.z * r.dz));
   const float dy = fmaf(b.x, r.dx, fmaf(b.y, r.dy, b.z * r.dz));
   const float dz = fmaf(c.x, r.dx, fmaf(c.y, r.dy, c.z * r.dz));
+  const float qn = fmaxf(fmaxf(fabsf(qx), fabsf(qy)), fabsf(qz));
+  const float vn = fmaxf(fmaxf(fabsf(vx), fabsf(vy)), fabsf(vz));
+  const float v1 = fabsf(vx) + fabsf(vy) + fabsf(vz);
+  const float on = fmaxf(fmaxf(fabsf(ox), fabsf(oy)), fabsf(oz));
+  const float cn = fmaxf(fmaxf(fabsf(a.w), fabsf(b.w)), fabsf(c.w));
+  const float eta =
+      kU * (2.0f * pa.n_ainv * (qn + 5.0f * vn + 4.0f * (v1 + fabsf(s.w))) + 2.0f * cn + 8.0f * on + 6.0f) * 1.001f;
+  const float tmin_rel = __fsub_rd(r.tmin, tref), tmax_rel = __fsub_ru(r.tmax, tref);
   if (STATS) ++cnt.parts_entered;
-  descend_part<float, CertState, STATS>(pa.nodes, pa.n_nodes, pa.depth, ox, oy, oz, dx, dy, dz, r.tmin, r.tmax,
-                                        eta, part, tab, st, err, cnt);
+  descend_part<float, CertState, STATS>(pa.nodes, pa.n_nodes, pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel,
+                                        eta, tref, part, tab, st, &con, err, cnt);
 }
 
 // Insert (t, p) into the sorted register list (ct, cp); the displaced largest
@@ -445,17 +532,23 @@ template <bool STATS>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
-                              CertState &st, unsigned int &err, Counters &cnt) {
+                              CertState &st, Contenders &con, unsigned int &err, Counters &cnt) {
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
   st.cert1 = 0;
   st.vox1 = kMissVoxel;
+  con.n = 0;
+  con.overflow = false;
   const bool cull = (flags & SVO_TRACE_CULL) != 0;
   const bool sort = (flags & SVO_TRACE_SORT) != 0;
   if (cull && sort) {
+    // Passes are warp-uniform (every lane of the warp calls this function for
+    // one ray each): a lane that needs no further pass takes part with
+    // need = false, so every vote below runs with the full warp mask.
     float last_t = -Num<float>::inf();
     int last_p = -1;
-    for (;;) {
+    bool need = active;
+    while (__any_sync(0xffffffffu, need)) {
       float ct[kCap], ce[kCap];
       int cp[kCap];
 #pragma unroll
@@ -465,63 +558,61 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
         cp[i] = 0x7fffffff;
       }
       float over_t = Num<float>::inf();  // smallest entry that did not fit the list
-      if (STATS && active) ++cnt.passes;
+      if (STATS && need) ++cnt.passes;
       for (int c = 0; c < NC; ++c) {
         const Cluster cc = cl[c];
-        const bool hc = active && cluster_cull(r, cc);
-        if (__ballot_sync(__activemask(), hc) == 0u) continue;  // no lane needs this cluster
-        if (!hc) continue;
-        const uint32_t fc = __float_as_uint(cc.aux.w);
-        const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
-        for (int k = 0; k < count; ++k) {
-          const int p = order[first + k];
-          float tin, eta;
-          if (STATS) ++cnt.parts_tested;
-          if (!part_cull(r, hot[p], aux[p], tin, eta)) continue;
-          if (tin < last_t || (tin == last_t && p <= last_p)) continue;  // visited in an earlier pass
-          float t = tin, e = eta;
-          int pp = p;
-          list_insert(ct, ce, cp, t, e, pp);
-          over_t = fminf(over_t, t);
+        const bool hc = need && cluster_cull(r, cc);
+        if (__ballot_sync(0xffffffffu, hc) == 0u) continue;  // no lane needs this cluster
+        if (hc) {
+          const uint32_t fc = __float_as_uint(cc.aux.w);
+          const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
+          for (int k = 0; k < count; ++k) {
+            const int p = order[first + k];
+            float tin, eta;
+            if (STATS) ++cnt.parts_tested;
+            if (!part_cull(r, hot[p], tin, eta)) continue;
+            if (tin < last_t || (tin == last_t && p <= last_p)) continue;  // visited in an earlier pass
+            float t = tin, e = eta;
+            int pp = p;
+            list_insert(ct, ce, cp, t, e, pp);
+            over_t = fminf(over_t, t);
+          }
         }
       }
-      // visit in order of sphere entry, stop once the best hit is nearer
-      bool stopped = false;
-      while (ct[0] != Num<float>::inf()) {
-        const float tin = ct[0], eta = ce[0];
-        const int p = cp[0];
+      if (need) {
+        // visit in order of sphere entry, stop once the best hit is nearer
+        bool stopped = false;
+        while (ct[0] != Num<float>::inf()) {
+          const float tin = ct[0], eta = ce[0];
+          const int p = cp[0];
 #pragma unroll
-        for (int i = 0; i < kCap - 1; ++i) {
-          ct[i] = ct[i + 1];
-          ce[i] = ce[i + 1];
-          cp[i] = cp[i + 1];
+          for (int i = 0; i < kCap - 1; ++i) {
+            ct[i] = ct[i + 1];
+            ce[i] = ce[i + 1];
+            cp[i] = cp[i + 1];
+          }
+          ct[kCap - 1] = Num<float>::inf();
+          if (tin > prune_bound(st, r.tmax)) {
+            stopped = true;
+            break;
+          }
+          trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, st, con, err, cnt);
+          last_t = tin;
+          last_p = p;
         }
-        ct[kCap - 1] = Num<float>::inf();
-        if (tin > prune_bound(st, r.tmax)) {
-          stopped = true;
-          break;
-        }
-        trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, st, err, cnt);
-        last_t = tin;
-        last_p = p;
+        // another pass only if some candidate did not fit the list and may still matter
+        need = !stopped && over_t < Num<float>::inf() && over_t <= prune_bound(st, r.tmax);
       }
-      if (stopped || !(over_t <= prune_bound(st, r.tmax))) break;
     }
   } else {
     for (int p = 0; p < P; ++p) {
-      float tin, eta;
-      if (STATS) ++cnt.parts_tested;
-      const bool h = active && part_cull(r, hot[p], aux[p], tin, eta);
-      if (cull && !h) continue;
+      float tin, tref = r.tmin;
       if (!active) continue;
-      if (!h) {
-        // plain trace of a part whose sphere is missed: still descend, with an
-        // eta valid for any point of the ray near the part
-        const float4 s = hot[p].sphere;
-        const float ln = fabsf(s.x - r.ox) + fabsf(s.y - r.oy) + fabsf(s.z - r.oz);
-        eta = kU * (16.0f * fmaf(aux[p].n_ainv, r.onorm, aux[p].n_binv) + 8.0f * aux[p].n_ainv * (ln + 2.0f * fabsf(s.w)) + 8.0f);
-      }
-      trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, st, err, cnt);
+      if (STATS) ++cnt.parts_tested;
+      const bool h = part_cull(r, hot[p], tin, tref);
+      if (cull && !h) continue;
+      // the plain trace descends every part, even one whose sphere is missed
+      trace_part_f32<STATS>(r, hot[p], aux[p], tref, (uint32_t)p, tab, st, con, err, cnt);
     }
   }
 }
@@ -540,9 +631,10 @@ __device__ __forceinline__ int find_item(const TraceLaunchT<NI> &L, unsigned lon
 }
 
 __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters &c, uint32_t rays, uint32_t flagged) {
-  unsigned long long v[7] = {rays, flagged, c.parts_tested, c.parts_entered, c.nodes, c.leaves, c.passes};
+  unsigned long long v[10] = {rays, flagged, c.parts_tested, c.parts_entered, c.nodes, c.leaves, c.passes,
+                              c.f_winner, c.f_overlap, c.f_width};
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < 10; ++i) {
     unsigned long long x = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -556,6 +648,9 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
     atomicAdd(&st->nodes_visited, v[4]);
     atomicAdd(&st->leaves_tested, v[5]);
     atomicAdd(&st->passes, v[6]);
+    atomicAdd(&st->flag_winner, v[7]);
+    atomicAdd(&st->flag_overlap, v[8]);
+    atomicAdd(&st->flag_width, v[9]);
   }
 }
 
@@ -567,41 +662,38 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceL
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + kSmemParts);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + kSmemParts);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + kSmemParts / kClusterSize);
-  __shared__ unsigned long long s_tile;
-  build_tables(tab);
-  const PartHot *cur = nullptr;
+  load_tables(tab);
+  if (L.one_scene) {
+    const TraceItem &I0 = L.items[0];
+    for (int i = threadIdx.x; i < I0.n_parts; i += kBlock) {
+      sHot[i] = I0.hot[i];
+      sAux[i] = I0.aux[i];
+      sOrd[i] = I0.order[i];
+    }
+    for (int i = threadIdx.x; i < I0.n_clusters; i += kBlock) sCl[i] = I0.clusters[i];
+  }
+  __syncthreads();  // the only block barrier: warps then take tiles independently
   unsigned int err = 0;
-  Counters cnt = {0, 0, 0, 0, 0};
+  Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   uint32_t n_rays = 0, n_flag = 0;
   const int lane = threadIdx.x & 31;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(L.tile_counter, 1ull);
-    __syncthreads();
-    const unsigned long long tile = s_tile;
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= L.n_tiles) break;
     const int it = find_item(L, tile);
     const TraceItem &I = L.items[it];
     const int P = I.n_parts, NC = I.n_clusters;
-    const bool staged = P <= kSmemParts;
-    if (staged && I.hot != cur) {
-      for (int i = threadIdx.x; i < P; i += kBlock) {
-        sHot[i] = I.hot[i];
-        sAux[i] = I.aux[i];
-        sOrd[i] = I.order[i];
-      }
-      for (int i = threadIdx.x; i < NC; i += kBlock) sCl[i] = I.clusters[i];
-      cur = I.hot;
-      __syncthreads();
-    }
+    const bool staged = L.one_scene != 0;
     const PartHot *hot = staged ? sHot : I.hot;
     const PartAux *aux = staged ? sAux : I.aux;
     const Cluster *cls = staged ? sCl : I.clusters;
     const int32_t *ord = staged ? sOrd : I.order;
     const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)kTile;
 #pragma unroll 1
-    for (int j = 0; j < kRaysPerThread; ++j) {
-      const unsigned long long ray = base + (unsigned long long)(j * kBlock + threadIdx.x);
+    for (int j = 0; j < kRaysPerLane; ++j) {
+      const unsigned long long ray = base + (unsigned long long)(j * 32 + lane);
       bool active = ray < I.n;
       RayW r;
       if (active) {
@@ -619,6 +711,7 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceL
         const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
                             isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dd > 0.f && isfinite(dd);
         r.inv_dd = 1.0f / dd;
+        r.inv_len = rsqrtf(dd);
         r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
         active = finite && (o.w <= d.w);
         if (STATS) ++n_rays;
@@ -627,18 +720,29 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceL
         r.tmin = 0.f;
         r.tmax = -1.f;
         r.inv_dd = 0.f;
+        r.inv_len = 0.f;
         r.onorm = 0.f;
       }
       CertState st;
-      trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, st, err, cnt);
+      Contenders con;
+      trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, st, con, err, cnt);
       bool flagged = false;
       if (ray < I.n) {
         float t = Num<float>::inf();
         uint32_t part = kMissPart;
         unsigned long long vox = kMissVoxel;
         if (st.part1 != kMissPart) {
-          const bool certified = st.cert1 && st.lo2 > st.hi1 && (st.hi1 - st.lo1) <= kTau * st.lo1;
-          flagged = !certified;
+          // the reported t lies in [lo1, hi1]; its error is at most half the width
+          const float scale = fmaxf(st.lo1, aux[st.part1].hdiag * r.inv_len);
+          const bool w_ok = st.cert1 != 0u;
+          const bool o_ok = st.lo2 > st.hi1;
+          const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
+          flagged = !(w_ok && o_ok && t_ok);
+          if (STATS) {
+            cnt.f_winner += w_ok ? 0u : 1u;
+            cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
+            cnt.f_width += (w_ok && o_ok && !t_ok) ? 1u : 0u;
+          }
           t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
           if (!st.cert1) t = st.te1;
           part = st.part1;
@@ -663,10 +767,22 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceL
           basei = __shfl_sync(0xffffffffu, basei, leader);
           if (flagged) {
             const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
-            if (slot < L.fix_capacity)
-              L.fix_list[slot] = ((unsigned long long)it << kRayBits) | ray;
-            else
+            if (slot < L.fix_capacity) {
+              // contenders still in play (lo <= hi_min); none stored = full FP64 retrace
+              unsigned long long nc = 0;
+              if (!con.overflow && slot < L.cand_capacity) {
+                for (int q = 0; q < con.n; ++q) {
+                  if (!(con.lo[q] <= st.hi_min)) continue;
+                  L.fix_cand[slot * kContenders + nc] =
+                      make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull), (uint32_t)(con.vox[q] >> 32),
+                                 __float_as_uint(con.lo[q]));
+                  ++nc;
+                }
+              }
+              L.fix_list[slot] = (nc << 48) | ((unsigned long long)it << kRayBits) | ray;
+            } else {
               err |= kErrFixOverflow;
+            }
           }
         }
       }
@@ -678,56 +794,117 @@ __global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceL
 
 // ------------------------------------------------------------- FP64 pass
 
-__device__ __forceinline__ bool sphere_test64(double ox, double oy, double oz, double dx, double dy, double dz,
-                                              double tmin, double tmax, float4 s, double &tin) {
-  const double lx = s.x - ox, ly = s.y - oy, lz = s.z - oz;
-  const double dd = dx * dx + dy * dy + dz * dz;
-  const double tc = (lx * dx + ly * dy + lz * dz) / dd;
-  const double qx = lx - tc * dx, qy = ly - tc * dy, qz = lz - tc * dz;
-  const double p2 = qx * qx + qy * qy + qz * qz;
-  const double R = (double)s.w * (1.0 + 1e-9) + 1e-12 * (fabs(lx) + fabs(ly) + fabs(lz) + (double)s.w);
-  if (!(p2 <= R * R)) return false;
-  const double half = sqrt((R * R - p2) / dd);
-  tin = tc - half;
-  return tc + half >= tmin && tin <= tmax;
+// Exact closed-box entry of one leaf in FP64 (the definition the oracle
+// follows): ray to the part frame with the FP64 inverse, slab test of the leaf
+// cell's box; a zero direction component keeps the slab only if the origin
+// lies in it.  Returns whether the leaf is hit and its candidate t.
+__device__ __forceinline__ bool leaf_entry64(const double *__restrict__ m, int D, unsigned long long vox, float4 o,
+                                             float4 d, double &t) {
+  const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z;
+  const double lo3[3] = {fma(m[0], ox, fma(m[1], oy, fma(m[2], oz, m[3]))),
+                         fma(m[4], ox, fma(m[5], oy, fma(m[6], oz, m[7]))),
+                         fma(m[8], ox, fma(m[9], oy, fma(m[10], oz, m[11])))};
+  const double ld3[3] = {fma(m[0], dx, fma(m[1], dy, m[2] * dz)), fma(m[4], dx, fma(m[5], dy, m[6] * dz)),
+                         fma(m[8], dx, fma(m[9], dy, m[10] * dz))};
+  const unsigned long long mask = (1ull << D) - 1ull;
+  const double s = Num<double>::pow2neg(D);
+  double t0 = (double)o.w, t1 = (double)d.w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double c = (double)((vox >> (k * D)) & mask);
+    const double blo = c * s, bhi = (c + 1.0) * s;
+    if (ld3[k] == 0.0) {
+      if (lo3[k] < blo || lo3[k] > bhi) return false;
+      continue;
+    }
+    double ta = (blo - lo3[k]) / ld3[k], tb = (bhi - lo3[k]) / ld3[k];
+    if (ta > tb) {
+      const double x = ta;
+      ta = tb;
+      tb = x;
+    }
+    t0 = fmax(t0, ta);
+    t1 = fmin(t1, tb);
+  }
+  t = t0;
+  return t0 <= t1;
 }
 
+// Re-intersects the rays the FP32 pass flagged, in FP64 and without
+// certification: every part whose (conservative FP32) bounding-sphere test
+// passes and whose sphere entry is not beyond the best hit so far is descended
+// with the exact closed-box rule, keeping the lexicographic minimum of
+// (t, part, voxel).  List entries are dealt round-robin over the blocks so
+// that a short list still spreads over the whole GPU.
 template <int NI>
 __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLaunchT<NI> L) {
-  __shared__ Tables tab;
-  build_tables(&tab);
+  __shared__ __align__(16) Tables tab;
+  load_tables(&tab);
   __syncthreads();
   unsigned int err = 0;
-  Counters cnt = {0, 0, 0, 0, 0};
+  Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   const unsigned long long n = min((unsigned long long)*L.fix_count, L.fix_capacity);
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = blockIdx.x + (unsigned long long)gridDim.x * threadIdx.x; i < n; i += stride) {
     const unsigned long long e = L.fix_list[i];
-    const int it = (int)(e >> kRayBits);
+    const int nc = (int)(e >> 48);
+    const int it = (int)((e >> kRayBits) & 0xFFu);
     const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
     const TraceItem &I = L.items[it];
     const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
+    if (nc > 0) {
+      // the FP32 pass narrowed the ray to nc contender leaves: intersect each in FP64
+      ExactState st;
+      st.t = Num<double>::inf();
+      st.part = kMissPart;
+      st.vox = kMissVoxel;
+      for (int q = 0; q < nc; ++q) {
+        const uint4 cv = L.fix_cand[i * kContenders + q];
+        const uint32_t p = cv.x;
+        const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
+        double tq;
+        if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
+      }
+      uint4 hv;
+      hv.x = __float_as_uint((float)st.t);
+      hv.y = st.part;
+      hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
+      hv.w = (uint32_t)(st.vox >> 32);
+      I.hits[ray] = hv;
+      if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_UNCERTAIN | SVO_RAY_FIXED;
+      continue;
+    }
+    RayW r;
+    r.ox = o.x;
+    r.oy = o.y;
+    r.oz = o.z;
+    r.tmin = o.w;
+    r.dx = d.x;
+    r.dy = d.y;
+    r.dz = d.z;
+    r.tmax = d.w;
+    r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
+    r.inv_len = 0.f;
+    r.onorm = 0.f;
     const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z, tmin = o.w, tmax = d.w;
     ExactState st;
     st.t = Num<double>::inf();
     st.part = kMissPart;
     st.vox = kMissVoxel;
     for (int p = 0; p < I.n_parts; ++p) {
-      const float4 s = I.hot[p].sphere;
-      if (s.w < 0.f) continue;
-      double tin;
-      if (!sphere_test64(ox, oy, oz, dx, dy, dz, tmin, tmax, s, tin)) continue;
-      if (tin > st.t) continue;
+      float tin, tref;
+      if (!part_cull(r, I.hot[p], tin, tref)) continue;
+      if ((double)tin > st.t) continue;  // every candidate of p starts after the best hit
       const double *m = I.inv64 + 12 * p;
-      const double lx = m[0] * ox + m[1] * oy + m[2] * oz + m[3];
-      const double ly = m[4] * ox + m[5] * oy + m[6] * oz + m[7];
-      const double lz = m[8] * ox + m[9] * oy + m[10] * oz + m[11];
-      const double ldx = m[0] * dx + m[1] * dy + m[2] * dz;
-      const double ldy = m[4] * dx + m[5] * dy + m[6] * dz;
-      const double ldz = m[8] * dx + m[9] * dy + m[10] * dz;
+      const double lx = fma(m[0], ox, fma(m[1], oy, fma(m[2], oz, m[3])));
+      const double ly = fma(m[4], ox, fma(m[5], oy, fma(m[6], oz, m[7])));
+      const double lz = fma(m[8], ox, fma(m[9], oy, fma(m[10], oz, m[11])));
+      const double ldx = fma(m[0], dx, fma(m[1], dy, m[2] * dz));
+      const double ldy = fma(m[4], dx, fma(m[5], dy, m[6] * dz));
+      const double ldz = fma(m[8], dx, fma(m[9], dy, m[10] * dz));
       const PartAux pa = I.aux[p];
       descend_part<double, ExactState, false>(pa.nodes, pa.n_nodes, pa.depth, lx, ly, lz, ldx, ldy, ldz, tmin, tmax,
-                                              0.0, (uint32_t)p, &tab, st, err, cnt);
+                                              0.0, 0.0, (uint32_t)p, &tab, st, nullptr, err, cnt);
     }
     uint4 hv;
     hv.x = __float_as_uint((float)st.t);
@@ -737,10 +914,8 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     I.hits[ray] = hv;
     if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_UNCERTAIN | SVO_RAY_FIXED;
   }
-  if (L.stats) {
-    // count fixed rays once per launch
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);
-  }
+  // count fixed rays once per launch
+  if (L.stats && blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);
   if (err) atomicOr(L.err, err);
 }
 
@@ -783,6 +958,11 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   dst.fix_list = src.fix_list;
   dst.fix_count = src.fix_count;
   dst.fix_capacity = src.fix_capacity;
+  dst.fix_cand = src.fix_cand;
+  dst.cand_capacity = src.cand_capacity;
+  bool one = true;
+  for (int i = 1; i < src.n_items && i < NI; ++i) one = one && src.items[i].hot == src.items[0].hot;
+  dst.one_scene = one && src.items[0].n_parts <= kSmemParts ? 1 : 0;
   dst.stats = src.stats;
   dst.err = src.err;
 }
@@ -790,6 +970,11 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
 }  // namespace
 
 unsigned long long trace_tile_rays() { return kTile; }
+
+cudaError_t init_trace_tables(cudaStream_t stream) {
+  k_init_tables<<<1, 256, 0, stream>>>();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_trace(const TraceLaunch &L, int n_sm, cudaStream_t stream) {
   if (L.n_items <= 1) {

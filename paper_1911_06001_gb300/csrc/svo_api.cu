@@ -21,6 +21,7 @@
 
 namespace svo {
 unsigned long long trace_tile_rays();
+cudaError_t init_trace_tables(cudaStream_t stream);
 }
 
 using namespace svo;
@@ -62,6 +63,8 @@ struct Slot {
   unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
   unsigned long long *d_fix = nullptr;
   unsigned long long cap = 0;
+  uint4 *d_cand = nullptr;                   // contender leaves of the first cand_cap flagged rays
+  unsigned long long cand_cap = 0;
   TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
   char *d_stage = nullptr;                   // rays | hits | flags staging of trace_rays_host
   unsigned long long stage_rays = 0;
@@ -113,16 +116,29 @@ svo_status get_slot(svo_ctx *ctx, void *stream, unsigned long long need, Slot **
     unsigned long long cap = need < 65536 ? 65536 : need;
     unsigned long long *p = nullptr;
     if (s.d_fix) {
-      // the old list may still be read by queued work on this stream
+      // the old lists may still be read by queued work on this stream
       CK(cudaStreamSynchronize((cudaStream_t)stream));
       CK(cudaFree(s.d_fix));
+      CK(cudaFree(s.d_cand));
       s.d_fix = nullptr;
+      s.d_cand = nullptr;
       s.cap = 0;
+      s.cand_cap = 0;
     }
+    // contenders are stored for up to 1/8 of the rays (flagged rays are far
+    // fewer); later list entries fall back to a full FP64 retrace
+    const unsigned long long ccap = cap / 8 > 65536 ? cap / 8 : (cap < 65536 ? cap : 65536);
+    uint4 *c = nullptr;
     cudaError_t e = cudaMalloc(&p, cap * sizeof(unsigned long long));
-    if (e != cudaSuccess) return fail(SVO_ERR_OOM, "scratch for %llu rays: %s", cap, cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaMalloc(&c, ccap * kContenders * sizeof(uint4));
+    if (e != cudaSuccess) {
+      if (p) cudaFree(p);
+      return fail(SVO_ERR_OOM, "scratch for %llu rays: %s", cap, cudaGetErrorString(e));
+    }
     s.d_fix = p;
     s.cap = cap;
+    s.d_cand = c;
+    s.cand_cap = ccap;
   }
   *out = &s;
   return SVO_OK;
@@ -154,6 +170,8 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
   L.fix_list = slot->d_fix;
   L.fix_capacity = slot->cap;
+  L.fix_cand = slot->d_cand;
+  L.cand_capacity = slot->cand_cap;
   L.err = ctx->d_err;
   CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
   CK(launch_trace(L, ctx->n_sm, st));
@@ -203,6 +221,8 @@ svo_status svo_ctx_create(int32_t device, svo_ctx **out) {
   cudaError_t e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = init_trace_tables(nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     if (c->d_err) cudaFree(c->d_err);
     delete c;
@@ -227,6 +247,7 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
   for (auto &kv : ctx->slots) {
     if (kv.second.d_counters) cudaFree(kv.second.d_counters);
     if (kv.second.d_fix) cudaFree(kv.second.d_fix);
+    if (kv.second.d_cand) cudaFree(kv.second.d_cand);
     if (kv.second.d_stage) cudaFree(kv.second.d_stage);
     delete kv.second.pending;
   }

@@ -15,6 +15,7 @@ constexpr int kMaxParts = SVO_MAX_PARTS;
 constexpr int kClusterSize = 8;                 // parts per sphere-hierarchy cluster
 constexpr int kMaxClusters = kMaxParts / kClusterSize;
 constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
+constexpr int kContenders = 8;                  // contender leaves kept per flagged ray
 
 // Device error word bits (svo_check_device reports them).
 constexpr unsigned int kErrNodeIndex = 1u;      // a child index fell outside the node array
@@ -32,8 +33,10 @@ struct PartStatic {
 };
 
 // Per-frame FP32 data of a part used by the trace kernel (64 B, staged in
-// shared memory).  rows: world->local [Ainv | binv]; sphere: conservative
-// bounding sphere in world space.
+// shared memory).  rows .xyz: the FP32 world->local matrix Ainv; rows .w: the
+// local coordinates of the FP32 sphere centre (computed in FP64), so that a
+// world point q maps to Ainv (q - c) + rows.w with only small numbers
+// cancelling; sphere: conservative bounding sphere (c, r) in world space.
 struct PartHot {
   float4 r0, r1, r2;
   float4 sphere;
@@ -45,15 +48,14 @@ struct PartAux {
   uint32_t n_nodes;
   int32_t depth;
   float n_ainv;      // upper bound of ||Ainv||_inf (max abs row sum of the FP32 rows)
-  float n_binv;      // upper bound of ||binv||_inf
-  float cull_scale;  // upper bound of 2*sqrt(3)*||A||_F (local -> world length)
-  uint32_t pad;
+  float hdiag;       // world length of a leaf's diagonal, |A (1,1,1)| 2^-depth
+  float spare0, spare1;
 };
 
 // Cluster of up to kClusterSize parts (consecutive in `order`).
 struct Cluster {
   float4 sphere;  // encloses the member spheres
-  float4 aux;     // max n_ainv, max n_binv, max cull_scale, bits: first | count << 16
+  float4 aux;     // .x max n_ainv of the members, .w bits: first | count << 16
 };
 
 // One item of a trace launch (by value in the kernel parameters).
@@ -78,9 +80,11 @@ struct TraceLaunch {
   uint32_t flags;
   unsigned long long n_tiles;
   unsigned long long *tile_counter;   // zeroed before the launch
-  unsigned long long *fix_list;       // (item << 40) | ray, capacity fix_capacity
+  unsigned long long *fix_list;       // (count << 48) | (item << 40) | ray, capacity fix_capacity
   unsigned int *fix_count;            // zeroed before the launch
   unsigned long long fix_capacity;
+  uint4 *fix_cand;                    // kContenders entries per list slot < cand_capacity
+  unsigned long long cand_capacity;
   svo_trace_stats *stats;
   unsigned int *err;
 };

@@ -86,7 +86,7 @@ def compare(scene, local, rays, gpu, ora, allow_flagged_mismatch=0):
         "flagged_id_mismatch": int(flag_id_bad.sum()),
         "flagged_t_mismatch": int(flag_t_bad.sum()),
         "fp64_ties": int(fp64_tie.sum()),
-        "max_rel_t_err": float(np.max(np.where(hit_o, np.abs(t_g - t_o) / np.maximum(np.abs(t_o), h), 0.0)))
+        "max_rel_t_err": float(np.max(np.abs(t_g[hit_o] - t_o[hit_o]) / np.maximum(np.abs(t_o[hit_o]), h[hit_o])))
         if hit_o.any() else 0.0,
     }
     if fixed.any():
