@@ -63,6 +63,9 @@ constexpr float kTau = 7.62939453125e-6f;      // 2^-17
 constexpr int kCap = 8;                         // candidate parts per pass
 constexpr int kSmemParts = 256;                 // parts staged in shared memory
 constexpr int kBlock = 128;
+#ifndef SVO_TRACE_MIN_BLOCKS
+#define SVO_TRACE_MIN_BLOCKS 1  // resident blocks per SM the register allocation must allow
+#endif
 constexpr int kRaysPerLane = 4;                 // rays per lane per warp tile
 constexpr int kTile = 32 * kRaysPerLane;        // rays per warp tile
 constexpr unsigned long long kRayBits = 40;
@@ -655,7 +658,7 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 }
 
 template <int NI, bool STATS>
-__global__ void __launch_bounds__(kBlock) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+__global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tables *tab = reinterpret_cast<Tables *>(smem);
   PartHot *sHot = reinterpret_cast<PartHot *>(smem + ((sizeof(Tables) + 15) & ~size_t(15)));
