@@ -60,6 +60,7 @@ typedef int32_t svo_status;
 /* Limits. */
 #define SVO_MAX_DEPTH 16        /* octree depth of an asset (leaf level) */
 #define SVO_MAX_PARTS 1024      /* parts per scene */
+#define SVO_NOALLOC_MAX_RAYS 262144 /* rays per trace_rays_noalloc call (size of its fixed scratch) */
 
 /* trace flags (bitmask).  With none set the call is the plain trace: every
  * part in index order, no sphere culling, no cross-part early exit. */
@@ -223,6 +224,23 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
  * exceeds the largest n traced so far on this stream. */
 svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n, svo_hit *hits_host,
                            uint32_t *ray_flags_host, uint32_t flags, void *stream);
+
+/* trace_rays for callers that cannot allocate device memory -- for example a
+ * frame loop with a hard deadline, where cudaMalloc may synchronise the
+ * device, or a host application whose own allocator owns all device memory.
+ * (The paper has no counterpart; this is a deployment variant.)  Same
+ * arguments and results as trace_rays without `stats`; SVO_TRACE_STATS and
+ * SVO_TRACE_DEFER_FIX are rejected (SVO_ERR_ARG).  It never calls cudaMalloc
+ * or cudaFree: its scratch (about 6.3 MB) is a static device array inside the
+ * library that every GPU loading the library holds until the process exits.
+ * n above SVO_NOALLOC_MAX_RAYS returns SVO_ERR_LIMIT.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array: the
+ * counters are cleared on `stream` at every call, and two calls whose work
+ * overlaps on the GPU (other streams or host threads) race -- serialise
+ * them. */
+svo_status trace_rays_noalloc(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits,
+                              uint32_t *ray_flags, uint32_t flags, void *stream);
 
 /* Run the FP64 re-intersection pass left pending by the last trace_rays /
  * trace_batch issued on `stream` with SVO_TRACE_FP64_FIX | SVO_TRACE_DEFER_FIX

@@ -27,6 +27,7 @@ RAY_FIXED = 2
 
 MAX_DEPTH = 16
 MAX_PARTS = 1024
+NOALLOC_MAX_RAYS = 262144
 
 # every symbol include/svoanim.h declares
 EXPORTS = [
@@ -34,7 +35,7 @@ EXPORTS = [
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
-    "trace_rays_host",
+    "trace_rays_host", "trace_rays_noalloc",
 ]
 
 
@@ -94,6 +95,7 @@ def load(path: str | None = None):
         "trace_batch": ([vp, C.POINTER(SvoBatchItem), i32, u32, vp, vp], i32),
         "trace_fix_pending": ([vp, vp], i32),
         "trace_rays_host": ([vp, vp, u64, vp, vp, u32, vp], i32),
+        "trace_rays_noalloc": ([vp, vp, u64, vp, vp, u32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

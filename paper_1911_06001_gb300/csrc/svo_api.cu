@@ -188,6 +188,18 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
 
 }  // namespace
 
+// Accessors for trace_rays_noalloc (svo_noalloc.cu), which keeps its scratch
+// in a static device array of its own translation unit.
+namespace svo {
+int scene_device(const svo_scene *s) { return s->ctx->device; }
+TraceItem scene_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *flags) {
+  return make_item(s, rays, n, hits, flags);
+}
+unsigned int *scene_err_word(const svo_scene *s) { return s->ctx->d_err; }
+int scene_sm_count(const svo_scene *s) { return s->ctx->n_sm; }
+svo_status set_last_error(svo_status code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace svo
+
 extern "C" {
 
 const char *svo_last_error(void) { return g_last_error.c_str(); }

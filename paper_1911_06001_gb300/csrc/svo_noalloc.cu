@@ -1,0 +1,124 @@
+// svo_noalloc.cu -- trace_rays for callers that cannot allocate device memory.
+//
+// trace_rays keeps its scratch (the tile counter, the list of flagged rays and
+// their contender leaves) in per-stream buffers that it grows with cudaMalloc
+// the first time a larger ray count arrives.  Some callers cannot let that
+// happen: a frame loop with a hard deadline, where cudaMalloc may synchronise
+// the whole device, or a host application whose own allocator owns all device
+// memory and forbids other allocations.  trace_rays_noalloc runs the same
+// trace and FP64 kernels on a fixed scratch area that lives in this file as a
+// static __device__ array: the library never calls cudaMalloc, cudaFree or an
+// allocating library routine on this path.
+//
+// The array is part of the loaded module, so every GPU that loads the library
+// holds it (kNoallocScratchBytes, about 6.3 MB) until the process exits.  All
+// calls share it and it keeps the previous call's contents; the counters that
+// must start at zero are cleared on `stream` at the start of every call.  Two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads) therefore race on the array and must be serialised by the caller.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "svo_internal.h"
+
+namespace svo {
+unsigned long long trace_tile_rays();
+}
+
+using namespace svo;
+
+namespace {
+
+constexpr unsigned long long kNoallocMaxRays = SVO_NOALLOC_MAX_RAYS;
+constexpr unsigned long long kCounterBytes = 256;
+constexpr unsigned long long kFixBytes = kNoallocMaxRays * sizeof(unsigned long long);
+constexpr unsigned long long kCandRays = kNoallocMaxRays / 8;
+constexpr unsigned long long kCandBytes = kCandRays * kContenders * sizeof(uint4);
+constexpr unsigned long long kNoallocScratchBytes = kCounterBytes + kFixBytes + kCandBytes;
+
+// The shared scratch: [counters | flagged-ray list | contender leaves].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  In host code the symbol itself is only a host-side stand-in, so
+// the kernels must be given this address.
+cudaError_t scratch_address(int device, unsigned char **out) {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_scratch_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[device] = p;
+  }
+  *out = static_cast<unsigned char *>(g_scratch_ptr[device]);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// The scene's layout is private to svo_api.cu; these accessors live there.
+namespace svo {
+int scene_device(const svo_scene *s);
+TraceItem scene_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *flags);
+unsigned int *scene_err_word(const svo_scene *s);
+int scene_sm_count(const svo_scene *s);
+svo_status set_last_error(svo_status code, const char *msg);
+}
+
+extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits,
+                                         uint32_t *ray_flags, uint32_t flags, void *stream) {
+  if (!s) return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: scene is NULL");
+  if (n == 0) return SVO_OK;
+  if (!rays || !hits) return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: rays/hits is NULL");
+  if (n > kNoallocMaxRays) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "trace_rays_noalloc: %llu rays exceed the fixed scratch limit of %llu rays",
+             (unsigned long long)n, kNoallocMaxRays);
+    return set_last_error(SVO_ERR_LIMIT, buf);
+  }
+  if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
+    return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: rays and hits must be 16-byte aligned");
+  if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX))
+    return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: STATS and DEFER_FIX are not supported");
+  const int dev = scene_device(s);
+  if (dev < 0 || dev >= kMaxDevices) return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: bad device");
+  cudaError_t e = cudaSetDevice(dev);
+  unsigned char *base = nullptr;
+  if (e == cudaSuccess) e = scratch_address(dev, &base);
+  if (e != cudaSuccess) {
+    std::string m = std::string("trace_rays_noalloc: ") + cudaGetErrorString(e);
+    return set_last_error(SVO_ERR_CUDA, m.c_str());
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  TraceLaunch launch;  // on the stack: no host heap either
+  TraceLaunch *L = &launch;
+  L->items[0] = scene_item(s, rays, n, hits, ray_flags);
+  L->n_items = 1;
+  L->flags = flags;
+  L->stats = nullptr;
+  const unsigned long long tile = trace_tile_rays();
+  L->n_tiles = (n + tile - 1) / tile;
+  L->tile_counter = reinterpret_cast<unsigned long long *>(base);
+  L->fix_count = reinterpret_cast<unsigned int *>(base + sizeof(unsigned long long));
+  L->fix_list = reinterpret_cast<unsigned long long *>(base + kCounterBytes);
+  L->fix_capacity = kNoallocMaxRays;
+  L->fix_cand = reinterpret_cast<uint4 *>(base + kCounterBytes + kFixBytes);
+  L->cand_capacity = kCandRays;
+  L->err = scene_err_word(s);
+  // clear what the kernels expect at zero: the tile counter and the list count
+  e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_trace(*L, scene_sm_count(s), st);
+  if (e == cudaSuccess && (flags & SVO_TRACE_FP64_FIX)) e = launch_fix(*L, scene_sm_count(s), st);
+  if (e != cudaSuccess) {
+    std::string m = std::string("trace_rays_noalloc: ") + cudaGetErrorString(e);
+    return set_last_error(SVO_ERR_CUDA, m.c_str());
+  }
+  return SVO_OK;
+}
