@@ -167,8 +167,10 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
                         svo_scene **out);
 svo_status scene_destroy(svo_scene *scene);
 /* Set every part's local pose (host, n_parts*12 doubles, parent <- part).
- * Async: the array is copied to pinned staging before return, then to the
- * device on `stream`.  SVO_ERR_NAN if any entry is NaN/inf. */
+ * The array is copied before return.  Scenes of up to 256 parts pass the
+ * poses to the device inside the next scene_refit launch (kernel
+ * parameters, no separate copy); larger scenes copy them to the device on
+ * `stream` through pinned staging.  SVO_ERR_NAN if any entry is NaN/inf. */
 svo_status scene_set_transforms(svo_scene *scene, const double *local_3x4, void *stream);
 /* Same from a device array (n_parts*12 doubles); no check for NaN. */
 svo_status scene_set_transforms_device(svo_scene *scene, const double *local_3x4_dev, void *stream);

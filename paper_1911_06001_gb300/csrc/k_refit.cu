@@ -26,7 +26,12 @@ namespace svo {
 
 namespace {
 
-constexpr int kRefitThreads = 256;
+constexpr int kRefitThreads = 256;  // block size for large scenes; one warp for <= 32 parts
+
+// Poses passed by value in the kernel parameters (no host-to-device copy).
+struct InlinePoses {
+  double local[kInlinePoseParts * 12];
+};
 
 __device__ __forceinline__ void compose_affine(const double *p, const double *q, double *out) {
 #pragma unroll
@@ -51,19 +56,26 @@ __device__ __forceinline__ unsigned int spread10(unsigned int v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
+template <bool INLINE>
+__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses poses) {
   const int P = a.n_parts;
   const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
   __shared__ unsigned long long s_key[kMaxParts];
   __shared__ float s_red[6][kRefitThreads];
+  if (INLINE) {
+    // keep the device copy of the local poses in step with what is composed
+    for (int k = tid; k < P * 12; k += nthr) const_cast<double *>(a.local)[k] = poses.local[k];
+  }
+  const double *local = INLINE ? poses.local : a.local;
 
   // 1. compose, level by level (parents are on earlier levels)
   for (int L = 0; L < a.n_levels; ++L) {
     const int b = a.level_start[L], e = a.level_start[L + 1];
-    for (int j = b + tid; j < e; j += kRefitThreads) {
+    for (int j = b + tid; j < e; j += nthr) {
       const int i = a.level_order[j];
       const int p = a.stat[i].parent;
-      const double *Li = a.local + 12 * i;
+      const double *Li = local + 12 * i;
       double *Wi = a.world + 12 * i;
       if (p < 0) {
 #pragma unroll
@@ -85,7 +97,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
 
   // 2-4. per part: invert, FP32 rows, norms, sphere
   float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  for (int i = tid; i < P; i += kRefitThreads) {
+  for (int i = tid; i < P; i += nthr) {
     double m[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) m[k] = a.world[12 * i + k];
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     s_red[3 + k][tid] = mx[k];
   }
   __syncthreads();
-  for (int w = kRefitThreads / 2; w > 0; w >>= 1) {
+  for (int w = nthr / 2; w > 0; w >>= 1) {
     if (tid < w) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -203,7 +215,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
   const float ex = fmaxf(s_red[3][0] - bx0, 1e-30f), ey = fmaxf(s_red[4][0] - by0, 1e-30f),
               ez = fmaxf(s_red[5][0] - bz0, 1e-30f);
   // 5. Morton keys and a rank sort (P <= kMaxParts)
-  for (int i = tid; i < P; i += kRefitThreads) {
+  for (int i = tid; i < P; i += nthr) {
     const float4 s = a.hot[i].sphere;
     const unsigned int qx = (unsigned int)fminf(fmaxf((s.x - bx0) / ex * 1023.0f, 0.0f), 1023.0f);
     const unsigned int qy = (unsigned int)fminf(fmaxf((s.y - by0) / ey * 1023.0f, 0.0f), 1023.0f);
@@ -212,14 +224,14 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
     s_key[i] = ((unsigned long long)mc << 11) | (unsigned long long)i;
   }
   __syncthreads();
-  for (int i = tid; i < P; i += kRefitThreads) {
+  for (int i = tid; i < P; i += nthr) {
     const unsigned long long k = s_key[i];
     int rank = 0;
     for (int j = 0; j < P; ++j) rank += (s_key[j] < k) ? 1 : 0;
     a.order[rank] = i;
   }
   __syncthreads();
-  for (int cidx = tid; cidx < a.n_clusters; cidx += kRefitThreads) {
+  for (int cidx = tid; cidx < a.n_clusters; cidx += nthr) {
     const int first = cidx * kClusterSize;
     const int cnt = min(kClusterSize, P - first);
     double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
@@ -261,8 +273,16 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a) {
 
 }  // namespace
 
-cudaError_t launch_refit(const RefitArgs &a, cudaStream_t stream) {
-  k_refit<<<1, kRefitThreads, 0, stream>>>(a);
+cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
+  const int threads = a.n_parts <= 32 ? 32 : kRefitThreads;
+  if (host_local && a.n_parts <= kInlinePoseParts) {
+    InlinePoses p;
+    for (int k = 0; k < a.n_parts * 12; ++k) p.local[k] = host_local[k];
+    k_refit<true><<<1, threads, 0, stream>>>(a, p);
+  } else {
+    static const InlinePoses none = {};
+    k_refit<false><<<1, threads, 0, stream>>>(a, none);
+  }
   return cudaGetLastError();
 }
 

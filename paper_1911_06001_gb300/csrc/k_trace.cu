@@ -34,6 +34,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "svo_internal.h"
 
@@ -53,7 +54,8 @@ struct TraceLaunchT {
   unsigned long long cand_capacity;
   svo_trace_stats *stats;
   unsigned int *err;
-  int32_t one_scene;  // every item traces the same scene: stage its tables in shared memory
+  int32_t one_scene;     // every item traces the same scene: stage its tables in shared memory
+  int32_t stack_levels;  // traversal stack levels per thread (max asset depth - 1)
 };
 
 namespace {
@@ -74,6 +76,7 @@ struct Tables {
   uint8_t q[8][6][256];  // [mirror][perm][true child mask] -> mask in visiting order
   uint8_t k[8][6][8];    // [mirror][perm][q] -> true octant
 };
+constexpr size_t kTablesBytes = (sizeof(Tables) + 15) & ~size_t(15);
 
 __device__ __forceinline__ void perm_axes(int p, int &a0, int &a1, int &a2) {
   // p = 2*rank_x + (rank_y > rank_z)
@@ -173,6 +176,57 @@ struct ExactState {
   unsigned long long vox;
 };
 
+// Exact closed-box entry of one leaf in FP64 (the definition the oracle
+// follows): ray to the part frame with the FP64 inverse, slab test of the leaf
+// cell's box; a zero direction component keeps the slab only if the origin
+// lies in it.  Returns whether the leaf is hit and its candidate t.
+__device__ __forceinline__ bool leaf_entry64(const double *__restrict__ m, int D, unsigned long long vox, float4 o,
+                                             float4 d, double &t) {
+  const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z;
+  const double lo3[3] = {fma(m[0], ox, fma(m[1], oy, fma(m[2], oz, m[3]))),
+                         fma(m[4], ox, fma(m[5], oy, fma(m[6], oz, m[7]))),
+                         fma(m[8], ox, fma(m[9], oy, fma(m[10], oz, m[11])))};
+  const double ld3[3] = {fma(m[0], dx, fma(m[1], dy, m[2] * dz)), fma(m[4], dx, fma(m[5], dy, m[6] * dz)),
+                         fma(m[8], dx, fma(m[9], dy, m[10] * dz))};
+  const unsigned long long mask = (1ull << D) - 1ull;
+  const double s = Num<double>::pow2neg(D);
+  double t0 = (double)o.w, t1 = (double)d.w;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double c = (double)((vox >> (k * D)) & mask);
+    const double blo = c * s, bhi = (c + 1.0) * s;
+    if (ld3[k] == 0.0) {
+      if (lo3[k] < blo || lo3[k] > bhi) return false;
+      continue;
+    }
+    double ta = (blo - lo3[k]) / ld3[k], tb = (bhi - lo3[k]) / ld3[k];
+    if (ta > tb) {
+      const double x = ta;
+      ta = tb;
+      tb = x;
+    }
+    t0 = fmax(t0, ta);
+    t1 = fmin(t1, tb);
+  }
+  t = t0;
+  return t0 <= t1;
+}
+
+// The FP64 pass for a ray whose contender list overflowed: the FP32 descent
+// with inflated boxes (as in the certified pass, so no leaf the FP64 rule could
+// hit is skipped), each leaf reached decided by leaf_entry64, and the
+// lexicographic minimum kept in FP64.  Same result as an FP64 descent, at FP32
+// speed for the interior nodes.
+struct HybridState {
+  ExactState ex;
+  const double *inv64;  // the part's FP64 world->local rows
+  float4 o, d;          // the ray as given (FP32)
+};
+
+__device__ __forceinline__ float rel_bound(const HybridState &s, float tmax_rel, float tshift) {
+  return fminf(tmax_rel, __fsub_ru(__double2float_ru(s.ex.t), tshift));
+}
+
 // Leaves that may still be the closest hit: every candidate whose entry lower
 // bound lo does not exceed hi_min (the best upper bound of a certainly hit
 // leaf).  The true winner is always among them, so a flagged ray can be
@@ -249,13 +303,16 @@ struct Counters {
 // whose parameter is t - tshift; tmin/tmax are in that shifted parameter;
 // eta: inflation (0 for the exact FP64 search, whose tshift is 0).  State S is
 // CertState (R = float, certified) or ExactState (R = double).
-template <typename R, typename S, bool STATS>
-__device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, uint32_t n_nodes, int D, R ox, R oy,
+template <typename R, typename S, bool STATS, int STRIDE>
+__device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
+                                             int D, R ox, R oy,
                                              R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, R tshift, uint32_t part,
                                              const Tables *__restrict__ tab, S &st, Contenders *con,
                                              unsigned int &err, Counters &cnt) {
   if (n_nodes == 0) return;
-  constexpr bool CERT = sizeof(R) == 4;
+  constexpr bool CERT = std::is_same<S, CertState>::value;
+  constexpr bool HYBRID = std::is_same<S, HybridState>::value;
+  constexpr bool INFLATE = sizeof(R) == 4;  // FP32 descents inflate boxes by eta
   uint32_t mir = 0;
   if (dx < R(0)) {
     ox = R(1) - ox;
@@ -286,7 +343,6 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
   const uint8_t *__restrict__ kt = &tab->k[mir][0][0];
   const uint32_t side = 1u << D;
 
-  uint2 stk[kMaxDepth];
   int level = 0;
   uint32_t px = 0, py = 0, pz = 0;
   uint2 desc = __ldg(&nodes[0]);
@@ -299,9 +355,9 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
       const R tl = rel_bound(st, tmax, tshift);
       const R Ax = Slab<R>::t(lx - eta, ix, ox, bx), Ay = Slab<R>::t(ly - eta, iy, oy, by), Az = Slab<R>::t(lz - eta, iz, oz, bz);
       const R Bx = Slab<R>::t((lx + h) - eta, ix, ox, bx), By = Slab<R>::t((ly + h) - eta, iy, oy, by), Bz = Slab<R>::t((lz + h) - eta, iz, oz, bz);
-      const R Cx = CERT ? Slab<R>::t((lx + h) + eta, ix, ox, bx) : Bx;
-      const R Cy = CERT ? Slab<R>::t((ly + h) + eta, iy, oy, by) : By;
-      const R Cz = CERT ? Slab<R>::t((lz + h) + eta, iz, oz, bz) : Bz;
+      const R Cx = INFLATE ? Slab<R>::t((lx + h) + eta, ix, ox, bx) : Bx;
+      const R Cy = INFLATE ? Slab<R>::t((ly + h) + eta, iy, oy, by) : By;
+      const R Cz = INFLATE ? Slab<R>::t((lz + h) + eta, iz, oz, bz) : Bz;
       const R Ex = Slab<R>::t((lx + sz) + eta, ix, ox, bx), Ey = Slab<R>::t((ly + sz) + eta, iy, oy, by), Ez = Slab<R>::t((lz + sz) + eta, iz, oz, bz);
       const R T0 = fmax(fmax(Ax, Ay), fmax(Az, tmin));
       const R T1 = fmin(fmin(Ex, Ey), fmin(Ez, tl));
@@ -359,6 +415,9 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
             // back to the ray's own parameter, rounding the bounds outward
             offer(st, *con, __fadd_rd(tshift, lo), cert ? __fadd_ru(tshift, dlo) : Num<R>::inf(), tshift + te, cert,
                   part, vox);
+          } else if constexpr (HYBRID) {
+            double tq;
+            if (leaf_entry64(st.inv64, D, vox, st.o, st.d, tq)) offer(st.ex, tq, part, vox);
           } else {
             offer(st, lo, part, vox);
           }
@@ -368,7 +427,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
       }
       const int q = __ffs(hq) - 1;
       const uint32_t rest = hq & (hq - 1u);
-      stk[level] = make_uint2(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16));
+      stk[level * STRIDE] = make_uint2(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16));
       const uint32_t k = kt[p * 8 + q];
       const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
       if (idx >= n_nodes) {
@@ -388,7 +447,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
       px >>= 1;
       py >>= 1;
       pz >>= 1;
-      const uint2 e = stk[level];
+      const uint2 e = stk[level * STRIDE];
       uint32_t rest = (e.y >> 8) & 0xFFu;
       if (rest == 0u) continue;
       const int q = __ffs(rest) - 1;
@@ -405,7 +464,7 @@ __device__ __forceinline__ void descend_part(const uint2 *__restrict__ nodes, ui
       const R Bsel = ax == 0 ? Slab<R>::t((lx + h) - eta, ix, ox, bx) : (ax == 1 ? Slab<R>::t((ly + h) - eta, iy, oy, by) : Slab<R>::t((lz + h) - eta, iz, oz, bz));
       const R en = fmax(T0, Bsel);
       if (en > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
-      stk[level].y = (e.y & ~0xFF00u) | (rest << 8);
+      stk[level * STRIDE].y = (e.y & ~0xFF00u) | (rest << 8);
       const uint32_t k = kt[p * 8 + q];
       const uint32_t cmask = e.y & 0xFFu;
       const uint32_t idx = e.x + __popc(cmask & ((1u << k) - 1u));
@@ -486,10 +545,10 @@ __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
 //   q - c and Ainv (q-c)   5u ||Ainv||_inf ||q - c||_inf, c' rounding u |c'|
 //   mirroring, slabs      u (4 |o'| + 3)
 //   FP32 direction        4u ||Ainv||_inf (|c - q|_1 + r)
-template <bool STATS>
+template <bool STATS, typename S = CertState, int STRIDE = kBlock>
 __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
-                                               uint32_t part, const Tables *tab, CertState &st, Contenders &con,
-                                               unsigned int &err, Counters &cnt) {
+                                               uint32_t part, const Tables *tab, uint2 *stk, S &st,
+                                               Contenders *con, unsigned int &err, Counters &cnt) {
   const float4 a = ph.r0, b = ph.r1, c = ph.r2;
   const float4 s = ph.sphere;
   const float qx = fmaf(tref, r.dx, r.ox), qy = fmaf(tref, r.dy, r.oy), qz = fmaf(tref, r.dz, r.oz);
@@ -509,8 +568,8 @@ __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph,
       kU * (2.0f * pa.n_ainv * (qn + 5.0f * vn + 4.0f * (v1 + fabsf(s.w))) + 2.0f * cn + 8.0f * on + 6.0f) * 1.001f;
   const float tmin_rel = __fsub_rd(r.tmin, tref), tmax_rel = __fsub_ru(r.tmax, tref);
   if (STATS) ++cnt.parts_entered;
-  descend_part<float, CertState, STATS>(pa.nodes, pa.n_nodes, pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel,
-                                        eta, tref, part, tab, st, &con, err, cnt);
+  descend_part<float, S, STATS, STRIDE>(stk, pa.nodes, pa.n_nodes, pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel,
+                                        tmax_rel, eta, tref, part, tab, st, con, err, cnt);
 }
 
 // Insert (t, p) into the sorted register list (ct, cp); the displaced largest
@@ -535,7 +594,7 @@ template <bool STATS>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
-                              CertState &st, Contenders &con, unsigned int &err, Counters &cnt) {
+                              uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt) {
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
   st.cert1 = 0;
@@ -599,7 +658,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
             stopped = true;
             break;
           }
-          trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, st, con, err, cnt);
+          trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, stk, st, &con, err, cnt);
           last_t = tin;
           last_p = p;
         }
@@ -615,7 +674,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       const bool h = part_cull(r, hot[p], tin, tref);
       if (cull && !h) continue;
       // the plain trace descends every part, even one whose sphere is missed
-      trace_part_f32<STATS>(r, hot[p], aux[p], tref, (uint32_t)p, tab, st, con, err, cnt);
+      trace_part_f32<STATS>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
     }
   }
 }
@@ -660,11 +719,15 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 template <int NI, bool STATS>
 __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
-  PartHot *sHot = reinterpret_cast<PartHot *>(smem + ((sizeof(Tables) + 15) & ~size_t(15)));
-  PartAux *sAux = reinterpret_cast<PartAux *>(sHot + kSmemParts);
-  Cluster *sCl = reinterpret_cast<Cluster *>(sAux + kSmemParts);
-  int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + kSmemParts / kClusterSize);
+  uint2 *sStack = reinterpret_cast<uint2 *>(smem + kTablesBytes) + threadIdx.x;
+  const int sp = L.one_scene ? L.items[0].n_parts : 0;
+  const int sc = L.one_scene ? L.items[0].n_clusters : 0;
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * kBlock * sizeof(uint2));
+  PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
+  Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
+  int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
   load_tables(tab);
   if (L.one_scene) {
     const TraceItem &I0 = L.items[0];
@@ -728,7 +791,7 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
       }
       CertState st;
       Contenders con;
-      trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, st, con, err, cnt);
+      trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
       bool flagged = false;
       if (ray < I.n) {
         float t = Num<float>::inf();
@@ -797,42 +860,6 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
 
 // ------------------------------------------------------------- FP64 pass
 
-// Exact closed-box entry of one leaf in FP64 (the definition the oracle
-// follows): ray to the part frame with the FP64 inverse, slab test of the leaf
-// cell's box; a zero direction component keeps the slab only if the origin
-// lies in it.  Returns whether the leaf is hit and its candidate t.
-__device__ __forceinline__ bool leaf_entry64(const double *__restrict__ m, int D, unsigned long long vox, float4 o,
-                                             float4 d, double &t) {
-  const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z;
-  const double lo3[3] = {fma(m[0], ox, fma(m[1], oy, fma(m[2], oz, m[3]))),
-                         fma(m[4], ox, fma(m[5], oy, fma(m[6], oz, m[7]))),
-                         fma(m[8], ox, fma(m[9], oy, fma(m[10], oz, m[11])))};
-  const double ld3[3] = {fma(m[0], dx, fma(m[1], dy, m[2] * dz)), fma(m[4], dx, fma(m[5], dy, m[6] * dz)),
-                         fma(m[8], dx, fma(m[9], dy, m[10] * dz))};
-  const unsigned long long mask = (1ull << D) - 1ull;
-  const double s = Num<double>::pow2neg(D);
-  double t0 = (double)o.w, t1 = (double)d.w;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double c = (double)((vox >> (k * D)) & mask);
-    const double blo = c * s, bhi = (c + 1.0) * s;
-    if (ld3[k] == 0.0) {
-      if (lo3[k] < blo || lo3[k] > bhi) return false;
-      continue;
-    }
-    double ta = (blo - lo3[k]) / ld3[k], tb = (bhi - lo3[k]) / ld3[k];
-    if (ta > tb) {
-      const double x = ta;
-      ta = tb;
-      tb = x;
-    }
-    t0 = fmax(t0, ta);
-    t1 = fmin(t1, tb);
-  }
-  t = t0;
-  return t0 <= t1;
-}
-
 // Re-intersects the rays the FP32 pass flagged, in FP64 and without
 // certification: every part whose (conservative FP32) bounding-sphere test
 // passes and whose sphere entry is not beyond the best hit so far is descended
@@ -889,26 +916,22 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
     r.inv_len = 0.f;
     r.onorm = 0.f;
-    const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z, tmin = o.w, tmax = d.w;
-    ExactState st;
-    st.t = Num<double>::inf();
-    st.part = kMissPart;
-    st.vox = kMissVoxel;
+    HybridState hs;
+    hs.ex.t = Num<double>::inf();
+    hs.ex.part = kMissPart;
+    hs.ex.vox = kMissVoxel;
+    hs.o = o;
+    hs.d = d;
+    uint2 stk_local[kMaxDepth];
     for (int p = 0; p < I.n_parts; ++p) {
       float tin, tref;
       if (!part_cull(r, I.hot[p], tin, tref)) continue;
-      if ((double)tin > st.t) continue;  // every candidate of p starts after the best hit
-      const double *m = I.inv64 + 12 * p;
-      const double lx = fma(m[0], ox, fma(m[1], oy, fma(m[2], oz, m[3])));
-      const double ly = fma(m[4], ox, fma(m[5], oy, fma(m[6], oz, m[7])));
-      const double lz = fma(m[8], ox, fma(m[9], oy, fma(m[10], oz, m[11])));
-      const double ldx = fma(m[0], dx, fma(m[1], dy, m[2] * dz));
-      const double ldy = fma(m[4], dx, fma(m[5], dy, m[6] * dz));
-      const double ldz = fma(m[8], dx, fma(m[9], dy, m[10] * dz));
-      const PartAux pa = I.aux[p];
-      descend_part<double, ExactState, false>(pa.nodes, pa.n_nodes, pa.depth, lx, ly, lz, ldx, ldy, ldz, tmin, tmax,
-                                              0.0, 0.0, (uint32_t)p, &tab, st, nullptr, err, cnt);
+      if (tin > __double2float_ru(hs.ex.t)) continue;  // every candidate of p starts after the best hit
+      hs.inv64 = I.inv64 + 12 * p;
+      trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, &tab, stk_local, hs, nullptr,
+                                            err, cnt);
     }
+    const ExactState &st = hs.ex;
     uint4 hv;
     hv.x = __float_as_uint((float)st.t);
     hv.y = st.part;
@@ -922,14 +945,15 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-size_t trace_smem_bytes() {
-  return ((sizeof(Tables) + 15) & ~size_t(15)) + kSmemParts * (sizeof(PartHot) + sizeof(PartAux)) +
-         (kSmemParts / kClusterSize) * sizeof(Cluster) + kSmemParts * sizeof(int32_t);
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters) {
+  return kTablesBytes + (size_t)stack_levels * kBlock * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
+         clusters * sizeof(Cluster) + parts * sizeof(int32_t);
 }
 
 template <int NI>
 cudaError_t launch_trace_t(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes();
+  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
+                                       L.one_scene ? L.items[0].n_clusters : 0);
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
   auto kern = stats ? k_trace<NI, true> : k_trace<NI, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -966,6 +990,9 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   bool one = true;
   for (int i = 1; i < src.n_items && i < NI; ++i) one = one && src.items[i].hot == src.items[0].hot;
   dst.one_scene = one && src.items[0].n_parts <= kSmemParts ? 1 : 0;
+  int lv = 1;
+  for (int i = 0; i < src.n_items && i < NI; ++i) lv = src.items[i].max_depth - 1 > lv ? src.items[i].max_depth - 1 : lv;
+  dst.stack_levels = lv;
   dst.stats = src.stats;
   dst.err = src.err;
 }

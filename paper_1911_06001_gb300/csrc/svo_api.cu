@@ -85,6 +85,7 @@ struct svo_ctx {
 struct svo_scene {
   svo_ctx *ctx = nullptr;
   int P = 0, L = 0, NC = 0;
+  int max_depth = 1;
   std::vector<int32_t> parent;
   std::vector<svo_handle> asset;
   char *d_mem = nullptr;
@@ -98,6 +99,8 @@ struct svo_scene {
   double *h_stage = nullptr;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
+  std::vector<double> h_local;  // poses set from the host, not yet composed
+  bool host_pending = false;
 };
 
 namespace {
@@ -158,6 +161,8 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.tile_begin = 0;
   it.n_parts = s->P;
   it.n_clusters = s->NC;
+  it.max_depth = s->max_depth;
+  it.pad = 0;
   return it;
 }
 
@@ -404,6 +409,7 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   s->NC = NC;
   s->parent.assign(parent, parent + P);
   s->asset.assign(asset, asset + P);
+  for (int i = 0; i < P; ++i) s->max_depth = stat[i].depth > s->max_depth ? stat[i].depth : s->max_depth;
   cudaError_t e = cudaMalloc(&s->d_mem, total);
   if (e != cudaSuccess) {
     delete s;
@@ -478,6 +484,12 @@ svo_status scene_set_transforms(svo_scene *s, const double *local, void *stream)
   const int n = s->P * 12;
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(local[i])) return fail(SVO_ERR_NAN, "scene_set_transforms: entry %d is not finite", i);
+  if (s->P <= kInlinePoseParts) {
+    // small scenes: the poses ride in the next scene_refit's kernel parameters
+    s->h_local.assign(local, local + n);
+    s->host_pending = true;
+    return ok();
+  }
   CK(cudaSetDevice(s->ctx->device));
   if (s->stage_pending) CK(cudaEventSynchronize(s->ev_stage));  // previous copy out of the staging buffer
   memcpy(s->h_stage, local, n * sizeof(double));
@@ -490,6 +502,7 @@ svo_status scene_set_transforms(svo_scene *s, const double *local, void *stream)
 svo_status scene_set_transforms_device(svo_scene *s, const double *local_dev, void *stream) {
   if (!s || !local_dev) return fail(SVO_ERR_ARG, "scene_set_transforms_device: NULL argument");
   CK(cudaSetDevice(s->ctx->device));
+  s->host_pending = false;
   CK(cudaMemcpyAsync(s->d_local, local_dev, s->P * 12 * sizeof(double), cudaMemcpyDeviceToDevice,
                      (cudaStream_t)stream));
   return ok();
@@ -513,7 +526,8 @@ svo_status scene_refit(svo_scene *s, void *stream) {
   a.order = s->d_order;
   a.n_clusters = s->NC;
   a.err = s->ctx->d_err;
-  CK(launch_refit(a, (cudaStream_t)stream));
+  CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
+  s->host_pending = false;
   return ok();
 }
 

@@ -16,6 +16,7 @@ constexpr int kClusterSize = 8;                 // parts per sphere-hierarchy cl
 constexpr int kMaxClusters = kMaxParts / kClusterSize;
 constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
 constexpr int kContenders = 8;                  // contender leaves kept per flagged ray
+constexpr int kInlinePoseParts = 256;           // poses up to this many parts go by kernel parameter
 
 // Device error word bits (svo_check_device reports them).
 constexpr unsigned int kErrNodeIndex = 1u;      // a child index fell outside the node array
@@ -72,6 +73,8 @@ struct TraceItem {
   unsigned long long tile_begin;
   int32_t n_parts;
   int32_t n_clusters;
+  int32_t max_depth;  // deepest asset among the scene's parts
+  int32_t pad;
 };
 
 struct TraceLaunch {
@@ -109,6 +112,8 @@ struct RefitArgs {
   int32_t n_clusters;
   unsigned int *err;
 };
-cudaError_t launch_refit(const RefitArgs &a, cudaStream_t stream);
+// host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses
+// travel in the kernel parameters instead of through a device copy.
+cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream);
 
 }  // namespace svo
