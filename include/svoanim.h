@@ -70,6 +70,8 @@ typedef int32_t svo_status;
 #define SVO_TRACE_STATS 8u    /* accumulate counters into *stats (device) */
 #define SVO_TRACE_DEFER_FIX 16u /* with FP64_FIX: collect flagged rays but leave the FP64 pass to
                                    trace_fix_pending (lets a caller time the two passes apart) */
+#define SVO_TRACE_ORDER_DIR 32u    /* trace rays in an order grouped by direction (results unchanged) */
+#define SVO_TRACE_ORDER_ORIGIN 64u /* ... grouped by origin cell, then direction (results unchanged) */
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 
 /* per-ray flags written when ray_flags != NULL */
@@ -110,6 +112,15 @@ typedef struct {
   unsigned long long flag_overlap;  /* flagged because another candidate's entry bound reached it */
   unsigned long long flag_width;    /* flagged because the winner's t interval was too wide */
 } svo_trace_stats;
+
+/* A pinhole camera for svo_raygen_pinhole. */
+typedef struct {
+  float eye[3];     /* centre of projection */
+  float target[3];  /* a point on the optical axis */
+  float up[3];      /* approximate up direction */
+  float fov_y_deg;  /* vertical field of view, degrees, in (0, 180) */
+  float tmin, tmax; /* ray segment written into every ray */
+} svo_camera;
 
 /* One entry of a batched trace (trace_batch). */
 typedef struct {
@@ -211,6 +222,9 @@ svo_status scene_read_clusters(svo_scene *scene, int32_t *n_clusters, float *sph
  * cudaMalloc, so call it once at full size before capturing a CUDA graph. */
 svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits, uint32_t *ray_flags,
                       uint32_t flags, svo_trace_stats *stats, void *stream);
+/* (With SVO_TRACE_ORDER_DIR / _ORIGIN the rays are first counting-sorted by a
+ * 16-bit direction / origin-cell key into per-stream scratch, grown like the
+ * FP64 list; hits still land at each ray's own index.) */
 /* Batched trace: every item's rays against its own scene, in one persistent
  * launch whose thread blocks take fixed-size tiles of rays from a device work
  * counter (async).  Items may reference different scenes of the context. */
@@ -243,6 +257,14 @@ svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n,
  * them. */
 svo_status trace_rays_noalloc(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits,
                               uint32_t *ray_flags, uint32_t flags, void *stream);
+
+/* Primary rays of a pinhole camera, one per pixel (async): pixel (i, j) of a
+ * width x height image -> ray j*width + i in `rays` (device, 8 floats per
+ * ray, 16-byte aligned) with unit directions through the pixel centres.  This
+ * prepares inputs on the device (e.g. for served render requests); it is not
+ * part of the paper's method. */
+svo_status svo_raygen_pinhole(svo_ctx *ctx, const svo_camera *cam, uint32_t width, uint32_t height, float *rays,
+                              void *stream);
 
 /* Run the FP64 re-intersection pass left pending by the last trace_rays /
  * trace_batch issued on `stream` with SVO_TRACE_FP64_FIX | SVO_TRACE_DEFER_FIX

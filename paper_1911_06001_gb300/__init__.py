@@ -22,6 +22,8 @@ from ._lib import (  # noqa: F401
     TRACE_CULL,
     TRACE_DEFAULT,
     TRACE_DEFER_FIX,
+    TRACE_ORDER_DIR,
+    TRACE_ORDER_ORIGIN,
     TRACE_FP64_FIX,
     TRACE_SORT,
     TRACE_STATS,
@@ -100,6 +102,18 @@ class Context:
             arr[i] = _lib.SvoBatchItem(sc.h.value, rays.data_ptr(), rays.shape[0], hits.data_ptr(),
                                        0 if rf is None else rf.data_ptr())
         _lib.check(self.lib.trace_batch(self.h, arr, len(items), int(flags), _ptr(stats), _stream_ptr(stream)))
+
+    def raygen(self, eye, target, width: int, height: int, fov_y_deg: float = 60.0, up=(0.0, 1.0, 0.0),
+               tmin: float = 0.0, tmax: float = float("inf"), rays=None, stream=None):
+        """Pinhole primary rays generated on the device: returns a CUDA float32 tensor [W*H, 8]."""
+        import torch
+
+        if rays is None:
+            rays = torch.empty((width * height, RAY_FLOATS), dtype=torch.float32, device=f"cuda:{self.device}")
+        cam = _lib.SvoCamera((C.c_float * 3)(*eye), (C.c_float * 3)(*target), (C.c_float * 3)(*up), fov_y_deg, tmin,
+                             tmax)
+        _lib.check(self.lib.svo_raygen_pinhole(self.h, C.byref(cam), width, height, _ptr(rays), _stream_ptr(stream)))
+        return rays
 
     def fix_pending(self, stream=None) -> None:
         """Run the FP64 pass deferred by a trace issued with TRACE_DEFER_FIX on ``stream``."""

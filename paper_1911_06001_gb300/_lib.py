@@ -20,6 +20,8 @@ TRACE_SORT = 2
 TRACE_FP64_FIX = 4
 TRACE_STATS = 8
 TRACE_DEFER_FIX = 16
+TRACE_ORDER_DIR = 32
+TRACE_ORDER_ORIGIN = 64
 TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
 
 RAY_UNCERTAIN = 1
@@ -35,7 +37,7 @@ EXPORTS = [
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
-    "trace_rays_host", "trace_rays_noalloc",
+    "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole",
 ]
 
 
@@ -47,6 +49,11 @@ class SvoTraceStats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("rays", "flagged", "fixed", "parts_tested", "parts_entered",
                                              "nodes_visited", "leaves_tested", "passes", "flag_winner",
                                              "flag_overlap", "flag_width")]
+
+
+class SvoCamera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_y_deg", C.c_float),
+                ("tmin", C.c_float), ("tmax", C.c_float)]
 
 
 class SvoBatchItem(C.Structure):
@@ -96,6 +103,7 @@ def load(path: str | None = None):
         "trace_fix_pending": ([vp, vp], i32),
         "trace_rays_host": ([vp, vp, u64, vp, vp, u32, vp], i32),
         "trace_rays_noalloc": ([vp, vp, u64, vp, vp, u32, vp], i32),
+        "svo_raygen_pinhole": ([vp, C.POINTER(SvoCamera), u32, u32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -269,6 +269,19 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     cl.aux = make_float4(na, 0.f, 0.f, __uint_as_float((unsigned int)first | ((unsigned int)cnt << 16)));
     a.clusters[cidx] = cl;
   }
+  __syncthreads();
+  if (tid == 0) {
+    // a sphere around all cluster spheres: the frame of origin-based ray ordering
+    const float Cx = 0.5f * (bx0 + s_red[3][0]), Cy = 0.5f * (by0 + s_red[4][0]), Cz = 0.5f * (bz0 + s_red[5][0]);
+    float R = 0.f;
+    for (int c = 0; c < a.n_clusters; ++c) {
+      const float4 s = a.clusters[c].sphere;
+      if (s.w < 0.f) continue;
+      const float dx = s.x - Cx, dy = s.y - Cy, dz = s.z - Cz;
+      R = fmaxf(R, sqrtf(dx * dx + dy * dy + dz * dz) + s.w);
+    }
+    *a.bound = make_float4(Cx, Cy, Cz, R);
+  }
 }
 
 }  // namespace

@@ -759,8 +759,10 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
     const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)kTile;
 #pragma unroll 1
     for (int j = 0; j < kRaysPerLane; ++j) {
-      const unsigned long long ray = base + (unsigned long long)(j * 32 + lane);
-      bool active = ray < I.n;
+      const unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
+      const bool in_range = slot_i < I.n;
+      const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
+      bool active = in_range;
       RayW r;
       if (active) {
         const float4 o = __ldcs(&I.rays[2 * ray]);
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
       Contenders con;
       trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
       bool flagged = false;
-      if (ray < I.n) {
+      if (in_range) {
         float t = Num<float>::inf();
         uint32_t part = kMissPart;
         unsigned long long vox = kMissVoxel;

@@ -68,6 +68,8 @@ struct Slot {
   TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
   char *d_stage = nullptr;                   // rays | hits | flags staging of trace_rays_host
   unsigned long long stage_rays = 0;
+  void *d_order = nullptr;                   // ray-ordering keys, histogram and permutations
+  size_t order_cap = 0;
 };
 
 }  // namespace
@@ -96,6 +98,7 @@ struct svo_scene {
   int32_t *d_order = nullptr;
   PartStatic *d_stat = nullptr;
   int32_t *d_level_order = nullptr, *d_level_start = nullptr;
+  float4 *d_bound = nullptr;
   double *h_stage = nullptr;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
@@ -157,6 +160,7 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.rays = reinterpret_cast<const float4 *>(rays);
   it.hits = reinterpret_cast<uint4 *>(hits);
   it.ray_flags = flags;
+  it.perm = nullptr;
   it.n = n;
   it.tile_begin = 0;
   it.n_parts = s->P;
@@ -166,11 +170,38 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   return it;
 }
 
-svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays, void *stream) {
+// bounds[i]: scene bound of item i (frame of origin-based ray ordering).
+svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays, const float4 *const *bounds,
+                     void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   Slot *slot = nullptr;
   svo_status rc = get_slot(ctx, stream, total_rays, &slot);
   if (rc != SVO_OK) return rc;
+  const int order_mode = (L.flags & SVO_TRACE_ORDER_ORIGIN) ? 2 : ((L.flags & SVO_TRACE_ORDER_DIR) ? 1 : 0);
+  if (order_mode) {
+    size_t need = 0;
+    for (int i = 0; i < L.n_items; ++i) need += (order_scratch_bytes(L.items[i].n) + 255) & ~size_t(255);
+    if (need > slot->order_cap) {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      if (slot->d_order) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaFree(slot->d_order));
+        slot->d_order = nullptr;
+        slot->order_cap = 0;
+      }
+      cudaError_t e = cudaMalloc(&slot->d_order, need);
+      if (e != cudaSuccess) return fail(SVO_ERR_OOM, "ray-order scratch: %s", cudaGetErrorString(e));
+      slot->order_cap = need;
+    }
+    size_t off = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      uint32_t *perm = nullptr;
+      CK(launch_order(reinterpret_cast<const float *>(L.items[i].rays), L.items[i].n, order_mode, bounds[i],
+                      static_cast<char *>(slot->d_order) + off, &perm, ctx->n_sm, st));
+      L.items[i].perm = perm;
+      off += (order_scratch_bytes(L.items[i].n) + 255) & ~size_t(255);
+    }
+  }
   L.tile_counter = slot->d_counters;
   L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
   L.fix_list = slot->d_fix;
@@ -266,6 +297,7 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
     if (kv.second.d_fix) cudaFree(kv.second.d_fix);
     if (kv.second.d_cand) cudaFree(kv.second.d_cand);
     if (kv.second.d_stage) cudaFree(kv.second.d_stage);
+    if (kv.second.d_order) cudaFree(kv.second.d_order);
     delete kv.second.pending;
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -400,7 +432,8 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   size_t off_stat = al(off_order + P * sizeof(int32_t));
   size_t off_lo = al(off_stat + P * sizeof(PartStatic));
   size_t off_ls = al(off_lo + P * sizeof(int32_t));
-  size_t total = al(off_ls + (L + 1) * sizeof(int32_t));
+  size_t off_bd = al(off_ls + (L + 1) * sizeof(int32_t));
+  size_t total = al(off_bd + sizeof(float4));
   CK(cudaSetDevice(ctx->device));
   svo_scene *s = new svo_scene();
   s->ctx = ctx;
@@ -425,6 +458,7 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   s->d_stat = reinterpret_cast<PartStatic *>(s->d_mem + off_stat);
   s->d_level_order = reinterpret_cast<int32_t *>(s->d_mem + off_lo);
   s->d_level_start = reinterpret_cast<int32_t *>(s->d_mem + off_ls);
+  s->d_bound = reinterpret_cast<float4 *>(s->d_mem + off_bd);
   std::vector<double> ident(P * 12, 0.0);
   for (int i = 0; i < P; ++i) ident[12 * i + 0] = ident[12 * i + 5] = ident[12 * i + 10] = 1.0;
   e = cudaMallocHost(&s->h_stage, P * 12 * sizeof(double));
@@ -525,6 +559,7 @@ svo_status scene_refit(svo_scene *s, void *stream) {
   a.clusters = s->d_cl;
   a.order = s->d_order;
   a.n_clusters = s->NC;
+  a.bound = s->d_bound;
   a.err = s->ctx->d_err;
   CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
   s->host_pending = false;
@@ -602,7 +637,8 @@ svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits
   L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
   const unsigned long long tile = trace_tile_rays();
   L->n_tiles = (n + tile - 1) / tile;
-  svo_status rc = run_trace(s->ctx, *L, n, stream);
+  const float4 *bounds[1] = {s->d_bound};
+  svo_status rc = run_trace(s->ctx, *L, n, bounds, stream);
   delete L;
   return rc;
 }
@@ -619,6 +655,7 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
     TraceLaunch *L = new TraceLaunch();
     L->n_items = 0;
     unsigned long long tiles = 0, total = 0;
+    const float4 *bounds[kMaxBatchItems];
     for (int i = 0; i < cnt; ++i) {
       const svo_batch_item &it = items[b + i];
       if (!it.scene) {
@@ -639,13 +676,14 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
       ti.tile_begin = tiles;
       tiles += (it.n + tile - 1) / tile;
       total += it.n;
+      bounds[L->n_items] = it.scene->d_bound;
       L->items[L->n_items++] = ti;
     }
     if (L->n_items > 0) {
       L->flags = flags;
       L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
       L->n_tiles = tiles;
-      svo_status rc = run_trace(ctx, *L, total, stream);
+      svo_status rc = run_trace(ctx, *L, total, bounds, stream);
       if (rc != SVO_OK) {
         delete L;
         return rc;
@@ -690,6 +728,49 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   if (rc != SVO_OK) return rc;
   CK(cudaMemcpyAsync(hits_host, d_hits, n * 16, cudaMemcpyDeviceToHost, st));
   if (d_flags) CK(cudaMemcpyAsync(ray_flags_host, d_flags, n * 4, cudaMemcpyDeviceToHost, st));
+  return ok();
+}
+
+svo_status svo_raygen_pinhole(svo_ctx *ctx, const svo_camera *cam, uint32_t width, uint32_t height, float *rays,
+                              void *stream) {
+  if (!ctx || !cam || !rays) return fail(SVO_ERR_ARG, "svo_raygen_pinhole: NULL argument");
+  if (width == 0 || height == 0) return ok();
+  if (reinterpret_cast<uintptr_t>(rays) & 15) return fail(SVO_ERR_ARG, "svo_raygen_pinhole: rays not 16-byte aligned");
+  if (!(cam->fov_y_deg > 0.f && cam->fov_y_deg < 180.f)) return fail(SVO_ERR_ARG, "svo_raygen_pinhole: fov out of (0,180)");
+  double f[3] = {(double)cam->target[0] - cam->eye[0], (double)cam->target[1] - cam->eye[1],
+                 (double)cam->target[2] - cam->eye[2]};
+  double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  if (!(fl > 0.0)) return fail(SVO_ERR_ARG, "svo_raygen_pinhole: eye == target");
+  for (double &v : f) v /= fl;
+  double up[3] = {cam->up[0], cam->up[1], cam->up[2]};
+  double ul = std::sqrt(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+  if (!(ul > 0.0) || std::fabs((up[0] * f[0] + up[1] * f[1] + up[2] * f[2]) / ul) > 0.999) {
+    up[0] = std::fabs(f[0]) < 0.9 ? 1.0 : 0.0;
+    up[1] = 0.0;
+    up[2] = std::fabs(f[0]) < 0.9 ? 0.0 : 1.0;
+  }
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (double &v : r) v /= rl;
+  double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  RaygenArgs a;
+  for (int k = 0; k < 3; ++k) {
+    a.eye[k] = cam->eye[k];
+    a.f[k] = (float)f[k];
+    a.r[k] = (float)r[k];
+    a.u[k] = (float)u[k];
+  }
+  const double th = std::tan(cam->fov_y_deg * 3.14159265358979323846 / 360.0);
+  a.tan_y = (float)th;
+  a.tan_x = (float)(th * width / height);
+  a.inv_w = 1.0f / (float)width;
+  a.inv_h = 1.0f / (float)height;
+  a.tmin = cam->tmin;
+  a.tmax = cam->tmax;
+  a.width = width;
+  a.height = height;
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_raygen(a, rays, ctx->n_sm, (cudaStream_t)stream));
   return ok();
 }
 

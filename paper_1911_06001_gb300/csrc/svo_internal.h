@@ -69,6 +69,7 @@ struct TraceItem {
   const float4 *rays;   // 2 float4 per ray
   uint4 *hits;          // svo_hit per ray
   uint32_t *ray_flags;  // or nullptr
+  const uint32_t *perm; // visiting order of the rays (nullptr = index order)
   unsigned long long n;
   unsigned long long tile_begin;
   int32_t n_parts;
@@ -96,6 +97,17 @@ struct TraceLaunch {
 cudaError_t launch_trace(const TraceLaunch &L, int n_sm, cudaStream_t stream);
 cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream);
 
+struct RaygenArgs {
+  float eye[3], f[3], r[3], u[3];  // camera origin and unit forward / right / up
+  float tan_x, tan_y, inv_w, inv_h, tmin, tmax;
+  uint32_t width, height;
+};
+cudaError_t launch_raygen(const RaygenArgs &a, float *rays, int n_sm, cudaStream_t stream);
+size_t order_scratch_bytes(unsigned long long n);
+// mode 1: by direction, 2: by origin cell then direction; *perm_out points into scratch.
+cudaError_t launch_order(const float *rays, unsigned long long n, int mode, const float4 *bound, void *scratch,
+                         uint32_t **perm_out, int n_sm, cudaStream_t stream);
+
 struct RefitArgs {
   int32_t n_parts;
   int32_t n_levels;
@@ -110,6 +122,7 @@ struct RefitArgs {
   Cluster *clusters;
   int32_t *order;
   int32_t n_clusters;
+  float4 *bound;  // sphere enclosing every part sphere (ray-ordering frame)
   unsigned int *err;
 };
 // host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses

@@ -318,3 +318,37 @@ def test_articulated_full_size_sampled(ctx):
         assert rep["hits"] > 500
         print("ART full sampled frame", frame, rep, "flag rate full frame",
               float(((res["flags"] & 1) != 0).mean()))
+
+
+def test_ray_ordering_does_not_change_results(ctx, pr1):
+    """Ray ordering only changes which rays share a warp: hits and flags are
+    bit-identical with and without it, for coherent and incoherent rays."""
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    rng = np.random.default_rng(4)
+    cases = [(gs, synthetic.pr1_rays(scene)[:12345]),
+             (gs, synthetic.random_rays(9999, rng, (-3,) * 3, (3,) * 3))]
+    for sc, rays in cases:
+        ref = sc.trace(rays, 7)
+        for extra in (g.TRACE_ORDER_DIR, g.TRACE_ORDER_ORIGIN):
+            res = sc.trace(rays, 7 | extra)
+            for k in ("t", "part", "voxel", "flags"):
+                assert np.array_equal(res[k], ref[k]), (extra, k)
+    ora = so.trace(cases[1][1])
+    compare(scene, gs.local, cases[1][1], gs.trace(cases[1][1], 7 | g.TRACE_ORDER_ORIGIN), ora)
+
+
+def test_raygen_matches_host_pinhole(ctx):
+    import torch
+
+    eye, tgt = (3.0, 2.0, 5.0), (0.2, -0.1, 0.3)
+    for w, h in ((128, 128), (333, 77)):
+        dev = ctx.raygen(eye, tgt, w, h, 60.0)
+        torch.cuda.synchronize()
+        got = dev.cpu().numpy()
+        ref = synthetic.pinhole_rays(eye, tgt, w, h, 60.0)
+        assert got.shape == ref.shape
+        assert np.array_equal(got[:, 0:4], ref[:, 0:4])
+        assert np.max(np.abs(got[:, 4:7] - ref[:, 4:7])) <= 2e-6
+        assert np.all(np.isinf(got[:, 7]))
