@@ -27,4 +27,12 @@ from .scenes import (  # noqa: F401
     ArticulatedFigure,
     articulated_figure,
     random_rays,
+    PoolAsset,
+    asset_pool,
+    BatchedScenes,
+    batched_scenes,
+    ServedScene,
+    RenderRequest,
+    ServingWorld,
+    serving_world,
 )

@@ -456,3 +456,189 @@ def articulated_figure(seed: int | None = None, depth: int = 9) -> ArticulatedFi
     fig = ArticulatedFigure(scene=scene, attach=attach, joint=joint, rest=rest, axis=axis, freq=freq, phase=phase)
     scene.local = fig.pose(0)
     return fig
+
+
+# ------------------------------------------------------ asset pool, BAT, SRV
+
+@dataclass
+class PoolAsset:
+    asset: Asset
+    semi: np.ndarray  # semi-axes in unit-cube units (x, y, z)
+
+
+def asset_pool(depths, per_depth: int = 4, seed: int = 0, thin_from: int = 11) -> list:
+    """Seeded ellipsoid / capsule shells, ``per_depth`` per depth.  Shells are
+    two cells thick, one cell from depth ``thin_from`` on (to bound memory)."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for depth in depths:
+        n = 1 << depth
+        for _ in range(per_depth):
+            ax = rng.uniform(0.15, 0.45, 3) * n
+            thick = 1.0 if depth >= thin_from else 2.0
+            c = np.array([n / 2.0] * 3)
+            if rng.random() < 0.5:
+                cells = ellipsoid_shell(depth, c, ax, thick)
+                semi = ax / n
+            else:
+                rad = min(ax[0], ax[1])
+                hl = max(ax[2] - rad, 0.0)
+                cells = capsule_shell(depth, c, rad, hl, thick)
+                semi = np.array([rad, rad, hl + rad]) / n
+            pool.append(PoolAsset(make_asset(depth, cells), semi))
+    return pool
+
+
+def _random_rotation(rng) -> np.ndarray:
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+@dataclass
+class BatchedScenes:
+    """Scenes of uneven size over a shared asset pool, each with its own rays."""
+
+    pool: list
+    scenes: list  # Scene (assets = the pool's Asset list; part_asset indexes it)
+    rays: list    # float32 [n_s, 8] per scene
+
+
+def batched_scenes(seed: int | None = None, n_scenes: int = 64, parts=(4, 256), depths=range(6, 12),
+                   side=(64, 1024), per_depth: int = 4, thin_from: int = 11) -> BatchedScenes:
+    """Uneven scenes: P log-uniform in ``parts``; per part a random pool asset
+    of a random depth; pose = rotation (uniform) x scale U(0.5, 2) per axis x
+    shear U(-0.1, 0.1) on three off-diagonals, translation in a box of side
+    4 P^(1/3) part widths.  Rays: side log-uniform in ``side`` (side^2 rays),
+    origins uniform in the box, directions uniform on the sphere."""
+    rng = np.random.default_rng(config_seed(2) if seed is None else seed)
+    depths = list(depths)
+    pool = asset_pool(depths, per_depth, seed=int(rng.integers(1 << 31)), thin_from=thin_from)
+    assets = [p.asset for p in pool]
+    scenes, rays = [], []
+    for _ in range(n_scenes):
+        P = int(round(math.exp(rng.uniform(math.log(parts[0]), math.log(parts[1])))))
+        box = 4.0 * P ** (1.0 / 3.0)
+        local = np.zeros((P, 12))
+        part_asset = np.zeros(P, dtype=np.int32)
+        for i in range(P):
+            d = int(rng.integers(len(depths)))
+            part_asset[i] = d * per_depth + int(rng.integers(per_depth))
+            S = np.diag(rng.uniform(0.5, 2.0, 3))
+            H = np.eye(3)
+            H[0, 1], H[0, 2], H[1, 2] = rng.uniform(-0.1, 0.1, 3)
+            A = _random_rotation(rng) @ S @ H
+            t = rng.uniform(-box / 2, box / 2, 3) - A @ np.full(3, 0.5)
+            local[i] = affine12(A, t)
+        scenes.append(Scene("BAT", assets, part_asset, np.full(P, -1, np.int32), local, {"box": box}))
+        s = int(round(math.exp(rng.uniform(math.log(side[0]), math.log(side[1])))))
+        rays.append(random_rays(s * s, rng, (-box / 2,) * 3, (box / 2,) * 3))
+    return BatchedScenes(pool, scenes, rays)
+
+
+@dataclass
+class ServedScene:
+    """One resident scene of the serving workload: a tree of pool assets with
+    joints animated like the articulated figure."""
+
+    scene: Scene
+    attach: np.ndarray
+    joint: np.ndarray
+    rest: np.ndarray
+    axis: np.ndarray
+    radius: float  # rough extent of the figure (camera framing)
+
+    def pose(self, rng: np.random.Generator) -> np.ndarray:
+        """A fresh seeded pose: every joint angle uniform in [-0.5, 0.5] rad."""
+        P = self.scene.n_parts
+        local = np.zeros((P, 12))
+        for i in range(P):
+            th = rng.uniform(-0.5, 0.5) if i > 0 else 0.0
+            A = self.rest[i] @ axis_angle(self.axis[i], th)
+            local[i] = affine12(A, self.attach[i] - A @ self.joint[i])
+        return local
+
+
+@dataclass
+class RenderRequest:
+    scene: int
+    local: np.ndarray
+    eye: np.ndarray
+    target: np.ndarray
+    width: int
+    height: int
+    arrival: float  # seconds from the start of the stream
+
+
+@dataclass
+class ServingWorld:
+    pool: list
+    scenes: list  # ServedScene
+
+    def requests(self, n: int, rate: float, seed: int, resolutions=((256, 256), (512, 512), (1280, 720),
+                                                                     (1920, 1080))) -> list:
+        """Poisson arrivals (exponential gaps of mean 1/rate), a uniformly chosen
+        scene, resolution and camera direction, and a fresh pose per request."""
+        rng = np.random.default_rng(seed)
+        t = 0.0
+        out = []
+        for _ in range(n):
+            t += rng.exponential(1.0 / rate)
+            s = int(rng.integers(len(self.scenes)))
+            sc = self.scenes[s]
+            w, h = resolutions[int(rng.integers(len(resolutions)))]
+            view = rng.standard_normal(3)
+            view /= np.linalg.norm(view)
+            eye = view * sc.radius * 2.2
+            out.append(RenderRequest(s, sc.pose(rng), eye, np.zeros(3), w, h, t))
+        return out
+
+
+def serving_world(seed: int | None = None, n_scenes: int = 32, parts=(16, 128), depths=range(8, 12),
+                  per_depth: int = 4, thin_from: int = 11) -> ServingWorld:
+    """Resident scenes for the serving workload: P uniform in ``parts``, parts
+    drawn from a pool of depths ``depths``; each part hangs from a random
+    earlier part at a point on its surface and swings about a seeded axis."""
+    rng = np.random.default_rng(config_seed(4) if seed is None else seed)
+    depths = list(depths)
+    pool = asset_pool(depths, per_depth, seed=int(rng.integers(1 << 31)), thin_from=thin_from)
+    assets = [p.asset for p in pool]
+    scenes = []
+    c = np.array([0.5, 0.5, 0.5])
+    for _ in range(n_scenes):
+        P = int(rng.integers(parts[0], parts[1] + 1))
+        part_asset = np.array([int(rng.integers(len(pool))) for _ in range(P)], dtype=np.int32)
+        parent = np.array([-1] + [int(rng.integers(max(0, i - 6), i)) for i in range(1, P)], dtype=np.int32)
+        attach = np.zeros((P, 3))
+        joint = np.zeros((P, 3))
+        rest = np.zeros((P, 3, 3))
+        axis = np.zeros((P, 3))
+        level = np.zeros(P, dtype=np.int64)
+        for i in range(P):
+            semi = pool[part_asset[i]].semi
+            a = rng.standard_normal(3)
+            axis[i] = a / np.linalg.norm(a)
+            if i == 0:
+                attach[i] = -c
+                joint[i] = np.zeros(3)
+                rest[i] = np.eye(3)
+                continue
+            p = parent[i]
+            level[i] = level[p] + 1
+            u = rng.standard_normal(3)
+            u /= np.linalg.norm(u)
+            attach[i] = c + u * pool[part_asset[p]].semi
+            joint[i] = c - np.array([0.0, 0.0, semi[2]])
+            rest[i] = _rot_z_to(u)
+        radius = 1.0 + 0.9 * float(level.max() + 1)
+        local0 = np.zeros((P, 12))
+        sc = Scene("SRV", assets, part_asset, parent, local0)
+        served = ServedScene(sc, attach, joint, rest, axis, radius)
+        sc.local = served.pose(np.random.default_rng(0))
+        scenes.append(served)
+    return ServingWorld(pool, scenes)
