@@ -92,6 +92,14 @@ class Context:
     def scene(self, part_assets, parent) -> "Scene":
         return Scene(self, part_assets, parent)
 
+    def set_trace_config(self, block: int = 128, rays_per_lane: int = 4) -> None:
+        _lib.check(self.lib.svo_set_trace_config(self.h, int(block), int(rays_per_lane)))
+
+    def trace_config(self) -> tuple:
+        b, r = C.c_int32(0), C.c_int32(0)
+        _lib.check(self.lib.svo_get_trace_config(self.h, C.byref(b), C.byref(r)))
+        return b.value, r.value
+
     def check_device(self) -> None:
         _lib.check(self.lib.svo_check_device(self.h))
 

@@ -34,6 +34,7 @@ NOALLOC_MAX_RAYS = 262144
 # every symbol include/svoanim.h declares
 EXPORTS = [
     "svo_ctx_create", "svo_ctx_destroy", "svo_last_error", "svo_status_string", "svo_check_device",
+    "svo_set_trace_config", "svo_get_trace_config",
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
@@ -87,6 +88,8 @@ def load(path: str | None = None):
         "svo_last_error": ([], C.c_char_p),
         "svo_status_string": ([i32], C.c_char_p),
         "svo_check_device": ([vp], i32),
+        "svo_set_trace_config": ([vp, i32, i32], i32),
+        "svo_get_trace_config": ([vp, C.POINTER(i32), C.POINTER(i32)], i32),
         "svo_build_host": ([C.POINTER(SvoDesc), C.POINTER(u64), C.POINTER(u64), vp, vp], i32),
         "svo_upload": ([vp, C.POINTER(SvoDesc), C.POINTER(u32)], i32),
         "svo_release": ([vp, u32], i32),

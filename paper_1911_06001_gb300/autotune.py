@@ -1,0 +1,95 @@
+"""Autotuner for the trace launch.
+
+Knobs that change only speed, never results: the trace kernel's block size
+(64 / 128 / 256 threads), the rays each lane takes per warp tile (1 / 2 / 4 /
+8) and the ray order (as given, grouped by direction, grouped by origin cell
+then direction).  ``tune`` times every combination on the caller's rays with
+CUDA events (L2 flushed between repetitions), keeps the fastest, and can
+remember it in a JSON cache under a caller-chosen key (for example the scene
+and ray-batch shape).
+"""
+
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+
+from . import TRACE_DEFAULT, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN, Context
+
+BLOCKS = (64, 128, 256)
+RAYS_PER_LANE = (1, 2, 4, 8)
+ORDERS = {"none": 0, "dir": TRACE_ORDER_DIR, "origin": TRACE_ORDER_ORIGIN}
+_ORDER_BITS = TRACE_ORDER_DIR | TRACE_ORDER_ORIGIN
+
+
+def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> float:
+    import torch
+
+    evs = []
+    for i in range(reps + 1):
+        flush.fill_(i & 0xFF)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        scene.trace(rays, hits, flags=flags)
+        e[1].record()
+        evs.append(e)
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in evs[1:]]))
+
+
+def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, blocks=BLOCKS,
+         rays_per_lane=RAYS_PER_LANE, orders=tuple(ORDERS), cache_path: str | None = None,
+         key: str | None = None) -> dict:
+    """Time every (block, rays_per_lane, order) on ``rays`` (CUDA [n, 8]) traced
+    against ``scene``; apply and return the fastest."""
+    import torch
+
+    if cache_path and key:
+        cached = load(cache_path).get(key)
+        if cached:
+            apply(ctx, cached)
+            return cached
+    hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
+    old = ctx.trace_config()
+    table = []
+    for b, r, o in itertools.product(blocks, rays_per_lane, orders):
+        ctx.set_trace_config(b, r)
+        f = (flags & ~_ORDER_BITS) | ORDERS[o]
+        table.append({"block": b, "rays_per_lane": r, "order": o, "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
+    ctx.set_trace_config(*old)
+    best = min(table, key=lambda x: x["ms"])
+    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 4 and x["order"] == "none"), None)
+    result = dict(best)
+    result["default_ms"] = default["ms"] if default else None
+    result["n_rays"] = int(rays.shape[0])
+    result["table"] = table
+    apply(ctx, result)
+    if cache_path and key:
+        data = load(cache_path)
+        data[key] = result
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(tmp, cache_path)
+    return result
+
+
+def apply(ctx: Context, cfg: dict) -> int:
+    """Set the tuned launch shape on ``ctx``; returns the order flag to OR into trace flags."""
+    ctx.set_trace_config(int(cfg["block"]), int(cfg["rays_per_lane"]))
+    return ORDERS[cfg["order"]]
+
+
+def order_flag(cfg: dict) -> int:
+    return ORDERS[cfg["order"]]
+
+
+def load(cache_path: str) -> dict:
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            return json.load(f)
+    return {}

@@ -56,6 +56,8 @@ struct TraceLaunchT {
   unsigned int *err;
   int32_t one_scene;     // every item traces the same scene: stage its tables in shared memory
   int32_t stack_levels;  // traversal stack levels per thread (max asset depth - 1)
+  int32_t block;         // threads per block of the trace kernel: 64, 128 or 256
+  int32_t rays_per_lane; // rays per lane in a warp's tile (tile = 32 * rays_per_lane rays)
 };
 
 namespace {
@@ -64,12 +66,11 @@ constexpr float kU = 5.9604644775390625e-8f;   // 2^-24, FP32 unit roundoff
 constexpr float kTau = 7.62939453125e-6f;      // 2^-17
 constexpr int kCap = 8;                         // candidate parts per pass
 constexpr int kSmemParts = 256;                 // parts staged in shared memory
-constexpr int kBlock = 128;
+constexpr int kBlock = 128;  // block size of the FP64 pass; the trace kernel takes 64, 128 or 256
 #ifndef SVO_TRACE_MIN_BLOCKS
 #define SVO_TRACE_MIN_BLOCKS 1  // resident blocks per SM the register allocation must allow
 #endif
-constexpr int kRaysPerLane = 4;                 // rays per lane per warp tile
-constexpr int kTile = 32 * kRaysPerLane;        // rays per warp tile
+
 constexpr unsigned long long kRayBits = 40;
 
 struct Tables {
@@ -590,7 +591,7 @@ __device__ __forceinline__ void list_insert(float (&ct)[kCap], float (&ce)[kCap]
   }
 }
 
-template <bool STATS>
+template <bool STATS, int BLOCK>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
@@ -658,7 +659,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
             stopped = true;
             break;
           }
-          trace_part_f32<STATS>(r, hot[p], aux[p], eta, (uint32_t)p, tab, stk, st, &con, err, cnt);
+          trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], eta, (uint32_t)p, tab, stk, st, &con, err, cnt);
           last_t = tin;
           last_p = p;
         }
@@ -674,7 +675,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       const bool h = part_cull(r, hot[p], tin, tref);
       if (cull && !h) continue;
       // the plain trace descends every part, even one whose sphere is missed
-      trace_part_f32<STATS>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
+      trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
     }
   }
 }
@@ -716,27 +717,27 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
   }
 }
 
-template <int NI, bool STATS>
-__global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+template <int NI, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
   uint2 *sStack = reinterpret_cast<uint2 *>(smem + kTablesBytes) + threadIdx.x;
   const int sp = L.one_scene ? L.items[0].n_parts : 0;
   const int sc = L.one_scene ? L.items[0].n_clusters : 0;
-  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * kBlock * sizeof(uint2));
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * BLOCK * sizeof(uint2));
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
   load_tables(tab);
   if (L.one_scene) {
     const TraceItem &I0 = L.items[0];
-    for (int i = threadIdx.x; i < I0.n_parts; i += kBlock) {
+    for (int i = threadIdx.x; i < I0.n_parts; i += BLOCK) {
       sHot[i] = I0.hot[i];
       sAux[i] = I0.aux[i];
       sOrd[i] = I0.order[i];
     }
-    for (int i = threadIdx.x; i < I0.n_clusters; i += kBlock) sCl[i] = I0.clusters[i];
+    for (int i = threadIdx.x; i < I0.n_clusters; i += BLOCK) sCl[i] = I0.clusters[i];
   }
   __syncthreads();  // the only block barrier: warps then take tiles independently
   unsigned int err = 0;
@@ -756,9 +757,10 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
     const PartAux *aux = staged ? sAux : I.aux;
     const Cluster *cls = staged ? sCl : I.clusters;
     const int32_t *ord = staged ? sOrd : I.order;
-    const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)kTile;
+    const int rpl = L.rays_per_lane;
+    const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
 #pragma unroll 1
-    for (int j = 0; j < kRaysPerLane; ++j) {
+    for (int j = 0; j < rpl; ++j) {
       const unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
       const bool in_range = slot_i < I.n;
       const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(kBlock, SVO_TRACE_MIN_BLOCKS) k_trace(const __
       }
       CertState st;
       Contenders con;
-      trace_ray_f32<STATS>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
+      trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
       bool flagged = false;
       if (in_range) {
         float t = Num<float>::inf();
@@ -947,28 +949,37 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-size_t trace_smem_bytes(int stack_levels, int parts, int clusters) {
-  return kTablesBytes + (size_t)stack_levels * kBlock * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block) {
+  return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
          clusters * sizeof(Cluster) + parts * sizeof(int32_t);
+}
+
+template <int NI, int BLOCK>
+cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
+  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
+                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK);
+  const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
+  auto kern = stats ? k_trace<NI, true, BLOCK> : k_trace<NI, false, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  // one warp per tile: no more blocks than the tiles can keep busy
+  unsigned long long grid = (unsigned long long)n_sm * per_sm;
+  const unsigned long long need = (L.n_tiles + BLOCK / 32 - 1) / (BLOCK / 32);
+  if (grid > need) grid = need;
+  if (grid == 0) return cudaSuccess;
+  kern<<<(unsigned int)grid, BLOCK, smem, stream>>>(L);
+  return cudaGetLastError();
 }
 
 template <int NI>
 cudaError_t launch_trace_t(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
-                                       L.one_scene ? L.items[0].n_clusters : 0);
-  const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
-  auto kern = stats ? k_trace<NI, true> : k_trace<NI, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  unsigned long long grid = (unsigned long long)n_sm * per_sm;
-  if (grid > L.n_tiles) grid = L.n_tiles;
-  if (grid == 0) return cudaSuccess;
-  kern<<<(unsigned int)grid, kBlock, smem, stream>>>(L);
-  return cudaGetLastError();
+  if (L.block == 64) return launch_trace_b<NI, 64>(L, n_sm, stream);
+  if (L.block == 256) return launch_trace_b<NI, 256>(L, n_sm, stream);
+  return launch_trace_b<NI, 128>(L, n_sm, stream);
 }
 
 template <int NI>
@@ -997,11 +1008,11 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   dst.stack_levels = lv;
   dst.stats = src.stats;
   dst.err = src.err;
+  dst.block = src.block;
+  dst.rays_per_lane = src.rays_per_lane < 1 ? 1 : src.rays_per_lane;
 }
 
 }  // namespace
-
-unsigned long long trace_tile_rays() { return kTile; }
 
 cudaError_t init_trace_tables(cudaStream_t stream) {
   k_init_tables<<<1, 256, 0, stream>>>();

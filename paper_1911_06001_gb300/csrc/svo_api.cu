@@ -20,7 +20,6 @@
 #include "svo_internal.h"
 
 namespace svo {
-unsigned long long trace_tile_rays();
 cudaError_t init_trace_tables(cudaStream_t stream);
 }
 
@@ -77,6 +76,8 @@ struct Slot {
 struct svo_ctx {
   int device = 0;
   int n_sm = 1;
+  int block = 128;         // trace kernel block size
+  int rays_per_lane = 4;   // warp tile = 32 * rays_per_lane rays
   std::mutex mu;
   std::vector<AssetRec> assets;
   std::unordered_set<svo_scene *> scenes;
@@ -209,6 +210,8 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.fix_cand = slot->d_cand;
   L.cand_capacity = slot->cand_cap;
   L.err = ctx->d_err;
+  L.block = ctx->block;
+  L.rays_per_lane = ctx->rays_per_lane;
   CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
   CK(launch_trace(L, ctx->n_sm, st));
   delete slot->pending;
@@ -233,6 +236,10 @@ TraceItem scene_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits,
 }
 unsigned int *scene_err_word(const svo_scene *s) { return s->ctx->d_err; }
 int scene_sm_count(const svo_scene *s) { return s->ctx->n_sm; }
+void scene_trace_config(const svo_scene *s, int *block, int *rays_per_lane) {
+  *block = s->ctx->block;
+  *rays_per_lane = s->ctx->rays_per_lane;
+}
 svo_status set_last_error(svo_status code, const char *msg) { return fail(code, "%s", msg); }
 }  // namespace svo
 
@@ -302,6 +309,24 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
+  return ok();
+}
+
+svo_status svo_set_trace_config(svo_ctx *ctx, int32_t block, int32_t rays_per_lane) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_set_trace_config: ctx is NULL");
+  if (block != 64 && block != 128 && block != 256)
+    return fail(SVO_ERR_ARG, "svo_set_trace_config: block %d (64, 128 or 256)", block);
+  if (rays_per_lane != 1 && rays_per_lane != 2 && rays_per_lane != 4 && rays_per_lane != 8)
+    return fail(SVO_ERR_ARG, "svo_set_trace_config: rays_per_lane %d (1, 2, 4 or 8)", rays_per_lane);
+  ctx->block = block;
+  ctx->rays_per_lane = rays_per_lane;
+  return ok();
+}
+
+svo_status svo_get_trace_config(svo_ctx *ctx, int32_t *block, int32_t *rays_per_lane) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_get_trace_config: ctx is NULL");
+  if (block) *block = ctx->block;
+  if (rays_per_lane) *rays_per_lane = ctx->rays_per_lane;
   return ok();
 }
 
@@ -635,7 +660,7 @@ svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits
   L->n_items = 1;
   L->flags = flags;
   L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
-  const unsigned long long tile = trace_tile_rays();
+  const unsigned long long tile = 32ull * s->ctx->rays_per_lane;
   L->n_tiles = (n + tile - 1) / tile;
   const float4 *bounds[1] = {s->d_bound};
   svo_status rc = run_trace(s->ctx, *L, n, bounds, stream);
@@ -649,7 +674,7 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
   if (n_items < 0) return fail(SVO_ERR_ARG, "trace_batch: n_items < 0");
   if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_batch: STATS without stats buffer");
   CK(cudaSetDevice(ctx->device));
-  const unsigned long long tile = trace_tile_rays();
+  const unsigned long long tile = 32ull * ctx->rays_per_lane;
   for (int b = 0; b < n_items; b += kMaxBatchItems) {
     const int cnt = (n_items - b) < kMaxBatchItems ? (n_items - b) : kMaxBatchItems;
     TraceLaunch *L = new TraceLaunch();

@@ -91,6 +91,8 @@ struct TraceLaunch {
   unsigned long long cand_capacity;
   svo_trace_stats *stats;
   unsigned int *err;
+  int32_t block;          // trace kernel block size: 64, 128 or 256
+  int32_t rays_per_lane;  // warp tile = 32 * rays_per_lane rays
 };
 
 // Kernel launchers (k_trace.cu, k_refit.cu).

@@ -24,10 +24,6 @@
 
 #include "svo_internal.h"
 
-namespace svo {
-unsigned long long trace_tile_rays();
-}
-
 using namespace svo;
 
 namespace {
@@ -69,6 +65,7 @@ int scene_device(const svo_scene *s);
 TraceItem scene_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *flags);
 unsigned int *scene_err_word(const svo_scene *s);
 int scene_sm_count(const svo_scene *s);
+void scene_trace_config(const svo_scene *s, int *block, int *rays_per_lane);
 svo_status set_last_error(svo_status code, const char *msg);
 }
 
@@ -103,7 +100,11 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->n_items = 1;
   L->flags = flags;
   L->stats = nullptr;
-  const unsigned long long tile = trace_tile_rays();
+  int block = 128, rpl = 4;
+  scene_trace_config(s, &block, &rpl);
+  L->block = block;
+  L->rays_per_lane = rpl;
+  const unsigned long long tile = 32ull * rpl;
   L->n_tiles = (n + tile - 1) / tile;
   L->tile_counter = reinterpret_cast<unsigned long long *>(base);
   L->fix_count = reinterpret_cast<unsigned int *>(base + sizeof(unsigned long long));

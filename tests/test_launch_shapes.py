@@ -1,0 +1,99 @@
+"""Launch-shape knobs (block size, rays per lane, ray order), the autotuner and
+the CUDA-graph frame: none of them may change a result."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import synthetic
+from gpu_helpers import GpuScene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1911_06001_gb300 as g
+
+    c = g.Context(0)
+    yield c
+    c.check_device()
+    c.close()
+
+
+def _same(a, b):
+    for k in ("t", "part", "voxel", "flags"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_every_launch_shape_gives_identical_hits(ctx):
+    import paper_1911_06001_gb300 as g
+
+    s = synthetic.pr1_scene()
+    gs = GpuScene(ctx, s)
+    rng = np.random.default_rng(3)
+    rays = np.concatenate([synthetic.pr1_rays(s)[:9000], synthetic.random_rays(3001, rng, (-3,) * 3, (3,) * 3)])
+    ctx.set_trace_config(128, 4)
+    ref = gs.trace(rays, g.TRACE_DEFAULT)
+    for block in (64, 128, 256):
+        for rpl in (1, 2, 4, 8):
+            ctx.set_trace_config(block, rpl)
+            _same(gs.trace(rays, g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN), ref)
+    ctx.set_trace_config(128, 4)
+    with pytest.raises(g.SvoError):
+        ctx.set_trace_config(96, 4)
+    with pytest.raises(g.SvoError):
+        ctx.set_trace_config(128, 3)
+
+
+def test_autotune_picks_a_valid_shape_and_caches_it(ctx, tmp_path):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300 import autotune
+
+    s = synthetic.pr1_scene()
+    gs = GpuScene(ctx, s)
+    rays = torch.from_numpy(synthetic.pr1_rays(s, 256, 256)).cuda()
+    cache = str(tmp_path / "tune.json")
+    cfg = autotune.tune(ctx, gs.sc, rays, reps=2, blocks=(64, 128), rays_per_lane=(2, 4), cache_path=cache,
+                        key="pr1-256")
+    assert cfg["block"] in (64, 128) and cfg["rays_per_lane"] in (2, 4) and cfg["order"] in autotune.ORDERS
+    assert ctx.trace_config() == (cfg["block"], cfg["rays_per_lane"])
+    assert len(cfg["table"]) == 2 * 2 * 3
+    assert autotune.load(cache)["pr1-256"]["block"] == cfg["block"]
+    again = autotune.tune(ctx, gs.sc, rays, cache_path=cache, key="pr1-256")  # from the cache
+    assert again["ms"] == cfg["ms"]
+    ctx.set_trace_config(128, 4)
+    assert g.TRACE_ORDER_DIR == autotune.ORDERS["dir"]
+
+
+def test_frame_graph_replays_match_eager_frames(ctx):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300.graphs import FrameGraph
+
+    fig = synthetic.articulated_figure(depth=6)
+    gs = GpuScene(ctx, fig.scene)
+    rays_np = fig.rays(240, 135)
+    rays = torch.from_numpy(rays_np).cuda()
+    hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device="cuda")
+    fg = FrameGraph(ctx, gs.sc, rays, hits, flags=g.TRACE_DEFAULT)
+    for frame in (3, 19, 44):
+        local = fig.pose(frame)
+        fg.replay(local)
+        torch.cuda.synchronize()
+        got = g.decode_hits(hits)
+        gs.set_pose(local)
+        ref = gs.trace(rays_np, g.TRACE_DEFAULT)
+        for k in ("t", "part", "voxel"):
+            assert np.array_equal(got[k], ref[k]), (frame, k)
+        assert (ref["part"] != 0xFFFFFFFF).sum() > 200
