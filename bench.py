@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving sections")
+    ap.add_argument("--serve-requests", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -185,6 +187,79 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(out))
 
 
+def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
+    """The batched configuration: many uneven scenes traced in one persistent
+    launch (trace_batch) against the same scenes traced one call each."""
+    import torch
+
+    scenes = []
+    for sc_spec in bat.scenes:
+        sc = ctx.scene([pool_handles[int(a)] for a in sc_spec.part_asset], sc_spec.parent)
+        sc.set_transforms(sc_spec.local)
+        sc.refit()
+        scenes.append(sc)
+    rays = [torch.from_numpy(r).to(dev) for r in bat.rays]
+    hits = [torch.empty((r.shape[0], 2), dtype=torch.int64, device=dev) for r in rays]
+    n = sum(int(r.shape[0]) for r in rays)
+    items = [(sc, r, h, None) for sc, r, h in zip(scenes, rays, hits)]
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        evs = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record()
+            fn()
+            e[1].record()
+            evs.append(e)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs[2:]]))
+
+    flags = g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN
+    t_batch = timed(lambda: ctx.trace_batch(items, flags=flags))
+    t_each = timed(lambda: [sc.trace(r, h, flags=flags) for sc, r, h, _ in items])
+    ctx.check_device()
+    for sc in scenes:
+        sc.close()
+    return {"workload": f"{len(bat.scenes)} scenes of 4-256 parts (depth 6-11 pool, affine with shear), "
+                        f"{n} incoherent rays in all", "rays": n,
+            "batched": {"value": n / (t_batch / 1e3) / 1e6, "unit": "Mrays/s", "ms": t_batch,
+                        "launch": "one persistent trace_batch (ray order: origin)"},
+            "per_scene_calls": {"value": n / (t_each / 1e3) / 1e6, "unit": "Mrays/s", "ms": t_each}}
+
+
+def serving_section(g, ctx, srv, pool_handles, n_requests: int, warm: int, rate: float) -> dict:
+    """Served render requests (continuous batching) against the same stream
+    rendered one request at a time."""
+    from paper_1911_06001_gb300.serving import Server, latency_stats, run_unbatched
+
+    scenes = [([pool_handles[int(a)] for a in s.scene.part_asset], s.scene.parent) for s in srv.scenes]
+    reqs = srv.requests(n_requests, rate=rate, seed=int(SEED_SERVE))
+    server = Server(ctx, scenes, n_slots=4, max_batch_rays=8 << 20, instances_per_scene=4)
+    tickets = server.run(reqs)
+    meas = {id(r) for r in reqs[warm:]}
+    served = latency_stats([(t.arrival, t.done, t.n_rays) for t in tickets if id(t.request) in meas])
+    batches = {}
+    for t in tickets:
+        batches[t.submitted] = batches.get(t.submitted, 0) + 1
+    served["mean_batch"] = float(np.mean(list(batches.values())))
+    # saturation: every request queued at once -> the server's throughput ceiling
+    burst = srv.requests(max(n_requests // 3, 64), rate=1e9, seed=int(SEED_SERVE) + 1)
+    bt = server.run(burst)
+    sat = latency_stats([(t.arrival, t.done, t.n_rays) for t in bt])
+    alone = [ctx.scene(h, p) for h, p in scenes]
+    plain = latency_stats(run_unbatched(ctx, alone, reqs)[warm:])
+    ctx.check_device()
+    return {"workload": f"{len(srv.scenes)} resident scenes (16-128 parts, depth 8-11), Poisson {rate:g} req/s, "
+                        f"resolutions 256^2/512^2/1280x720/1920x1080, fresh pose per request",
+            "served": served, "unbatched": plain,
+            "saturated": {"requests": sat["requests"], "mrays_per_s": sat["mrays_per_s"]}}
+
+
+SEED_SERVE = 1911_06001 + 4 * 1000 + 7
+
+
 def main() -> None:
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -200,6 +275,11 @@ def main() -> None:
     fig = synthetic.articulated_figure()
     poses = [fig.pose(f) for f in range(FRAMES)]
     rays_np = fig.rays(WIDTH, HEIGHT)
+    extra = not args.no_extra
+    if extra:
+        pool = synthetic.asset_pool(range(6, 12), 4, seed=synthetic.config_seed(2, 1))
+        bat = synthetic.batched_scenes(pool=pool)
+        srv = synthetic.serving_world(pool=pool, pool_indices=list(range(2 * 4, 6 * 4)))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(fig, poses)
@@ -219,6 +299,8 @@ def main() -> None:
         dist.barrier()
     __graft_entry__.build()
     import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300 import autotune
+    from paper_1911_06001_gb300.graphs import FrameGraph
 
     ctx = g.Context(local_rank)
     handles = [ctx.upload(a.depth, a.leaf_ids, a.rgb) for a in fig.scene.assets]
@@ -227,8 +309,14 @@ def main() -> None:
     rays = torch.from_numpy(rays_np).to(dev)
     hits = torch.empty((N_RAYS, 2), dtype=torch.int64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX
     torch.cuda.synchronize()
+
+    # launch shape: autotuned on the first frame (results do not depend on it)
+    sc.set_transforms(poses[0])
+    sc.refit()
+    tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3)
+    order = autotune.order_flag(tuned)
+    flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX | order
 
     def frame_of(s: int) -> int:
         return (s * world + rank) % FRAMES
@@ -253,11 +341,10 @@ def main() -> None:
         with torch.cuda.stream(stream):
             sc.set_transforms(poses[f], stream=stream)
             sc.refit(stream=stream)
-            sc.trace(rays, hits, flags=g.TRACE_DEFAULT | g.TRACE_STATS, stats=st, stream=stream)
+            sc.trace(rays, hits, flags=g.TRACE_DEFAULT | g.TRACE_STATS | order, stats=st, stream=stream)
         stream.synchronize()
         stats_by_frame[f] = g.read_stats(st)
     ctx.check_device()
-
     # warm-up
     for s in range(args.warmup):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -293,6 +380,21 @@ def main() -> None:
         total_ms = float(t.item())
     ctx.check_device()
     value = world * args.steps * N_RAYS / (total_ms / 1e3) / 1e6
+
+    # the same frames as CUDA-graph replays (pose copy + refit + trace + FP64 pass in one graph)
+    fg = FrameGraph(ctx, sc, rays, hits, flags=g.TRACE_DEFAULT | order)
+    graph_ev = []
+    with torch.cuda.stream(fg.stream):
+        for s in range(args.warmup + min(args.steps, 200)):
+            flush.fill_(s & 0xFF)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(fg.stream)
+            fg.replay(poses[frame_of(s)])
+            ev[1].record(fg.stream)
+            if s >= args.warmup:
+                graph_ev.append(ev)
+    torch.cuda.synchronize()
+    graph_ms = np.array([e[0].elapsed_time(e[1]) for e in graph_ev])
 
     # plain single-scene trace (no culling, no depth sort) on the same frames, same timing rules
     plain_ms = []
@@ -352,6 +454,13 @@ def main() -> None:
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                 "bytes_per_launch": alg_bytes, "launch_ms": float(trace_ms.mean())}
 
+    batched = serving = None
+    if extra:
+        pool_handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
+        batched = batched_section(g, ctx, bat, pool_handles, dev, reps=5, flush=flush)
+        serving = serving_section(g, ctx, srv, pool_handles, args.serve_requests, warm=args.serve_requests // 5,
+                                  rate=2000.0)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -359,20 +468,26 @@ def main() -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "rays_per_step": N_RAYS, "parts": fig.scene.n_parts, "svo_depth": 9,
                        "leaves": int(sum(a.n_leaves for a in fig.scene.assets)),
-                       "flags": "cull+sort+fp64_fix", "parallelism": f"replicas x{world} (frames sharded)",
+                       "flags": "cull+sort+fp64_fix (+ autotuned launch shape and ray order)", "parallelism": f"replicas x{world} (frames sharded)",
                        "l2": "flushed between steps (256 MiB write, outside the per-step events)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "per": "frame (pose upload + refit + trace + FP64 fix)"},
             "breakdown_ms": {"refit": float(refit_ms.mean()), "trace": float(trace_ms.mean()),
                              "fp64_fix": float(fix_ms.mean())},
             "plain_trace": {"value": plain_value, "unit": "Mrays/s", "flags": "fp64_fix only (no cull, no sort)"},
+            "graph": {"value": N_RAYS / (graph_ms.mean() / 1e3) / 1e6, "unit": "Mrays/s",
+                      "ms_per_step": float(graph_ms.mean()), "p99_ms": float(np.percentile(graph_ms, 99))},
+            "launch": {"block": tuned["block"], "rays_per_lane": tuned["rays_per_lane"], "order": tuned["order"],
+                       "autotuned_ms": tuned["ms"], "default_ms": tuned["default_ms"]},
+            "batched": batched,
+            "serving": serving,
             "flagged_frac": float(flagged / N_RAYS),
             "nodes_per_ray": float(nodes / N_RAYS),
             "parts_entered_per_ray": float(parts / N_RAYS),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (3 + (3 if order else 0)) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
         }

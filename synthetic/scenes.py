@@ -510,7 +510,7 @@ class BatchedScenes:
 
 
 def batched_scenes(seed: int | None = None, n_scenes: int = 64, parts=(4, 256), depths=range(6, 12),
-                   side=(64, 1024), per_depth: int = 4, thin_from: int = 11) -> BatchedScenes:
+                   side=(64, 1024), per_depth: int = 4, thin_from: int = 11, pool=None) -> BatchedScenes:
     """Uneven scenes: P log-uniform in ``parts``; per part a random pool asset
     of a random depth; pose = rotation (uniform) x scale U(0.5, 2) per axis x
     shear U(-0.1, 0.1) on three off-diagonals, translation in a box of side
@@ -518,7 +518,9 @@ def batched_scenes(seed: int | None = None, n_scenes: int = 64, parts=(4, 256), 
     origins uniform in the box, directions uniform on the sphere."""
     rng = np.random.default_rng(config_seed(2) if seed is None else seed)
     depths = list(depths)
-    pool = asset_pool(depths, per_depth, seed=int(rng.integers(1 << 31)), thin_from=thin_from)
+    pool_seed = int(rng.integers(1 << 31))
+    if pool is None:
+        pool = asset_pool(depths, per_depth, seed=pool_seed, thin_from=thin_from)
     assets = [p.asset for p in pool]
     scenes, rays = [], []
     for _ in range(n_scenes):
@@ -600,19 +602,23 @@ class ServingWorld:
 
 
 def serving_world(seed: int | None = None, n_scenes: int = 32, parts=(16, 128), depths=range(8, 12),
-                  per_depth: int = 4, thin_from: int = 11) -> ServingWorld:
+                  per_depth: int = 4, thin_from: int = 11, pool=None, pool_indices=None) -> ServingWorld:
     """Resident scenes for the serving workload: P uniform in ``parts``, parts
     drawn from a pool of depths ``depths``; each part hangs from a random
     earlier part at a point on its surface and swings about a seeded axis."""
     rng = np.random.default_rng(config_seed(4) if seed is None else seed)
     depths = list(depths)
-    pool = asset_pool(depths, per_depth, seed=int(rng.integers(1 << 31)), thin_from=thin_from)
+    pool_seed = int(rng.integers(1 << 31))
+    if pool is None:
+        pool = asset_pool(depths, per_depth, seed=pool_seed, thin_from=thin_from)
+    # the pool entries a part may draw (all of them unless a shared pool is restricted)
+    choices = np.arange(len(pool)) if pool_indices is None else np.asarray(pool_indices)
     assets = [p.asset for p in pool]
     scenes = []
     c = np.array([0.5, 0.5, 0.5])
     for _ in range(n_scenes):
         P = int(rng.integers(parts[0], parts[1] + 1))
-        part_asset = np.array([int(rng.integers(len(pool))) for _ in range(P)], dtype=np.int32)
+        part_asset = np.array([int(choices[rng.integers(len(choices))]) for _ in range(P)], dtype=np.int32)
         parent = np.array([-1] + [int(rng.integers(max(0, i - 6), i)) for i in range(1, P)], dtype=np.int32)
         attach = np.zeros((P, 3))
         joint = np.zeros((P, 3))
