@@ -58,6 +58,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def frame_of(step: int, world: int, rank: int) -> int:
+    """Frame rendered by ``rank`` at ``step``: ranks take interleaved frames
+    (weak scaling; no data moves between ranks)."""
+    return (step * world + rank) % FRAMES
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value across ranks (the slowest rank's time); the value
+    itself when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -318,9 +337,6 @@ def main() -> None:
     order = autotune.order_flag(tuned)
     flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX | order
 
-    def frame_of(s: int) -> int:
-        return (s * world + rank) % FRAMES
-
     def step(frame: int, ev):
         ev[0].record(stream)
         sc.set_transforms(poses[frame], stream=stream)
@@ -334,7 +350,7 @@ def main() -> None:
     # untimed: per-frame node-fetch counts for the algorithmic byte count
     stats_by_frame = {}
     for s in range(args.warmup, args.warmup + args.steps):
-        f = frame_of(s)
+        f = frame_of(s, world, rank)
         if f in stats_by_frame:
             continue
         st = g.new_stats(dev)
@@ -349,7 +365,7 @@ def main() -> None:
     for s in range(args.warmup):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         flush.fill_(s & 0xFF)
-        step(frame_of(s), ev)
+        step(frame_of(s, world, rank), ev)
     stream.synchronize()
 
     n_ev = args.steps
@@ -363,7 +379,7 @@ def main() -> None:
     with torch.cuda.stream(stream):
         for s in range(args.steps):
             flush.fill_((s + 1) & 0xFF)  # L2 flush, outside the step's events
-            step(frame_of(args.warmup + s), evs[s])
+            step(frame_of(args.warmup + s, world, rank), evs[s])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     if world > 1:
@@ -373,11 +389,7 @@ def main() -> None:
     refit_ms = np.array([e[0].elapsed_time(e[1]) for e in evs])
     trace_ms = np.array([e[1].elapsed_time(e[2]) for e in evs])
     fix_ms = np.array([e[2].elapsed_time(e[3]) for e in evs])
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(step_ms.sum()), dev)
     ctx.check_device()
     value = world * args.steps * N_RAYS / (total_ms / 1e3) / 1e6
 
@@ -389,7 +401,7 @@ def main() -> None:
             flush.fill_(s & 0xFF)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             ev[0].record(fg.stream)
-            fg.replay(poses[frame_of(s)])
+            fg.replay(poses[frame_of(s, world, rank)])
             ev[1].record(fg.stream)
             if s >= args.warmup:
                 graph_ev.append(ev)
@@ -402,7 +414,7 @@ def main() -> None:
         for s in range(min(args.steps, 10)):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             flush.fill_(s & 0xFF)
-            f = frame_of(args.warmup + s)
+            f = frame_of(args.warmup + s, world, rank)
             ev[0].record(stream)
             sc.set_transforms(poses[f], stream=stream)
             sc.refit(stream=stream)
@@ -423,7 +435,7 @@ def main() -> None:
             for s in range(args.warmup + args.steps):
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 flush.fill_(s & 0xFF)
-                f = frame_of(s)
+                f = frame_of(s, world, rank)
                 ev[0].record(stream)
                 sc.set_transforms(poses[f], stream=stream)
                 sc.refit(stream=stream)
@@ -432,17 +444,13 @@ def main() -> None:
                 if s >= args.warmup:
                     e2e_ev.append(ev)
         torch.cuda.synchronize()
-        e2e_ms = float(sum(e[0].elapsed_time(e[1]) for e in e2e_ev))
-        if world > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(float(sum(e[0].elapsed_time(e[1]) for e in e2e_ev)), dev)
         e2e = {"value": world * args.steps * N_RAYS / (e2e_ms / 1e3) / 1e6, "unit": "Mrays/s",
                "h2d_bytes_per_step": N_RAYS * 32 + fig.scene.n_parts * 96, "d2h_bytes_per_step": N_RAYS * 16,
                "ms_per_step": e2e_ms / args.steps}
 
     # roofline of the dominant kernel (the trace kernel)
-    timed_frames = [frame_of(args.warmup + s) for s in range(args.steps)]
+    timed_frames = [frame_of(args.warmup + s, world, rank) for s in range(args.steps)]
     nodes = np.mean([stats_by_frame[f]["nodes_visited"] for f in timed_frames])
     parts = np.mean([stats_by_frame[f]["parts_entered"] for f in timed_frames])
     flagged = np.mean([stats_by_frame[f]["flagged"] for f in timed_frames])

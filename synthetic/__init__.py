@@ -35,4 +35,7 @@ from .scenes import (  # noqa: F401
     RenderRequest,
     ServingWorld,
     serving_world,
+    PrecisionScene,
+    precision_scene,
+    grazing_rays,
 )

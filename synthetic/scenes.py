@@ -648,3 +648,95 @@ def serving_world(seed: int | None = None, n_scenes: int = 32, parts=(16, 128), 
         sc.local = served.pose(np.random.default_rng(0))
         scenes.append(served)
     return ServingWorld(pool, scenes)
+
+
+# ------------------------------------------------------------------ PREC
+
+@dataclass
+class PrecisionScene:
+    """Precision stress: visible parts at the ends of long rigid chains."""
+
+    scene: Scene
+    visible: np.ndarray  # indices of the parts that carry geometry
+    eye: np.ndarray
+    target: np.ndarray
+
+
+def precision_scene(seed: int | None = None, n_visible: int = 8, chain: int = 5, depth: int = 13,
+                    radius=(150.0, 400.0), max_shift_leaves: float = 1e4) -> PrecisionScene:
+    """``n_visible`` parts, each the last link of a ``chain``-level chain of
+    rigid transforms whose other links are empty parts; two depth-``depth``
+    one-cell sphere shells (radius uniform in ``radius`` cells) shared by the
+    visible parts; every link translates by up to ``max_shift_leaves`` leaf
+    sizes and rotates by a uniform random rotation."""
+    rng = np.random.default_rng(config_seed(3) if seed is None else seed)
+    n = 1 << depth
+    shells = []
+    for _ in range(2):
+        r = rng.uniform(*radius)
+        c = np.array([n / 2.0] * 3) + rng.uniform(-20, 20, 3)
+        shells.append(make_asset(depth, ellipsoid_shell(depth, c, (r, r, r), 1.0)))
+    empty = Asset(depth, np.zeros(0, np.uint64), np.zeros(0, np.uint32))
+    assets = shells + [empty]
+    P = n_visible * chain
+    parent = np.zeros(P, dtype=np.int32)
+    part_asset = np.zeros(P, dtype=np.int32)
+    local = np.zeros((P, 12))
+    visible = []
+    leaf = 1.0 / n
+    for v in range(n_visible):
+        for k in range(chain):
+            i = v * chain + k
+            parent[i] = -1 if k == 0 else i - 1
+            R = _random_rotation(rng)
+            shift = rng.uniform(-max_shift_leaves, max_shift_leaves, 3) * leaf
+            if k == 0:
+                shift = shift + rng.uniform(-3.0, 3.0, 3)
+            local[i] = affine12(R, shift)
+            part_asset[i] = 2 if k < chain - 1 else v % 2
+        visible.append(v * chain + chain - 1)
+    scene = Scene("PREC", assets, part_asset, parent, local)
+    view = rng.standard_normal(3)
+    view /= np.linalg.norm(view)
+    return PrecisionScene(scene, np.array(visible), view * 14.0, np.zeros(3))
+
+
+def grazing_rays(world12, depth: int, leaf_ids, n: int, rng: np.random.Generator, max_angle: float = 1e-3,
+                 back_off_leaves: float = 100.0) -> np.ndarray:
+    """Rays that graze a face of a leaf: pick a leaf and one of its faces, a
+    direction inside the face plane tilted by at most ``max_angle`` rad towards
+    the face normal, and an origin ``back_off_leaves`` leaf sizes behind a point
+    of the face.  Built in the part's local frame and mapped to world space by
+    the part's pose ``world12`` (the forward map, given by the caller)."""
+    M = np.asarray(world12, dtype=np.float64).reshape(3, 4)
+    ids = np.asarray(leaf_ids, dtype=np.uint64)
+    pick = ids[rng.integers(0, ids.shape[0], n)]
+    x, y, z = unpack_ids(pick, depth)
+    s = 1.0 / (1 << depth)
+    cell = np.stack([x, y, z], axis=1).astype(np.float64) * s
+    axis = rng.integers(0, 3, n)
+    side = rng.integers(0, 2, n).astype(np.float64)
+    out = np.empty((n, 8), dtype=np.float32)
+    for k in range(n):
+        a = int(axis[k])
+        others = [i for i in range(3) if i != a]
+        p = cell[k] + s * 0.5
+        p[a] = cell[k][a] + side[k] * s
+        p[others[0]] = cell[k][others[0]] + rng.uniform(0.1, 0.9) * s
+        p[others[1]] = cell[k][others[1]] + rng.uniform(0.1, 0.9) * s
+        phi = rng.uniform(0, 2 * math.pi)
+        tilt = rng.uniform(0, max_angle) * (1 if rng.random() < 0.5 else -1)
+        d = np.zeros(3)
+        d[others[0]] = math.cos(phi)
+        d[others[1]] = math.sin(phi)
+        d[a] = math.tan(tilt)
+        d /= np.linalg.norm(d)
+        o = p - d * back_off_leaves * s
+        wo = M[:, :3] @ o + M[:, 3]
+        wd = M[:, :3] @ d
+        wd /= np.linalg.norm(wd)
+        out[k, 0:3] = wo
+        out[k, 3] = 0.0
+        out[k, 4:7] = wd
+        out[k, 7] = np.inf
+    return out
