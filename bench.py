@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving sections")
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--launch", default="", help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER instead of autotuning")
     return ap.parse_args()
 
 
@@ -333,7 +334,12 @@ def main() -> None:
     # launch shape: autotuned on the first frame (results do not depend on it)
     sc.set_transforms(poses[0])
     sc.refit()
-    tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3)
+    if args.launch:
+        b, r, o = args.launch.split(",")
+        tuned = {"block": int(b), "rays_per_lane": int(r), "order": o, "ms": None, "default_ms": None}
+        autotune.apply(ctx, tuned)
+    else:
+        tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3)
     order = autotune.order_flag(tuned)
     flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX | order
 

@@ -75,8 +75,9 @@ typedef int32_t svo_status;
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 
 /* per-ray flags written when ray_flags != NULL */
-#define SVO_RAY_UNCERTAIN 1u /* FP32 could not certify the closest hit (near tie / grazing) */
+#define SVO_RAY_UNCERTAIN 1u /* FP32 could not certify which leaf is hit first (near tie / grazing) */
 #define SVO_RAY_FIXED 2u     /* the hit was recomputed in FP64 */
+#define SVO_RAY_T_REFINED 4u /* the ids were certified but t was recomputed in FP64 for precision */
 
 typedef struct svo_ctx svo_ctx;
 typedef struct svo_scene svo_scene;
@@ -101,7 +102,7 @@ typedef struct {
 /* Counters accumulated (atomically, on the device) when SVO_TRACE_STATS is set. */
 typedef struct {
   unsigned long long rays;          /* rays traced */
-  unsigned long long flagged;       /* rays flagged SVO_RAY_UNCERTAIN */
+  unsigned long long flagged;       /* rays flagged SVO_RAY_UNCERTAIN (ids not certified) */
   unsigned long long fixed;         /* rays recomputed in FP64 */
   unsigned long long parts_tested;  /* (ray, part) sphere tests */
   unsigned long long parts_entered; /* (ray, part) traversals started */
@@ -110,7 +111,7 @@ typedef struct {
   unsigned long long passes;        /* candidate-list passes (> rays when lists overflow) */
   unsigned long long flag_winner;   /* flagged because the nearest candidate was not certainly hit */
   unsigned long long flag_overlap;  /* flagged because another candidate's entry bound reached it */
-  unsigned long long flag_width;    /* flagged because the winner's t interval was too wide */
+  unsigned long long flag_width;    /* ids certified, but the winner's t interval was too wide (T_REFINED) */
 } svo_trace_stats;
 
 /* A pinhole camera for svo_raygen_pinhole. */
@@ -219,17 +220,17 @@ svo_status scene_read_clusters(svo_scene *scene, int32_t *n_clusters, float *sph
  * ray; hits: device, n svo_hit; ray_flags: device, n uint32 or NULL;
  * stats: device svo_trace_stats or NULL (used with SVO_TRACE_STATS; the caller
  * zeroes it).  Traversal runs in FP32; a ray whose closest hit FP32 cannot
- * certify (the error-bounded intervals of two candidates overlap, or half
- * the winner's own interval exceeds 2^-17 of max(t, leaf diagonal / |d|))
- * is flagged, and with
- * SVO_TRACE_FP64_FIX re-intersected in FP64.  The scene must have been
+ * certify (the error-bounded intervals of two candidates overlap) is flagged
+ * SVO_RAY_UNCERTAIN; a ray whose ids are certified but whose winner's t
+ * interval is wider than 2^-17 of max(t, leaf diagonal / |d|) is flagged
+ * SVO_RAY_T_REFINED; with SVO_TRACE_FP64_FIX both are re-intersected in FP64.  The scene must have been
  * refitted since its last scene_set_transforms.  If n exceeds the largest n
  * traced so far on this context the call grows the context's scratch with
  * cudaMalloc, so call it once at full size before capturing a CUDA graph. */
 svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits, uint32_t *ray_flags,
                       uint32_t flags, svo_trace_stats *stats, void *stream);
 /* (With SVO_TRACE_ORDER_DIR / _ORIGIN the rays are first counting-sorted by a
- * 16-bit direction / origin-cell key into per-stream scratch, grown like the
+ * 14-bit direction / origin-cell key into per-stream scratch, grown like the
  * FP64 list; hits still land at each ray's own index.) */
 /* Batched trace: every item's rays against its own scene, in one persistent
  * launch whose thread blocks take fixed-size tiles of rays from a device work

@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
     MAX_DEPTH,
     MAX_PARTS,
     RAY_FIXED,
+    RAY_T_REFINED,
     RAY_UNCERTAIN,
     TRACE_CULL,
     TRACE_DEFAULT,

@@ -26,6 +26,7 @@ TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
 
 RAY_UNCERTAIN = 1
 RAY_FIXED = 2
+RAY_T_REFINED = 4
 
 MAX_DEPTH = 16
 MAX_PARTS = 1024

@@ -6,7 +6,7 @@
 //
 // Ray ordering: rays are permuted so that a warp traces rays that are close in
 // direction (and, optionally, origin) and therefore walk the same spheres and
-// octree nodes.  A 16-bit key per ray, a counting sort (histogram, exclusive
+// octree nodes.  A 14-bit key per ray, a counting sort (histogram, exclusive
 // scan, scatter), and the trace kernel reads rays through the permutation and
 // writes every hit back at its ray's own index -- results do not change.
 #include <cuda_runtime.h>
@@ -19,7 +19,7 @@ namespace svo {
 
 namespace {
 
-constexpr int kKeyBits = 16;
+constexpr int kKeyBits = 14;  // 16384 bins: the histogram (64 KiB) stays in L1 during the scan
 constexpr int kBins = 1 << kKeyBits;
 
 __global__ void k_raygen(RaygenArgs a, float4 *__restrict__ rays) {
@@ -81,23 +81,23 @@ __device__ __forceinline__ uint32_t dir_face(float dx, float dy, float dz, float
   return face;
 }
 
-// mode 1 (direction): face (3 bits) | 2D Morton of (u, v) at 6+6 bits.
-// mode 2 (origin): face | Morton of the origin cell in an 8^3 grid over the
-// scene's bounding sphere (9 bits) | 2D Morton of (u, v) at 2+2 bits.
+// mode 1 (direction): face (3 bits) | 2D Morton of (u, v) at 5+5 bits.
+// mode 2 (origin): face | Morton of the origin cell in a 4^3 grid over the
+// scene's bounding sphere (6 bits) | 2D Morton of (u, v) at 2+2 bits.
 __device__ __forceinline__ uint32_t ray_key(float4 o, float4 d, int mode, float4 bound) {
   float u, v;
   const uint32_t face = dir_face(d.x, d.y, d.z, u, v);
   if (mode == 1) {
-    const uint32_t qu = (uint32_t)(u * 64.f), qv = (uint32_t)(v * 64.f);
-    return (face << 12) | spread2(qu) | (spread2(qv) << 1);
+    const uint32_t qu = (uint32_t)(u * 32.f), qv = (uint32_t)(v * 32.f);
+    return (face << 10) | spread2(qu) | (spread2(qv) << 1);
   }
-  const float s = bound.w > 0.f ? 4.0f / bound.w : 0.f;  // 8 cells across the diameter
-  const int cx = min(max((int)floorf((o.x - bound.x) * s + 4.0f), 0), 7);
-  const int cy = min(max((int)floorf((o.y - bound.y) * s + 4.0f), 0), 7);
-  const int cz = min(max((int)floorf((o.z - bound.z) * s + 4.0f), 0), 7);
+  const float s = bound.w > 0.f ? 2.0f / bound.w : 0.f;  // 4 cells across the diameter
+  const int cx = min(max((int)floorf((o.x - bound.x) * s + 2.0f), 0), 3);
+  const int cy = min(max((int)floorf((o.y - bound.y) * s + 2.0f), 0), 3);
+  const int cz = min(max((int)floorf((o.z - bound.z) * s + 2.0f), 0), 3);
   const uint32_t cell = spread3((uint32_t)cx) | (spread3((uint32_t)cy) << 1) | (spread3((uint32_t)cz) << 2);
   const uint32_t qu = (uint32_t)(u * 4.f), qv = (uint32_t)(v * 4.f);
-  return (face << 13) | (cell << 4) | spread2(qu) | (spread2(qv) << 1);
+  return (face << 10) | (cell << 4) | spread2(qu) | (spread2(qv) << 1);
 }
 
 // Warp-uniform grid-stride loops (blockDim is a multiple of 32): every lane of a

@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __g
       CertState st;
       Contenders con;
       trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
-      bool flagged = false;
+      bool flagged = false, ids_ok = true;
       if (in_range) {
         float t = Num<float>::inf();
         uint32_t part = kMissPart;
@@ -807,11 +807,12 @@ __global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __g
           const bool w_ok = st.cert1 != 0u;
           const bool o_ok = st.lo2 > st.hi1;
           const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
-          flagged = !(w_ok && o_ok && t_ok);
+          ids_ok = w_ok && o_ok;
+          flagged = !(ids_ok && t_ok);
           if (STATS) {
             cnt.f_winner += w_ok ? 0u : 1u;
             cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
-            cnt.f_width += (w_ok && o_ok && !t_ok) ? 1u : 0u;
+            cnt.f_width += (ids_ok && !t_ok) ? 1u : 0u;
           }
           t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
           if (!st.cert1) t = st.te1;
@@ -824,8 +825,8 @@ __global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __g
         hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
         hv.w = (uint32_t)(vox >> 32);
         __stcs(&I.hits[ray], hv);
-        if (I.ray_flags) I.ray_flags[ray] = flagged ? SVO_RAY_UNCERTAIN : 0u;
-        if (STATS && flagged) ++n_flag;
+        if (I.ray_flags) I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? SVO_RAY_T_REFINED : 0u);
+        if (STATS && !ids_ok) ++n_flag;
       }
       // compact flagged rays for the FP64 pass (one atomic per warp)
       if (L.flags & SVO_TRACE_FP64_FIX) {
@@ -849,7 +850,8 @@ __global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __g
                   ++nc;
                 }
               }
-              L.fix_list[slot] = (nc << 48) | ((unsigned long long)it << kRayBits) | ray;
+              const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
+              L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
             } else {
               err |= kErrFixOverflow;
             }
@@ -882,7 +884,8 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   for (unsigned long long i = blockIdx.x + (unsigned long long)gridDim.x * threadIdx.x; i < n; i += stride) {
     const unsigned long long e = L.fix_list[i];
     const int nc = (int)(e >> 48);
-    const int it = (int)((e >> kRayBits) & 0xFFu);
+    const uint32_t why = ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN;
+    const int it = (int)((e >> kRayBits) & 0x7Fu);
     const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
     const TraceItem &I = L.items[it];
     const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
@@ -905,7 +908,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
       hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
       hv.w = (uint32_t)(st.vox >> 32);
       I.hits[ray] = hv;
-      if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_UNCERTAIN | SVO_RAY_FIXED;
+      if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
       continue;
     }
     RayW r;
@@ -942,7 +945,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
     hv.w = (uint32_t)(st.vox >> 32);
     I.hits[ray] = hv;
-    if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_UNCERTAIN | SVO_RAY_FIXED;
+    if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
   }
   // count fixed rays once per launch
   if (L.stats && blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);

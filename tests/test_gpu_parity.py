@@ -294,7 +294,8 @@ def test_stats_counters(ctx, pr1):
     flags = rf.cpu().numpy()
     assert s["rays"] == rays.shape[0]
     assert s["flagged"] == int(((flags & 1) != 0).sum())
-    assert s["fixed"] == s["flagged"]
+    assert s["flag_width"] == int(((flags & 4) != 0).sum())
+    assert s["fixed"] == s["flagged"] + s["flag_width"] == int(((flags & 2) != 0).sum())
     assert s["nodes_visited"] > 0 and s["parts_entered"] <= s["parts_tested"]
     assert s["passes"] >= s["rays"]
 
