@@ -273,6 +273,22 @@ svo_status trace_rays_noalloc(svo_scene *scene, const float *rays, uint64_t n, s
 svo_status svo_raygen_pinhole(svo_ctx *ctx, const svo_camera *cam, uint32_t width, uint32_t height, float *rays,
                               void *stream);
 
+/* Colour of hits (async): rgb[i] = the 0x00RRGGBB payload of the leaf that
+ * hits[i] names in part hits[i].part of `scene` (the colour the paper's hit
+ * buffer carries for shading, Sec. IV-C), or `background` for a miss.  The
+ * leaf's colour is the one given for the first occurrence of its id in the
+ * svo_desc leaf list (0 if the asset was uploaded without colours).
+ *   hits: device, n svo_hit (16-byte aligned), e.g. the output of trace_rays
+ *         once its FP64 pass has run (issue both on the same stream);
+ *   rgb:  device, n uint32 (4-byte aligned), written by the library.
+ * A hit that names no occupied leaf of the scene (part out of range, voxel
+ * outside the asset's grid or not a leaf) gets SVO_COLOR_INVALID.
+ * SVO_ERR_ARG for NULL or misaligned buffers with n > 0, or a background
+ * above 0x00FFFFFF. */
+#define SVO_COLOR_INVALID 0xFFFFFFFFu
+svo_status trace_hit_colors(svo_scene *scene, const svo_hit *hits, uint64_t n, uint32_t background, uint32_t *rgb,
+                            void *stream);
+
 /* Run the FP64 re-intersection pass left pending by the last trace_rays /
  * trace_batch issued on `stream` with SVO_TRACE_FP64_FIX | SVO_TRACE_DEFER_FIX
  * (async).  No-op (SVO_OK) if nothing is pending on that stream. */

@@ -141,6 +141,41 @@ def trace(part_assets, inv, rays, mode: int = 1, threads: int | None = None) -> 
     return {"t": out_t, "part": out_p, "voxel": out_v, "second": out_s}
 
 
+COLOR_INVALID = 0xFFFFFFFF
+
+
+def hit_colors(leaf_lists, part_asset, part, voxel, background: int = 0) -> np.ndarray:
+    """Colour of each hit, as the hit buffer carries it for shading (Sec. IV-C):
+    the colour given with the hit voxel's id in the part's asset leaf list (the
+    first occurrence when an id is listed twice), ``background`` for a miss,
+    COLOR_INVALID when the part or voxel names no leaf.
+
+    ``leaf_lists``: per asset a pair (leaf_ids, rgb or None); ``part_asset``:
+    asset index of each part; ``part``/``voxel``: the hits."""
+    part = np.asarray(part, dtype=np.uint32)
+    voxel = np.asarray(voxel, dtype=np.uint64)
+    out = np.full(part.shape, background, dtype=np.uint32)
+    hit = part != MISS_PART
+    out[hit] = COLOR_INVALID
+    for p in np.unique(part[hit]):
+        sel = np.nonzero(part == p)[0]
+        if int(p) >= len(part_asset):
+            continue
+        ids, rgb = leaf_lists[int(part_asset[int(p)])]
+        ids = np.asarray(ids, dtype=np.uint64)
+        if rgb is None:
+            rgb = np.zeros(ids.shape, dtype=np.uint32)
+        # a stable sort keeps equal ids in list order, so the left end of each
+        # run of equal ids is the first occurrence
+        order = np.argsort(ids, kind="stable")
+        sids = ids[order]
+        pos = np.searchsorted(sids, voxel[sel], side="left")
+        found = pos < sids.shape[0]
+        found[found] = sids[pos[found]] == voxel[sel][found]
+        out[sel[found]] = np.asarray(rgb, dtype=np.uint32)[order[pos[found]]]
+    return out
+
+
 class SceneOracle:
     """Oracle view of a ``synthetic.Scene``: assets built once, poses per frame."""
 
@@ -152,6 +187,10 @@ class SceneOracle:
         local = self.scene.local if local is None else local
         world = compose(self.scene.parent, local)
         return world, invert(world)
+
+    def hit_colors(self, hits: dict, background: int = 0) -> np.ndarray:
+        leaf_lists = [(a.leaf_ids, a.rgb) for a in self.scene.assets]
+        return hit_colors(leaf_lists, self.scene.part_asset, hits["part"], hits["voxel"], background)
 
     def trace(self, rays, local=None, mode: int = 1, threads: int | None = None) -> dict:
         world, inv = self.poses(local)

@@ -15,6 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
+    COLOR_INVALID,
     MAX_DEPTH,
     MAX_PARTS,
     RAY_FIXED,
@@ -195,6 +196,18 @@ class Scene:
         _lib.check(self.lib.trace_rays(self.h, _ptr(rays), n, _ptr(hits), _ptr(ray_flags), int(flags), _ptr(stats),
                                        _stream_ptr(stream)))
         return hits
+
+    def hit_colors(self, hits, background: int = 0, out=None, stream=None):
+        """Leaf colours (0x00RRGGBB as int32) of hits from ``trace``; ``background`` for misses."""
+        import torch
+
+        if hits.dtype != torch.int64 or hits.dim() != 2 or hits.shape[1] != 2 or not hits.is_cuda:
+            raise ValueError("hits must be a CUDA int64 tensor [n, 2]")
+        n = hits.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=hits.device)
+        _lib.check(self.lib.trace_hit_colors(self.h, _ptr(hits), n, int(background), _ptr(out), _stream_ptr(stream)))
+        return out
 
     def trace_host(self, rays_host, hits_host, flags: int = TRACE_DEFAULT, ray_flags_host=None, stream=None):
         """Trace rays held in host memory (CPU tensors, ideally pinned) into host hits (async on ``stream``)."""

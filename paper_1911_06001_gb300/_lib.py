@@ -31,6 +31,7 @@ RAY_T_REFINED = 4
 MAX_DEPTH = 16
 MAX_PARTS = 1024
 NOALLOC_MAX_RAYS = 262144
+COLOR_INVALID = 0xFFFFFFFF
 
 # every symbol include/svoanim.h declares
 EXPORTS = [
@@ -39,7 +40,7 @@ EXPORTS = [
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
-    "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole",
+    "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole", "trace_hit_colors",
 ]
 
 
@@ -108,6 +109,7 @@ def load(path: str | None = None):
         "trace_rays_host": ([vp, vp, u64, vp, vp, u32, vp], i32),
         "trace_rays_noalloc": ([vp, vp, u64, vp, vp, u32, vp], i32),
         "svo_raygen_pinhole": ([vp, C.POINTER(SvoCamera), u32, u32, vp, vp], i32),
+        "trace_hit_colors": ([vp, vp, u64, u32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -433,6 +433,8 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
       stat[i].depth = a->depth;
       stat[i].parent = parent[i];
       stat[i].pad = 0;
+      stat[i].rgb = a->d_rgb;
+      stat[i].n_leaves = a->n_leaves;
     }
   }
   int L = 0;
@@ -753,6 +755,20 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   if (rc != SVO_OK) return rc;
   CK(cudaMemcpyAsync(hits_host, d_hits, n * 16, cudaMemcpyDeviceToHost, st));
   if (d_flags) CK(cudaMemcpyAsync(ray_flags_host, d_flags, n * 4, cudaMemcpyDeviceToHost, st));
+  return ok();
+}
+
+svo_status trace_hit_colors(svo_scene *s, const svo_hit *hits, uint64_t n, uint32_t background, uint32_t *rgb,
+                            void *stream) {
+  if (!s) return fail(SVO_ERR_ARG, "trace_hit_colors: scene is NULL");
+  if (background > 0x00FFFFFFu) return fail(SVO_ERR_ARG, "trace_hit_colors: background 0x%x is not 0x00RRGGBB", background);
+  if (n == 0) return ok();
+  if (!hits || !rgb) return fail(SVO_ERR_ARG, "trace_hit_colors: NULL buffer");
+  if (reinterpret_cast<uintptr_t>(hits) & 15) return fail(SVO_ERR_ARG, "trace_hit_colors: hits not 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(rgb) & 3) return fail(SVO_ERR_ARG, "trace_hit_colors: rgb not 4-byte aligned");
+  CK(cudaSetDevice(s->ctx->device));
+  CK(launch_hit_colors(reinterpret_cast<const uint4 *>(hits), n, s->d_stat, s->P, background, rgb, s->ctx->n_sm,
+                       (cudaStream_t)stream));
   return ok();
 }
 

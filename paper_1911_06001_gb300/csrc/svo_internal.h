@@ -31,6 +31,8 @@ struct PartStatic {
   int32_t depth;
   int32_t parent;
   int32_t pad;
+  const uint32_t *rgb;  // leaf payload, indexed like the leaf-level children
+  unsigned long long n_leaves;
 };
 
 // Per-frame FP32 data of a part used by the trace kernel (64 B, staged in
@@ -98,6 +100,10 @@ struct TraceLaunch {
 // Kernel launchers (k_trace.cu, k_refit.cu).
 cudaError_t launch_trace(const TraceLaunch &L, int n_sm, cudaStream_t stream);
 cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream);
+
+// Leaf colours of n hits (k_color.cu); see trace_hit_colors.
+cudaError_t launch_hit_colors(const uint4 *hits, unsigned long long n, const PartStatic *stat, int n_parts,
+                              uint32_t background, uint32_t *rgb, int n_sm, cudaStream_t stream);
 
 struct RaygenArgs {
   float eye[3], f[3], r[3], u[3];  // camera origin and unit forward / right / up

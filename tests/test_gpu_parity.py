@@ -353,3 +353,49 @@ def test_raygen_matches_host_pinhole(ctx):
         assert np.array_equal(got[:, 0:4], ref[:, 0:4])
         assert np.max(np.abs(got[:, 4:7] - ref[:, 4:7])) <= 2e-6
         assert np.all(np.isinf(got[:, 7]))
+
+
+def _pack_hits(t, part, voxel):
+    p = np.zeros((len(t), 4), np.uint32)
+    p[:, 0] = np.asarray(t, np.float32).view(np.uint32)
+    p[:, 1] = part
+    p[:, 2] = (np.asarray(voxel, np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    p[:, 3] = (np.asarray(voxel, np.uint64) >> np.uint64(32)).astype(np.uint32)
+    return p.view(np.int64).reshape(-1, 2)
+
+
+def test_hit_colors_match_oracle(ctx, pr1):
+    """Leaf colours of hits (Sec. IV-C hit buffer): the oracle's hits coloured
+    on the GPU equal the oracle's colours everywhere; the GPU's own trace gives
+    the oracle's colours on every ray whose ids are certified; hits that name
+    no leaf come back invalid."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    rays = synthetic.pr1_rays(scene)
+    ora = so.trace(rays)
+    bg = 0x102030
+    want = so.hit_colors(ora, background=bg)
+    hits = torch.from_numpy(_pack_hits(ora["t"], ora["part"], ora["voxel"])).cuda()
+    got = gs.sc.hit_colors(hits, background=bg).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, want)
+    assert (ora["part"] != oracle.MISS_PART).sum() > 1000
+    r = torch.from_numpy(np.ascontiguousarray(rays, dtype=np.float32)).cuda()
+    rf = torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")
+    h2 = gs.sc.trace(r, flags=g.TRACE_DEFAULT, ray_flags=rf)
+    c2 = gs.sc.hit_colors(h2, background=bg).cpu().numpy().view(np.uint32)
+    certified = (rf.cpu().numpy() & g.RAY_UNCERTAIN) == 0
+    assert np.array_equal(c2[certified], want[certified])
+    # invalid: part out of range, voxel outside the grid, voxel that is not a leaf
+    a = scene.assets[int(scene.part_asset[0])]
+    occupied = set(a.leaf_ids.tolist())
+    free = next(v for v in range(1 << (3 * a.depth)) if v not in occupied)
+    bad = _pack_hits([1.0, 1.0, 1.0, np.inf], [scene.n_parts, 0, 0, oracle.MISS_PART],
+                     [0, 1 << (3 * a.depth), free, oracle.MISS_VOXEL])
+    cb = gs.sc.hit_colors(torch.from_numpy(bad).cuda(), background=bg).cpu().numpy().view(np.uint32)
+    assert cb.tolist() == [g.COLOR_INVALID] * 3 + [bg]
+    with pytest.raises(g.SvoError):
+        gs.sc.hit_colors(hits, background=0x1000000)
+    torch.cuda.synchronize()

@@ -418,3 +418,31 @@ def test_rigid_scene_and_camera_invariant():
     assert np.array_equal(res["part"][ok], base["part"][ok])
     assert np.array_equal(res["voxel"][ok], base["voxel"][ok])
     assert ok.sum() > 300
+
+
+def test_hit_colors_closed_form_and_first_occurrence():
+    """Hit colours (Sec. IV-C): on a hash-coloured scene the colour of every hit
+    is the hash of the hit voxel's own coordinates; a duplicated id takes the
+    colour listed first; misses take the background; ids that are not leaves
+    are invalid."""
+    scene = synthetic.pr1_scene(depth=4)
+    so = oracle.SceneOracle(scene)
+    rays = synthetic.pr1_rays(scene, 48, 48)
+    ora = so.trace(rays)
+    col = so.hit_colors(ora, background=0x123456)
+    hit = ora["part"] != oracle.MISS_PART
+    assert hit.sum() > 100 and (~hit).sum() > 100
+    assert np.all(col[~hit] == 0x123456)
+    for i in np.nonzero(hit)[0]:
+        d = scene.assets[int(scene.part_asset[int(ora["part"][i])])].depth
+        x, y, z = synthetic.unpack_ids(np.array([ora["voxel"][i]]), d)
+        assert col[i] == synthetic.rgb_hash(x, y, z)[0]
+    # duplicates: the first listed colour wins; a non-leaf id and an unknown part are invalid
+    ids = synthetic.pack_ids(np.array([3, 1, 3, 2]), np.array([0, 0, 0, 5]), np.array([1, 1, 1, 7]), 3)
+    rgb = np.array([0xAA0000, 0x00BB00, 0x0000CC, 0x010203], dtype=np.uint32)
+    part = np.array([0, 0, 0, 0, 1, oracle.MISS_PART], dtype=np.uint32)
+    vox = np.array([ids[0], ids[1], ids[3], synthetic.pack_ids(4, 4, 4, 3), ids[0], 0], dtype=np.uint64)
+    got = oracle.hit_colors([(ids, rgb)], [0], part, vox, background=7)
+    assert got.tolist() == [0xAA0000, 0x00BB00, 0x010203, oracle.COLOR_INVALID, oracle.COLOR_INVALID, 7]
+    # an asset without colours gives 0 for its leaves
+    assert oracle.hit_colors([(ids, None)], [0], part[:1], vox[:1]).tolist() == [0]
