@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-requests", type=int, default=11000,
+                    help="served requests, the first min(1000, n/5) of them warm-up")
     ap.add_argument("--launch", default="", help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER instead of autotuning")
     return ap.parse_args()
 
@@ -162,7 +163,7 @@ def cpu_oracle_baseline(fig, poses, budget_s: float = 12.0) -> dict:
         so.trace(rays, local=poses[frames % FRAMES], threads=threads)
         done += rays.shape[0]
         frames += 1
-        if time.perf_counter() - t0 >= budget_s or frames >= FRAMES:
+        if time.perf_counter() - t0 >= budget_s or frames >= 4 * FRAMES:
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
@@ -472,7 +473,8 @@ def main() -> None:
     if extra:
         pool_handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
         batched = batched_section(g, ctx, bat, pool_handles, dev, reps=5, flush=flush)
-        serving = serving_section(g, ctx, srv, pool_handles, args.serve_requests, warm=args.serve_requests // 5,
+        serving = serving_section(g, ctx, srv, pool_handles, args.serve_requests,
+                                  warm=min(1000, args.serve_requests // 5),
                                   rate=2000.0)
 
     if rank == 0:

@@ -34,7 +34,7 @@ def lib():
         L.oracle_compose.restype = C.c_int
         L.oracle_invert.argtypes = [C.c_int, dp, dp]
         L.oracle_invert.restype = C.c_int
-        L.oracle_part_sphere.argtypes = [C.c_int, dp, dp]
+        L.oracle_part_sphere.argtypes = [C.c_int, dp, C.c_void_p, dp]
         L.oracle_part_sphere.restype = None
         L.oracle_ray_sphere.argtypes = [dp, dp, dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.oracle_ray_sphere.restype = C.c_int
@@ -74,11 +74,28 @@ def invert(world) -> np.ndarray:
     return inv
 
 
-def part_spheres(world) -> np.ndarray:
+def part_spheres(world, boxes=None) -> np.ndarray:
+    """Bounding sphere per part (Sec. IV-A) of the local box ``boxes[p] = (lo3,
+    hi3)`` of its content, or of the unit cube when ``boxes`` is None."""
     world = np.ascontiguousarray(world, dtype=np.float64).reshape(-1, 12)
     out = np.zeros((world.shape[0], 4))
-    lib().oracle_part_sphere(world.shape[0], world, out)
+    bx = None
+    if boxes is not None:
+        bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(world.shape[0], 6)
+    lib().oracle_part_sphere(world.shape[0], world, None if bx is None else bx.ctypes.data, out)
     return out
+
+
+def occupied_box(depth: int, leaf_ids) -> np.ndarray:
+    """Local box (lo3, hi3) of the occupied leaves of an asset: the cells'
+    min and max+1 corners over 2^depth; the unit cube for an empty asset."""
+    ids = np.asarray(leaf_ids, dtype=np.uint64)
+    if ids.size == 0:
+        return np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    m = np.uint64((1 << depth) - 1)
+    d = np.uint64(depth)
+    xyz = np.stack([ids & m, (ids >> d) & m, (ids >> (d + d)) & m], 1).astype(np.float64)
+    return np.concatenate([xyz.min(0), xyz.max(0) + 1.0]) / float(1 << depth)
 
 
 def ray_sphere(o, d, sphere4):
@@ -182,6 +199,11 @@ class SceneOracle:
     def __init__(self, scene):
         self.scene = scene
         self.assets = [OracleAsset(a.depth, a.leaf_ids) for a in scene.assets]
+
+    def boxes(self) -> np.ndarray:
+        """Occupied box of every part's asset, [P, 6]."""
+        b = [occupied_box(a.depth, a.leaf_ids) for a in self.scene.assets]
+        return np.array([b[int(i)] for i in self.scene.part_asset])
 
     def poses(self, local=None):
         local = self.scene.local if local is None else local

@@ -114,15 +114,22 @@ int oracle_invert(int n_parts, const double *world, double *inv) {
   return 0;
 }
 
-/* Bounding sphere of a part (Sec. IV-A): centre = image of the cube centre,
- * radius = largest distance from it to the image of a cube corner. */
-void oracle_part_sphere(int n_parts, const double *world, double *sphere4) {
+/* Bounding sphere of a part (Sec. IV-A) around the local box [lo, hi] of
+ * its content (box6 = lo[3], hi[3] per part; NULL = the unit cube):
+ * centre = image of the box centre, radius = largest distance from it to the
+ * image of a box corner.  Any box that holds every occupied leaf gives a
+ * sphere that culls no hit. */
+void oracle_part_sphere(int n_parts, const double *world, const double *box6, double *sphere4) {
   for (int p = 0; p < n_parts; ++p) {
     const double *m = world + 12 * p;
-    double c[3], r2 = 0.0;
-    for (int i = 0; i < 3; ++i) c[i] = 0.5 * (m[i * 4] + m[i * 4 + 1] + m[i * 4 + 2]) + m[i * 4 + 3];
+    const double lo[3] = {box6 ? box6[6 * p] : 0.0, box6 ? box6[6 * p + 1] : 0.0, box6 ? box6[6 * p + 2] : 0.0};
+    const double hi[3] = {box6 ? box6[6 * p + 3] : 1.0, box6 ? box6[6 * p + 4] : 1.0, box6 ? box6[6 * p + 5] : 1.0};
+    double mid[3], c[3], r2 = 0.0;
+    for (int i = 0; i < 3; ++i) mid[i] = 0.5 * (lo[i] + hi[i]);
+    for (int i = 0; i < 3; ++i) c[i] = m[i * 4] * mid[0] + m[i * 4 + 1] * mid[1] + m[i * 4 + 2] * mid[2] + m[i * 4 + 3];
     for (int corner = 0; corner < 8; ++corner) {
-      double q[3] = {(double)(corner & 1), (double)((corner >> 1) & 1), (double)((corner >> 2) & 1)};
+      double q[3] = {(corner & 1) ? hi[0] : lo[0], ((corner >> 1) & 1) ? hi[1] : lo[1],
+                     ((corner >> 2) & 1) ? hi[2] : lo[2]};
       double s = 0.0;
       for (int i = 0; i < 3; ++i) {
         double v = m[i * 4] * q[0] + m[i * 4 + 1] * q[1] + m[i * 4 + 2] * q[2] + m[i * 4 + 3] - c[i];

@@ -10,8 +10,11 @@
 //     coordinates of the FP32 sphere centre (FP64-accurate), and bounds on
 //     norms for the trace kernel's rounding-error bound;
 //  4. refit the part bounding spheres (Sec. IV-A: centre and radius follow
-//     from the pose): centre = image of the cube centre, radius = farthest
-//     image corner, rounded outward to FP32;
+//     from the pose).  The sphere bounds the asset's occupied box (the
+//     smallest grid-aligned box holding its leaves, found at upload) rather
+//     than its whole unit cube: centre = image of the box centre, radius =
+//     farthest image of a box corner, rounded outward to FP32.  Any sphere
+//     that holds every leaf culls no hit; the tighter one culls more rays;
 //  5. rebuild the cluster level of the sphere hierarchy: parts sorted by the
 //     Morton code of their sphere centres, runs of 8 enclosed by one sphere
 //     (the scene-level structure the paper proposes for many parts, Sec. V-E).
@@ -139,14 +142,22 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       double s = fabs((double)f[r * 4]) + fabs((double)f[r * 4 + 1]) + fabs((double)f[r * 4 + 2]);
       rowsum = fmax(rowsum, s);
     }
-    // sphere: centre = W (1/2,1/2,1/2), radius = farthest image corner
+    // sphere of the occupied box [lo, hi] (it holds every leaf of the part):
+    // centre = W (lo + hi) / 2, radius = farthest image of a box corner
+    const PartStatic &ps = a.stat[i];
+    double mid[3], ext[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      mid[q] = 0.5 * ((double)ps.box_lo[q] + (double)ps.box_hi[q]);
+      ext[q] = 0.5 * ((double)ps.box_hi[q] - (double)ps.box_lo[q]);
+    }
     double c[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) c[r] = 0.5 * (m[r * 4] + m[r * 4 + 1] + m[r * 4 + 2]) + m[r * 4 + 3];
+    for (int r = 0; r < 3; ++r) c[r] = m[r * 4] * mid[0] + m[r * 4 + 1] * mid[1] + m[r * 4 + 2] * mid[2] + m[r * 4 + 3];
     double r2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const double qx = (k & 1) ? 0.5 : -0.5, qy = (k & 2) ? 0.5 : -0.5, qz = (k & 4) ? 0.5 : -0.5;
+      const double qx = (k & 1) ? ext[0] : -ext[0], qy = (k & 2) ? ext[1] : -ext[1], qz = (k & 4) ? ext[2] : -ext[2];
       double s = 0.0;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -158,7 +169,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     const float cfx = (float)c[0], cfy = (float)c[1], cfz = (float)c[2];
     const double dcx = c[0] - cfx, dcy = c[1] - cfy, dcz = c[2] - cfz;
     const double rr = (sqrt(r2) + sqrt(dcx * dcx + dcy * dcy + dcz * dcz)) * (1.0 + 1e-12);
-    // local coordinates of the FP32 centre (close to (1/2, 1/2, 1/2))
+    // local coordinates of the FP32 centre (close to the box centre)
     float lc[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -168,7 +179,8 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     h.r0 = make_float4(f[0], f[1], f[2], lc[0]);
     h.r1 = make_float4(f[4], f[5], f[6], lc[1]);
     h.r2 = make_float4(f[8], f[9], f[10], lc[2]);
-    h.sphere = make_float4(cfx, cfy, cfz, ok ? __double2float_ru(rr) : -1.0f);
+    // a singular pose or an empty asset disables the sphere: no ray tests the part
+    h.sphere = make_float4(cfx, cfy, cfz, (ok && ps.n_nodes > 0) ? __double2float_ru(rr) : -1.0f);
     a.hot[i] = h;
     PartAux x;
     x.nodes = a.stat[i].nodes;

@@ -67,9 +67,11 @@ constexpr float kTau = 7.62939453125e-6f;      // 2^-17
 constexpr int kCap = 8;                         // candidate parts per pass
 constexpr int kSmemParts = 256;                 // parts staged in shared memory
 constexpr int kBlock = 128;  // block size of the FP64 pass; the trace kernel takes 64, 128 or 256
-#ifndef SVO_TRACE_MIN_BLOCKS
-#define SVO_TRACE_MIN_BLOCKS 1  // resident blocks per SM the register allocation must allow
-#endif
+// Resident threads per SM the trace kernel's register allocation must allow
+// (512 = 16 warps: at most 128 registers a thread).  Measured on the
+// articulated-figure frame: 0.353 ms with the compiler's own 163 registers
+// (12 warps), 0.327 ms at 128; 102 registers spill and lose again.
+constexpr int kTraceThreadsPerSM = 512;
 
 constexpr unsigned long long kRayBits = 40;
 
@@ -718,7 +720,7 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 }
 
 template <int NI, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, SVO_TRACE_MIN_BLOCKS) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+__global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);

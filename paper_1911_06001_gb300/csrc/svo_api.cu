@@ -54,6 +54,7 @@ struct AssetRec {
   uint64_t n_nodes = 0, n_leaves = 0;
   uint2 *d_nodes = nullptr;
   uint32_t *d_rgb = nullptr;
+  float box_lo[3] = {0.f, 0.f, 0.f}, box_hi[3] = {0.f, 0.f, 0.f};  // occupied leaves, local units
   int refs = 0;
 };
 
@@ -366,6 +367,10 @@ svo_status svo_upload(svo_ctx *ctx, const svo_desc *d, svo_handle *out) {
   a.depth = b.depth;
   a.n_nodes = b.n_nodes;
   a.n_leaves = b.n_leaves;
+  for (int k = 0; k < 3; ++k) {
+    a.box_lo[k] = (float)std::ldexp((double)b.box_lo[k], -b.depth);
+    a.box_hi[k] = (float)std::ldexp((double)b.box_hi[k], -b.depth);
+  }
   if (b.n_nodes) {
     cudaError_t e = cudaMalloc(&a.d_nodes, b.n_nodes * 8);
     if (e != cudaSuccess) return fail(SVO_ERR_OOM, "svo_upload: %llu nodes: %s", (unsigned long long)b.n_nodes,
@@ -435,6 +440,10 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
       stat[i].pad = 0;
       stat[i].rgb = a->d_rgb;
       stat[i].n_leaves = a->n_leaves;
+      for (int k = 0; k < 3; ++k) {
+        stat[i].box_lo[k] = a->box_lo[k];
+        stat[i].box_hi[k] = a->box_hi[k];
+      }
     }
   }
   int L = 0;

@@ -54,10 +54,17 @@ int build_octree(int depth, uint64_t n_in, const uint64_t *ids, const uint32_t *
   const uint64_t mask = (1ull << depth) - 1ull;
   std::vector<uint64_t> code(n_in);
   std::vector<uint32_t> src(n_in);
+  uint64_t lo[3] = {mask, mask, mask}, hi[3] = {0, 0, 0};
   for (uint64_t i = 0; i < n_in; ++i) {
     uint64_t v = ids[i];
     uint64_t x = v & mask, y = (v >> depth) & mask, z = (v >> (2 * depth)) & mask;
     if ((v >> (3 * depth)) != 0) return SVO_ERR_ARG;  // coordinates out of range
+    lo[0] = x < lo[0] ? x : lo[0];
+    lo[1] = y < lo[1] ? y : lo[1];
+    lo[2] = z < lo[2] ? z : lo[2];
+    hi[0] = x > hi[0] ? x : hi[0];
+    hi[1] = y > hi[1] ? y : hi[1];
+    hi[2] = z > hi[2] ? z : hi[2];
     code[i] = spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
     src[i] = (uint32_t)i;
   }
@@ -74,6 +81,10 @@ int build_octree(int depth, uint64_t n_in, const uint64_t *ids, const uint32_t *
   }
   out->n_leaves = lev.size();
   out->depth = depth;
+  for (int k = 0; k < 3; ++k) {
+    out->box_lo[k] = n_in ? (uint32_t)lo[k] : 0u;
+    out->box_hi[k] = n_in ? (uint32_t)hi[k] + 1u : 0u;
+  }
   // bottom-up: level l nodes are the distinct prefixes code >> 3 of level l+1
   std::vector<std::vector<uint32_t>> first(depth), cmask(depth);
   std::vector<size_t> count(depth + 1, 0);

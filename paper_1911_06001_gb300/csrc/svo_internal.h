@@ -33,6 +33,8 @@ struct PartStatic {
   int32_t pad;
   const uint32_t *rgb;  // leaf payload, indexed like the leaf-level children
   unsigned long long n_leaves;
+  float box_lo[3];      // local box of the occupied leaves (exact: multiples of 2^-depth);
+  float box_hi[3];      // the bounding sphere is fitted to it (empty asset: lo = hi = 0)
 };
 
 // Per-frame FP32 data of a part used by the trace kernel (64 B, staged in

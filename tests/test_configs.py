@@ -114,7 +114,6 @@ def test_precision_stress(ctx):
     got = gs.sc.read_poses()
     assert np.allclose(got["world"], world, rtol=0, atol=1e-12 * max(1.0, np.abs(world).max()))
     rng = np.random.default_rng(13)
-    spheres = oracle.part_spheres(world)
     n_total = 1 << 20
     n_graze = int(0.3 * n_total)
     per_cam = (n_total - n_graze) // len(prec.visible)

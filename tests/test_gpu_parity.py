@@ -63,8 +63,9 @@ def test_refit_matches_oracle(ctx, pr1):
     c32 = got["sphere"][:, :3].astype(np.float64)
     lc = np.einsum("pij,pj->pi", inv.reshape(-1, 3, 4)[:, :, :3], c32) + inv.reshape(-1, 3, 4)[:, :, 3]
     assert np.allclose(A32[:, :, 3], lc, rtol=0, atol=1e-6)
-    assert np.allclose(lc, 0.5, atol=1e-5)
-    sph = oracle.part_spheres(world)
+    boxes = so.boxes()
+    assert np.allclose(lc, 0.5 * (boxes[:, :3] + boxes[:, 3:]), atol=1e-5)  # the occupied box's centre
+    sph = oracle.part_spheres(world, boxes)
     dc = np.linalg.norm(got["sphere"][:, :3].astype(np.float64) - sph[:, :3], axis=1)
     r = got["sphere"][:, 3].astype(np.float64)
     assert np.all(dc + sph[:, 3] <= r)  # the FP32 sphere encloses the exact one

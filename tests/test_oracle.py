@@ -317,6 +317,42 @@ def test_part_sphere_encloses_and_is_tight():
     assert abs(oracle.part_spheres(rig[None])[0, 3] - math.sqrt(3) / 2) <= 1e-15
 
 
+def test_part_sphere_of_occupied_box():
+    """The sphere of a part's occupied box: closed forms for identity and rigid
+    poses; under any affine pose it holds every occupied leaf cell and one box
+    corner lies on it; the unit-cube box gives the plain part sphere."""
+    rng = np.random.default_rng(6)
+    # occupied box of a hand-made asset, depth 3: cells (1,2,5) and (6,3,2)
+    ids = synthetic.pack_ids(np.array([1, 6]), np.array([2, 3]), np.array([5, 2]), 3)
+    box = oracle.occupied_box(3, ids)
+    assert box.tolist() == [1 / 8, 2 / 8, 2 / 8, 7 / 8, 4 / 8, 6 / 8]
+    assert oracle.occupied_box(3, np.zeros(0, np.uint64)).tolist() == [0, 0, 0, 1, 1, 1]
+    lo, hi = box[:3], box[3:]
+    s = oracle.part_spheres(synthetic.affine12(np.eye(3), np.zeros(3))[None], box[None])[0]
+    assert np.allclose(s[:3], (lo + hi) / 2, rtol=0, atol=1e-15)
+    assert abs(s[3] - np.linalg.norm(hi - lo) / 2) <= 1e-15
+    R = _random_rotation(rng)
+    s = oracle.part_spheres(synthetic.affine12(R, np.array([3.0, -1.0, 2.0]))[None], box[None])[0]
+    assert abs(s[3] - np.linalg.norm(hi - lo) / 2) <= 1e-14
+    assert np.allclose(s[:3], R @ ((lo + hi) / 2) + np.array([3.0, -1.0, 2.0]), rtol=0, atol=1e-14)
+    a = synthetic.make_asset(5, synthetic.noise_voxels(5, 0.01, rng))
+    abox = oracle.occupied_box(5, a.leaf_ids)
+    for _ in range(10):
+        W = synthetic.affine12(_random_affine(rng), rng.uniform(-3, 3, 3))
+        s = oracle.part_spheres(W[None], abox[None])[0]
+        M = W.reshape(3, 4)
+        x, y, z = synthetic.unpack_ids(a.leaf_ids, 5)
+        cells = np.stack([x, y, z], 1).astype(np.float64)
+        for k in range(8):
+            corner = (cells + np.array([k & 1, (k >> 1) & 1, (k >> 2) & 1])) / 32.0
+            assert np.all(np.linalg.norm(corner @ M[:, :3].T + M[:, 3] - s[:3], axis=1) <= s[3] * (1 + 1e-12))
+        bc = np.array([[abox[3 * (k & 1)], abox[1 + 3 * ((k >> 1) & 1)], abox[2 + 3 * ((k >> 2) & 1)]]
+                       for k in range(8)])
+        assert abs(np.linalg.norm(bc @ M[:, :3].T + M[:, 3] - s[:3], axis=1).max() - s[3]) <= 1e-12
+        assert np.array_equal(oracle.part_spheres(W[None], np.array([[0, 0, 0, 1, 1, 1.0]]))[0],
+                              oracle.part_spheres(W[None])[0])
+
+
 # ------------------------------------------------------------------ Eq. 4
 
 def test_ray_sphere_eq4_against_sampled_distance():
