@@ -108,8 +108,7 @@ typedef struct {
   unsigned long long parts_entered; /* (ray, part) traversals started */
   unsigned long long nodes_visited; /* interior node descriptors fetched (8 B each) */
   unsigned long long leaves_tested; /* leaf cells slab-tested */
-  unsigned long long passes;        /* candidate-list passes of the rays some part sphere admits
-                                       (more than one per ray only when a list overflows) */
+  unsigned long long passes;        /* candidate-list passes (> rays when lists overflow) */
   unsigned long long flag_winner;   /* flagged because the nearest candidate was not certainly hit */
   unsigned long long flag_overlap;  /* flagged because another candidate's entry bound reached it */
   unsigned long long flag_width;    /* ids certified, but the winner's t interval was too wide (T_REFINED) */
@@ -227,8 +226,7 @@ svo_status scene_read_clusters(svo_scene *scene, int32_t *n_clusters, float *sph
  * SVO_RAY_T_REFINED; with SVO_TRACE_FP64_FIX both are re-intersected in FP64.  The scene must have been
  * refitted since its last scene_set_transforms.  If n exceeds the largest n
  * traced so far on this context the call grows the context's scratch with
- * cudaMalloc, so call it once at full size before capturing a CUDA graph.
- * At most 2^32 - 1 rays per call (per item of trace_batch): SVO_ERR_LIMIT. */
+ * cudaMalloc, so call it once at full size before capturing a CUDA graph. */
 svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits, uint32_t *ray_flags,
                       uint32_t flags, svo_trace_stats *stats, void *stream);
 /* (With SVO_TRACE_ORDER_DIR / _ORIGIN the rays are first counting-sorted by a

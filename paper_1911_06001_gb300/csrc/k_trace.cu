@@ -719,87 +719,10 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
   }
 }
 
-// Loads one ray (two float4, streamed) into the per-ray working set.  Rays
-// with a non-finite component, a zero or non-finite |d|^2, or tmin > tmax are
-// inactive: they are reported as misses.
-__device__ __forceinline__ bool load_ray(const TraceItem &I, unsigned long long ray, RayW &r) {
-  const float4 o = __ldcs(&I.rays[2 * ray]);
-  const float4 d = __ldcs(&I.rays[2 * ray + 1]);
-  r.ox = o.x;
-  r.oy = o.y;
-  r.oz = o.z;
-  r.tmin = o.w;
-  r.dx = d.x;
-  r.dy = d.y;
-  r.dz = d.z;
-  r.tmax = d.w;
-  const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
-  const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
-                      isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dd > 0.f && isfinite(dd);
-  r.inv_dd = 1.0f / dd;
-  r.inv_len = rsqrtf(dd);
-  r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
-  return finite && (o.w <= d.w);
-}
-
-__device__ __forceinline__ void idle_ray(RayW &r) {
-  r.ox = r.oy = r.oz = r.dx = r.dy = r.dz = 0.f;
-  r.tmin = 0.f;
-  r.tmax = -1.f;
-  r.inv_dd = 0.f;
-  r.inv_len = 0.f;
-  r.onorm = 0.f;
-}
-
-// Whether trace_ray_f32 would descend any part for this ray: the same sphere
-// tests without the sorted list (a lane stops at its first surviving part).
-// Every lane of the warp calls it (the cluster vote uses the full mask).
-__device__ __forceinline__ bool any_candidate(const RayW &r, bool active, uint32_t flags, int P, int NC,
-                                              const PartHot *__restrict__ hot, const Cluster *__restrict__ cl,
-                                              const int32_t *__restrict__ order) {
-  if (!(flags & SVO_TRACE_CULL)) return active;  // the plain trace descends every part
-  bool found = false;
-  if (flags & SVO_TRACE_SORT) {
-    for (int c = 0; c < NC; ++c) {
-      const bool hc = active && !found && cluster_cull(r, cl[c]);
-      if (__ballot_sync(0xffffffffu, hc) == 0u) continue;
-      if (hc) {
-        const uint32_t fc = __float_as_uint(cl[c].aux.w);
-        const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
-        for (int k = 0; k < count && !found; ++k) {
-          float tin, tref;
-          found = part_cull(r, hot[order[first + k]], tin, tref);
-        }
-      }
-    }
-  } else {
-    for (int p = 0; p < P && active && !found; ++p) {
-      float tin, tref;
-      found = part_cull(r, hot[p], tin, tref);
-    }
-  }
-  return found;
-}
-
-// Ray indices a warp can hold between its culling and tracing rounds: fewer
-// than 32 waiting plus one whole tile.
-__host__ __device__ constexpr int queue_cap(int rays_per_lane) { return 32 * rays_per_lane + 32; }
-
-// Persistent trace kernel.  Each warp alternates two rounds:
-//   fill:  claim tiles of 32 * rays_per_lane rays from the device counter and
-//          run only the sphere tests; a ray no part can hit is written as a
-//          miss at once, the others are queued (ray index, shared memory)
-//          until 32 are waiting;
-//   trace: the 32 queued rays, one per lane, go through the full path (cull,
-//          depth sort, descents, certification, FP64 list).
-// The queue holds rays of one item at a time (a tile of another item waits
-// until the queue drains).  Queued rays are exactly those the full path would
-// descend, so results do not depend on the compaction; it only keeps the
-// descents' lanes busy (most primary rays miss every part sphere).
 template <int NI, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // [tables | traversal stacks, level-major | staged part tables | ray queues]
+  // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
   uint2 *sStack = reinterpret_cast<uint2 *>(smem + kTablesBytes) + threadIdx.x;
   const int sp = L.one_scene ? L.items[0].n_parts : 0;
@@ -808,9 +731,6 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
-  const int rpl = L.rays_per_lane;
-  const int qcap = queue_cap(rpl);
-  uint32_t *q = reinterpret_cast<uint32_t *>(sOrd + sp) + (threadIdx.x >> 5) * qcap;
   load_tables(tab);
   if (L.one_scene) {
     const TraceItem &I0 = L.items[0];
@@ -826,153 +746,121 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   uint32_t n_rays = 0, n_flag = 0;
   const int lane = threadIdx.x & 31;
-  const bool staged = L.one_scene != 0;
-  constexpr unsigned long long kNone = ~0ull;
-  int qn = 0, qit = 0;  // warp-uniform: queued rays and their item
-  unsigned long long held = kNone;
-  bool exhausted = false;
   for (;;) {
-    // ---- fill: sphere tests only, misses written, candidates queued
-    while (qn < 32 && !exhausted) {
-      unsigned long long tile;
-      if (held != kNone) {
-        tile = held;
-        held = kNone;
-      } else {
-        tile = 0;
-        if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= L.n_tiles) {
-          exhausted = true;
-          break;
-        }
-      }
-      const int it = find_item(L, tile);
-      if (qn > 0 && it != qit) {  // another item: trace the queue first
-        held = tile;
-        break;
-      }
-      qit = it;
-      const TraceItem &I = L.items[it];
-      const PartHot *hot = staged ? sHot : I.hot;
-      const Cluster *cls = staged ? sCl : I.clusters;
-      const int32_t *ord = staged ? sOrd : I.order;
-      const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
-#pragma unroll 1
-      for (int j = 0; j < rpl; ++j) {
-        const unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
-        const bool in_range = slot_i < I.n;
-        const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
-        RayW r;
-        bool active = false;
-        if (in_range)
-          active = load_ray(I, ray, r);
-        else
-          idle_ray(r);
-        if (STATS && in_range) ++n_rays;
-        const bool cand = any_candidate(r, active, L.flags, I.n_parts, I.n_clusters, hot, cls, ord);
-        if (in_range && !cand) {
-          __stcs(&I.hits[ray], make_uint4(0x7f800000u, kMissPart, 0xFFFFFFFFu, 0xFFFFFFFFu));
-          if (I.ray_flags) I.ray_flags[ray] = 0u;
-        }
-        const unsigned int m = __ballot_sync(0xffffffffu, cand);
-        if (cand) q[qn + __popc(m & ((1u << lane) - 1u))] = (uint32_t)ray;
-        qn += __popc(m);
-      }
-      __syncwarp();
-    }
-    if (qn == 0) {
-      if (exhausted) break;
-      continue;
-    }
-    // ---- trace: up to 32 queued rays, one per lane
-    const int take = qn < 32 ? qn : 32;
-    const int it = qit;
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= L.n_tiles) break;
+    const int it = find_item(L, tile);
     const TraceItem &I = L.items[it];
+    const int P = I.n_parts, NC = I.n_clusters;
+    const bool staged = L.one_scene != 0;
     const PartHot *hot = staged ? sHot : I.hot;
     const PartAux *aux = staged ? sAux : I.aux;
     const Cluster *cls = staged ? sCl : I.clusters;
     const int32_t *ord = staged ? sOrd : I.order;
-    const bool in_range = lane < take;
-    const unsigned long long ray = in_range ? (unsigned long long)q[lane] : 0ull;
-    RayW r;
-    bool active = false;
-    if (in_range)
-      active = load_ray(I, ray, r);
-    else
-      idle_ray(r);
-    CertState st;
-    Contenders con;
-    trace_ray_f32<STATS, BLOCK>(r, active, L.flags, I.n_parts, I.n_clusters, hot, aux, cls, ord, tab, sStack, st,
-                                con, err, cnt);
-    bool flagged = false, ids_ok = true;
-    if (in_range) {
-      float t = Num<float>::inf();
-      uint32_t part = kMissPart;
-      unsigned long long vox = kMissVoxel;
-      if (st.part1 != kMissPart) {
-        // the reported t lies in [lo1, hi1]; its error is at most half the width
-        const float scale = fmaxf(st.lo1, aux[st.part1].hdiag * r.inv_len);
-        const bool w_ok = st.cert1 != 0u;
-        const bool o_ok = st.lo2 > st.hi1;
-        const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
-        ids_ok = w_ok && o_ok;
-        flagged = !(ids_ok && t_ok);
-        if (STATS) {
-          cnt.f_winner += w_ok ? 0u : 1u;
-          cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
-          cnt.f_width += (ids_ok && !t_ok) ? 1u : 0u;
-        }
-        t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
-        if (!st.cert1) t = st.te1;
-        part = st.part1;
-        vox = st.vox1;
+    const int rpl = L.rays_per_lane;
+    const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
+#pragma unroll 1
+    for (int j = 0; j < rpl; ++j) {
+      const unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
+      const bool in_range = slot_i < I.n;
+      const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
+      bool active = in_range;
+      RayW r;
+      if (active) {
+        const float4 o = __ldcs(&I.rays[2 * ray]);
+        const float4 d = __ldcs(&I.rays[2 * ray + 1]);
+        r.ox = o.x;
+        r.oy = o.y;
+        r.oz = o.z;
+        r.tmin = o.w;
+        r.dx = d.x;
+        r.dy = d.y;
+        r.dz = d.z;
+        r.tmax = d.w;
+        const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
+        const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
+                            isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dd > 0.f && isfinite(dd);
+        r.inv_dd = 1.0f / dd;
+        r.inv_len = rsqrtf(dd);
+        r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
+        active = finite && (o.w <= d.w);
+        if (STATS) ++n_rays;
+      } else {
+        r.ox = r.oy = r.oz = r.dx = r.dy = r.dz = 0.f;
+        r.tmin = 0.f;
+        r.tmax = -1.f;
+        r.inv_dd = 0.f;
+        r.inv_len = 0.f;
+        r.onorm = 0.f;
       }
-      uint4 hv;
-      hv.x = __float_as_uint(t);
-      hv.y = part;
-      hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
-      hv.w = (uint32_t)(vox >> 32);
-      __stcs(&I.hits[ray], hv);
-      if (I.ray_flags) I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? SVO_RAY_T_REFINED : 0u);
-      if (STATS && !ids_ok) ++n_flag;
-    }
-    // compact flagged rays for the FP64 pass (one atomic per warp)
-    if (L.flags & SVO_TRACE_FP64_FIX) {
-      const unsigned int m = __ballot_sync(0xffffffffu, flagged);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        unsigned int basei = 0;
-        if (lane == leader) basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
-        basei = __shfl_sync(0xffffffffu, basei, leader);
-        if (flagged) {
-          const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
-          if (slot < L.fix_capacity) {
-            // contenders still in play (lo <= hi_min); none stored = full FP64 retrace
-            unsigned long long nc = 0;
-            if (!con.overflow && slot < L.cand_capacity) {
-              for (int cq = 0; cq < con.n; ++cq) {
-                if (!(con.lo[cq] <= st.hi_min)) continue;
-                L.fix_cand[slot * kContenders + nc] =
-                    make_uint4(con.part[cq], (uint32_t)(con.vox[cq] & 0xFFFFFFFFull), (uint32_t)(con.vox[cq] >> 32),
-                               __float_as_uint(con.lo[cq]));
-                ++nc;
+      CertState st;
+      Contenders con;
+      trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
+      bool flagged = false, ids_ok = true;
+      if (in_range) {
+        float t = Num<float>::inf();
+        uint32_t part = kMissPart;
+        unsigned long long vox = kMissVoxel;
+        if (st.part1 != kMissPart) {
+          // the reported t lies in [lo1, hi1]; its error is at most half the width
+          const float scale = fmaxf(st.lo1, aux[st.part1].hdiag * r.inv_len);
+          const bool w_ok = st.cert1 != 0u;
+          const bool o_ok = st.lo2 > st.hi1;
+          const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
+          ids_ok = w_ok && o_ok;
+          flagged = !(ids_ok && t_ok);
+          if (STATS) {
+            cnt.f_winner += w_ok ? 0u : 1u;
+            cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
+            cnt.f_width += (ids_ok && !t_ok) ? 1u : 0u;
+          }
+          t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
+          if (!st.cert1) t = st.te1;
+          part = st.part1;
+          vox = st.vox1;
+        }
+        uint4 hv;
+        hv.x = __float_as_uint(t);
+        hv.y = part;
+        hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
+        hv.w = (uint32_t)(vox >> 32);
+        __stcs(&I.hits[ray], hv);
+        if (I.ray_flags) I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? SVO_RAY_T_REFINED : 0u);
+        if (STATS && !ids_ok) ++n_flag;
+      }
+      // compact flagged rays for the FP64 pass (one atomic per warp)
+      if (L.flags & SVO_TRACE_FP64_FIX) {
+        const unsigned int m = __ballot_sync(0xffffffffu, flagged);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          unsigned int basei = 0;
+          if (lane == leader) basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
+          basei = __shfl_sync(0xffffffffu, basei, leader);
+          if (flagged) {
+            const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
+            if (slot < L.fix_capacity) {
+              // contenders still in play (lo <= hi_min); none stored = full FP64 retrace
+              unsigned long long nc = 0;
+              if (!con.overflow && slot < L.cand_capacity) {
+                for (int q = 0; q < con.n; ++q) {
+                  if (!(con.lo[q] <= st.hi_min)) continue;
+                  L.fix_cand[slot * kContenders + nc] =
+                      make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull), (uint32_t)(con.vox[q] >> 32),
+                                 __float_as_uint(con.lo[q]));
+                  ++nc;
+                }
               }
+              const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
+              L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
+            } else {
+              err |= kErrFixOverflow;
             }
-            const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
-            L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
-          } else {
-            err |= kErrFixOverflow;
           }
         }
       }
     }
-
-    __syncwarp();
-    // the rays not taken move to the front of the queue
-    for (int k = 32 + lane; k < qn; k += 32) q[k - 32] = q[k];
-    __syncwarp();
-    qn -= take;
   }
   if (STATS) flush_stats(L.stats, cnt, n_rays, n_flag);
   if (err) atomicOr(L.err, err);
@@ -1066,16 +954,15 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, int rays_per_lane) {
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block) {
   return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
-         clusters * sizeof(Cluster) + parts * sizeof(int32_t) +
-         (size_t)(block / 32) * queue_cap(rays_per_lane) * sizeof(uint32_t);
+         clusters * sizeof(Cluster) + parts * sizeof(int32_t);
 }
 
 template <int NI, int BLOCK>
 cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
   const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
-                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK, L.rays_per_lane);
+                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK);
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
   auto kern = stats ? k_trace<NI, true, BLOCK> : k_trace<NI, false, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -663,8 +663,7 @@ svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits
   if (!rays || !hits) return fail(SVO_ERR_ARG, "trace_rays: rays/hits is NULL");
   if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
     return fail(SVO_ERR_ARG, "trace_rays: rays and hits must be 16-byte aligned");
-  if (n > 0xFFFFFFFFull) return fail(SVO_ERR_LIMIT, "trace_rays: %llu rays (at most 2^32 - 1 per call)",
-                                    (unsigned long long)n);
+  if (n >= (1ull << 40)) return fail(SVO_ERR_LIMIT, "trace_rays: %llu rays", (unsigned long long)n);
   if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_rays: STATS without stats buffer");
   CK(cudaSetDevice(s->ctx->device));
   TraceLaunch *L = new TraceLaunch();
@@ -708,11 +707,6 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
           (reinterpret_cast<uintptr_t>(it.hits) & 15)) {
         delete L;
         return fail(SVO_ERR_ARG, "trace_batch: item %d rays/hits NULL or not 16-byte aligned", b + i);
-      }
-      if (it.n > 0xFFFFFFFFull) {
-        delete L;
-        return fail(SVO_ERR_LIMIT, "trace_batch: item %d has %llu rays (at most 2^32 - 1)", b + i,
-                    (unsigned long long)it.n);
       }
       TraceItem ti = make_item(it.scene, it.rays, it.n, it.hits, it.ray_flags);
       ti.tile_begin = tiles;

@@ -298,8 +298,7 @@ def test_stats_counters(ctx, pr1):
     assert s["flag_width"] == int(((flags & 4) != 0).sum())
     assert s["fixed"] == s["flagged"] + s["flag_width"] == int(((flags & 2) != 0).sum())
     assert s["nodes_visited"] > 0 and s["parts_entered"] <= s["parts_tested"]
-    # only rays some sphere admits reach the sorted pass; misses end at the sphere pre-test
-    assert 0 < s["passes"] <= s["rays"]
+    assert s["passes"] >= s["rays"]
 
 
 def test_articulated_full_size_sampled(ctx):
