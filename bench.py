@@ -337,10 +337,11 @@ def main() -> None:
     sc.refit()
     if args.launch:
         b, r, o = args.launch.split(",")
-        tuned = {"block": int(b), "rays_per_lane": int(r), "order": o, "ms": None, "default_ms": None}
+        tuned = {"block": int(b), "rays_per_lane": int(r), "order": o, "ms": None, "default_ms": None,
+                 "image_width": WIDTH}
         autotune.apply(ctx, tuned)
     else:
-        tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3)
+        tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3, image_width=WIDTH)
     order = autotune.order_flag(tuned)
     flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX | order
 

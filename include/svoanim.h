@@ -72,6 +72,10 @@ typedef int32_t svo_status;
                                    trace_fix_pending (lets a caller time the two passes apart) */
 #define SVO_TRACE_ORDER_DIR 32u    /* trace rays in an order grouped by direction (results unchanged) */
 #define SVO_TRACE_ORDER_ORIGIN 64u /* ... grouped by origin cell, then direction (results unchanged) */
+#define SVO_TRACE_IMAGE_TILES 128u /* rays are the pixels of a row-major image whose width is in bits
+                                      16..31 of flags: warps take 8 x 4 pixel tiles instead of 32
+                                      consecutive rays (results unchanged; ignored with ORDER_*) */
+#define SVO_TRACE_IMAGE(width) (SVO_TRACE_IMAGE_TILES | ((uint32_t)(width) << 16))
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 
 /* per-ray flags written when ray_flags != NULL */
@@ -130,6 +134,8 @@ typedef struct {
   uint64_t n;          /* number of rays */
   svo_hit *hits;       /* device, n entries */
   uint32_t *ray_flags; /* device, n entries, or NULL */
+  uint32_t image_width; /* rays are a row-major image of this width (0: no image layout); it
+                           replaces the width bits of the trace_batch flags for this item */
 } svo_batch_item;
 
 /* ---------------------------------------------------------------- context */

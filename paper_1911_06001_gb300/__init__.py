@@ -27,9 +27,11 @@ from ._lib import (  # noqa: F401
     TRACE_ORDER_DIR,
     TRACE_ORDER_ORIGIN,
     TRACE_FP64_FIX,
+    TRACE_IMAGE_TILES,
     TRACE_SORT,
     TRACE_STATS,
     SvoError,
+    trace_image,
 )
 
 MISS_PART = 0xFFFFFFFF
@@ -106,11 +108,14 @@ class Context:
         _lib.check(self.lib.svo_check_device(self.h))
 
     def trace_batch(self, items, flags: int = TRACE_DEFAULT, stats=None, stream=None) -> None:
-        """items: list of (scene, rays, hits, ray_flags-or-None) with device tensors."""
+        """items: list of (scene, rays, hits, ray_flags-or-None[, image_width]) with device tensors;
+        image_width > 0 says the item's rays are a row-major image of that width."""
         arr = (_lib.SvoBatchItem * max(len(items), 1))()
-        for i, (sc, rays, hits, rf) in enumerate(items):
+        for i, item in enumerate(items):
+            sc, rays, hits, rf = item[:4]
+            width = int(item[4]) if len(item) > 4 else 0
             arr[i] = _lib.SvoBatchItem(sc.h.value, rays.data_ptr(), rays.shape[0], hits.data_ptr(),
-                                       0 if rf is None else rf.data_ptr())
+                                       0 if rf is None else rf.data_ptr(), width)
         _lib.check(self.lib.trace_batch(self.h, arr, len(items), int(flags), _ptr(stats), _stream_ptr(stream)))
 
     def raygen(self, eye, target, width: int, height: int, fov_y_deg: float = 60.0, up=(0.0, 1.0, 0.0),

@@ -22,7 +22,15 @@ TRACE_STATS = 8
 TRACE_DEFER_FIX = 16
 TRACE_ORDER_DIR = 32
 TRACE_ORDER_ORIGIN = 64
+TRACE_IMAGE_TILES = 128
 TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
+
+
+def trace_image(width: int) -> int:
+    """Flag bits saying the rays are a row-major image of ``width`` pixels (warps take 8 x 4 tiles)."""
+    if not 0 < int(width) < 65536:
+        raise ValueError("image width must be in 1..65535")
+    return TRACE_IMAGE_TILES | (int(width) << 16)
 
 RAY_UNCERTAIN = 1
 RAY_FIXED = 2
@@ -61,7 +69,7 @@ class SvoCamera(C.Structure):
 
 class SvoBatchItem(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("rays", C.c_void_p), ("n", C.c_uint64), ("hits", C.c_void_p),
-                ("ray_flags", C.c_void_p)]
+                ("ray_flags", C.c_void_p), ("image_width", C.c_uint32)]
 
 
 class SvoError(RuntimeError):

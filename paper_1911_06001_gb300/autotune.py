@@ -3,7 +3,8 @@
 Knobs that change only speed, never results: the trace kernel's block size
 (64 / 128 / 256 threads), the rays each lane takes per warp tile (1 / 2 / 4 /
 8) and the ray order (as given, grouped by direction, grouped by origin cell
-then direction).  ``tune`` times every combination on the caller's rays with
+then direction, or -- for rays that are the pixels of an image -- warp tiles
+of 8 x 4 pixels).  ``tune`` times every combination on the caller's rays with
 CUDA events (L2 flushed between repetitions), keeps the fastest, and can
 remember it in a JSON cache under a caller-chosen key (for example the scene
 and ray-batch shape).
@@ -17,12 +18,12 @@ import os
 
 import numpy as np
 
-from . import TRACE_DEFAULT, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN, Context
+from . import TRACE_DEFAULT, TRACE_IMAGE_TILES, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN, Context, trace_image
 
 BLOCKS = (64, 128, 256)
 RAYS_PER_LANE = (1, 2, 4, 8)
-ORDERS = {"none": 0, "dir": TRACE_ORDER_DIR, "origin": TRACE_ORDER_ORIGIN}
-_ORDER_BITS = TRACE_ORDER_DIR | TRACE_ORDER_ORIGIN
+ORDERS = {"none": 0, "dir": TRACE_ORDER_DIR, "origin": TRACE_ORDER_ORIGIN, "image": TRACE_IMAGE_TILES}
+_ORDER_BITS = TRACE_ORDER_DIR | TRACE_ORDER_ORIGIN | TRACE_IMAGE_TILES | 0xFFFF0000
 
 
 def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> float:
@@ -41,10 +42,11 @@ def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> floa
 
 
 def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, blocks=BLOCKS,
-         rays_per_lane=RAYS_PER_LANE, orders=tuple(ORDERS), cache_path: str | None = None,
-         key: str | None = None) -> dict:
+         rays_per_lane=RAYS_PER_LANE, orders=None, cache_path: str | None = None,
+         key: str | None = None, image_width: int = 0) -> dict:
     """Time every (block, rays_per_lane, order) on ``rays`` (CUDA [n, 8]) traced
-    against ``scene``; apply and return the fastest."""
+    against ``scene``; apply and return the fastest.  The "image" order is
+    tried only when ``image_width`` (row-major pixels) is given."""
     import torch
 
     if cache_path and key:
@@ -52,13 +54,15 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
         if cached:
             apply(ctx, cached)
             return cached
+    if orders is None:
+        orders = tuple(o for o in ORDERS if o != "image" or image_width > 0)
     hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
     old = ctx.trace_config()
     table = []
     for b, r, o in itertools.product(blocks, rays_per_lane, orders):
         ctx.set_trace_config(b, r)
-        f = (flags & ~_ORDER_BITS) | ORDERS[o]
+        f = (flags & ~_ORDER_BITS) | _flag(o, image_width)
         table.append({"block": b, "rays_per_lane": r, "order": o, "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
     best = min(table, key=lambda x: x["ms"])
@@ -66,6 +70,7 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
     result = dict(best)
     result["default_ms"] = default["ms"] if default else None
     result["n_rays"] = int(rays.shape[0])
+    result["image_width"] = int(image_width)
     result["table"] = table
     apply(ctx, result)
     if cache_path and key:
@@ -78,14 +83,18 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
     return result
 
 
+def _flag(order: str, image_width: int) -> int:
+    return trace_image(image_width) if order == "image" else ORDERS[order]
+
+
 def apply(ctx: Context, cfg: dict) -> int:
     """Set the tuned launch shape on ``ctx``; returns the order flag to OR into trace flags."""
     ctx.set_trace_config(int(cfg["block"]), int(cfg["rays_per_lane"]))
-    return ORDERS[cfg["order"]]
+    return order_flag(cfg)
 
 
 def order_flag(cfg: dict) -> int:
-    return ORDERS[cfg["order"]]
+    return _flag(cfg["order"], int(cfg.get("image_width", 0)))
 
 
 def load(cache_path: str) -> dict:

@@ -81,12 +81,11 @@ struct Tables {
 };
 constexpr size_t kTablesBytes = (sizeof(Tables) + 15) & ~size_t(15);
 
-__device__ __forceinline__ void perm_axes(int p, int &a0, int &a1, int &a2) {
+__host__ __device__ constexpr void perm_axes(int p, int &a0, int &a1, int &a2) {
   // p = 2*rank_x + (rank_y > rank_z)
   const int rx = p >> 1;
   const bool z_first = (p & 1) != 0;
-  int r[3];
-  r[0] = rx;
+  int r[3] = {rx, 0, 0};
   const int lo = (rx == 0) ? 1 : 0, hi = (rx == 2) ? 1 : 2;
   r[1] = z_first ? hi : lo;
   r[2] = z_first ? lo : hi;
@@ -94,6 +93,20 @@ __device__ __forceinline__ void perm_axes(int p, int &a0, int &a1, int &a2) {
   a1 = (r[0] == 1) ? 0 : (r[1] == 1 ? 1 : 2);
   a2 = (r[0] == 2) ? 0 : (r[1] == 2 ? 1 : 2);
 }
+
+// perm_axes packed: bits [6p + 2r, 6p + 2r + 2) hold the axis of rank r under
+// order p.
+constexpr unsigned long long pack_axis_order() {
+  unsigned long long v = 0;
+  for (int p = 0; p < 6; ++p) {
+    int a0 = 0, a1 = 0, a2 = 0;
+    perm_axes(p, a0, a1, a2);
+    v |= (unsigned long long)(a0 | (a1 << 2) | (a2 << 4)) << (6 * p);
+  }
+  return v;
+}
+constexpr unsigned long long kAxisOrder = pack_axis_order();
+static_assert(kAxisOrder == 0x1894a1624ull, "axis order table");
 
 __device__ void build_tables(Tables *t) {
   for (int e = threadIdx.x; e < 8 * 6 * 256; e += blockDim.x) {
@@ -350,9 +363,10 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
   uint32_t px = 0, py = 0, pz = 0;
   uint2 desc = __ldg(&nodes[0]);
   if (STATS) ++cnt.nodes;
-  bool down = true;
+  // While-while loop: lanes of a warp descend together, then pop together
+  // (a lane that has to pop waits for the others to finish descending).
   for (;;) {
-    if (down) {
+    for (;;) {  // descend while the current node has children to visit
       const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
       const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
       const R tl = rel_bound(st, tmax, tshift);
@@ -380,10 +394,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       hit &= (Bz <= Cy) ? 0xFFu : ~(HZ & ~HY);
       const uint32_t cmask = desc.y & 0xFFu;
       hit &= cmask;
-      if (hit == 0u) {
-        down = false;
-        continue;
-      }
+      if (hit == 0u) break;
       const bool cxy = Bx <= By, cxz = Bx <= Bz, cyz = By <= Bz;
       const int rx = (cxy ? 0 : 1) + (cxz ? 0 : 1);
       const int ry = (cxy ? 1 : 0) + (cyz ? 0 : 1);
@@ -425,8 +436,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
             offer(st, lo, part, vox);
           }
         }
-        down = false;
-        continue;
+        break;
       }
       const int q = __ffs(hq) - 1;
       const uint32_t rest = hq & (hq - 1u);
@@ -444,7 +454,8 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       py = 2u * py + ((m >> 1) & 1u);
       pz = 2u * pz + ((m >> 2) & 1u);
       ++level;
-    } else {
+    }
+    for (;;) {  // pop to the next sibling that may still hold the closest hit
       if (level == 0) return;
       --level;
       px >>= 1;
@@ -461,9 +472,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
       const R T0 = fmax(fmax(Slab<R>::t(lx - eta, ix, ox, bx), Slab<R>::t(ly - eta, iy, oy, by)), fmax(Slab<R>::t(lz - eta, iz, oz, bz), tmin));
       const int rank = 31 - __clz(q);
-      int a0, a1, a2;
-      perm_axes(p, a0, a1, a2);
-      const int ax = rank == 0 ? a0 : (rank == 1 ? a1 : a2);
+      const int ax = (int)((kAxisOrder >> (6 * p + 2 * rank)) & 3ull);
       const R Bsel = ax == 0 ? Slab<R>::t((lx + h) - eta, ix, ox, bx) : (ax == 1 ? Slab<R>::t((ly + h) - eta, iy, oy, by) : Slab<R>::t((lz + h) - eta, iz, oz, bz));
       const R en = fmax(T0, Bsel);
       if (en > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
@@ -482,7 +491,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       py = 2u * py + ((m >> 1) & 1u);
       pz = 2u * pz + ((m >> 2) & 1u);
       ++level;
-      down = true;
+      break;
     }
   }
 }
@@ -763,8 +772,18 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
     const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
 #pragma unroll 1
     for (int j = 0; j < rpl; ++j) {
-      const unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
-      const bool in_range = slot_i < I.n;
+      unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
+      bool in_range = slot_i < I.n;
+      if (I.tiles_x) {
+        // image layout: the tile is a block of 8 x 4*rpl pixels
+        const uint32_t T = (uint32_t)(tile - I.tile_begin);
+        const uint32_t ty = T / I.tiles_x, tx = T - ty * I.tiles_x;
+        const uint32_t k = (uint32_t)(j * 32 + lane);
+        const uint32_t x = tx * 8u + (k & 7u);
+        const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);
+        slot_i = y * I.width + x;
+        in_range = x < I.width && slot_i < I.n;
+      }
       const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
       bool active = in_range;
       RayW r;
@@ -782,7 +801,7 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
         const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
         const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
                             isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dd > 0.f && isfinite(dd);
-        r.inv_dd = 1.0f / dd;
+        r.inv_dd = __frcp_rn(dd);  // the correctly rounded 1 / dd
         r.inv_len = rsqrtf(dd);
         r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
         active = finite && (o.w <= d.w);

@@ -168,6 +168,8 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.n_parts = s->P;
   it.n_clusters = s->NC;
   it.max_depth = s->max_depth;
+  it.width = 0;
+  it.tiles_x = 0;
   it.pad = 0;
   return it;
 }
@@ -204,6 +206,7 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
       off += (order_scratch_bytes(L.items[i].n) + 255) & ~size_t(255);
     }
   }
+  L.n_tiles = layout_tiles(L.items, L.n_items, ctx->rays_per_lane);
   L.tile_counter = slot->d_counters;
   L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
   L.fix_list = slot->d_fix;
@@ -668,11 +671,10 @@ svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits
   CK(cudaSetDevice(s->ctx->device));
   TraceLaunch *L = new TraceLaunch();
   L->items[0] = make_item(s, rays, n, hits, ray_flags);
+  if (flags & SVO_TRACE_IMAGE_TILES) L->items[0].width = flags >> 16;
   L->n_items = 1;
   L->flags = flags;
   L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
-  const unsigned long long tile = 32ull * s->ctx->rays_per_lane;
-  L->n_tiles = (n + tile - 1) / tile;
   const float4 *bounds[1] = {s->d_bound};
   svo_status rc = run_trace(s->ctx, *L, n, bounds, stream);
   delete L;
@@ -685,12 +687,11 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
   if (n_items < 0) return fail(SVO_ERR_ARG, "trace_batch: n_items < 0");
   if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_batch: STATS without stats buffer");
   CK(cudaSetDevice(ctx->device));
-  const unsigned long long tile = 32ull * ctx->rays_per_lane;
   for (int b = 0; b < n_items; b += kMaxBatchItems) {
     const int cnt = (n_items - b) < kMaxBatchItems ? (n_items - b) : kMaxBatchItems;
     TraceLaunch *L = new TraceLaunch();
     L->n_items = 0;
-    unsigned long long tiles = 0, total = 0;
+    unsigned long long total = 0;
     const float4 *bounds[kMaxBatchItems];
     for (int i = 0; i < cnt; ++i) {
       const svo_batch_item &it = items[b + i];
@@ -709,8 +710,7 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
         return fail(SVO_ERR_ARG, "trace_batch: item %d rays/hits NULL or not 16-byte aligned", b + i);
       }
       TraceItem ti = make_item(it.scene, it.rays, it.n, it.hits, it.ray_flags);
-      ti.tile_begin = tiles;
-      tiles += (it.n + tile - 1) / tile;
+      ti.width = it.image_width;
       total += it.n;
       bounds[L->n_items] = it.scene->d_bound;
       L->items[L->n_items++] = ti;
@@ -718,7 +718,6 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
     if (L->n_items > 0) {
       L->flags = flags;
       L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
-      L->n_tiles = tiles;
       svo_status rc = run_trace(ctx, *L, total, bounds, stream);
       if (rc != SVO_OK) {
         delete L;

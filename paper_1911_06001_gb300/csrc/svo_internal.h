@@ -79,8 +79,37 @@ struct TraceItem {
   int32_t n_parts;
   int32_t n_clusters;
   int32_t max_depth;  // deepest asset among the scene's parts
+  uint32_t width;     // rays are a row-major image of this width (tiles of 8 x 4*rays_per_lane pixels), or 0
+  uint32_t tiles_x;   // tiles per image row band (width > 0)
   int32_t pad;
 };
+
+// Warp tiles of every item, laid out one item after another: sets each
+// item's tile_begin (and tiles_x) and returns the total.  A tile is
+// 32 * rays_per_lane consecutive rays, or, for an image of width >= 8, a block
+// of 8 x 4*rays_per_lane pixels (the last row band and column may be partial).
+template <typename Item>
+inline unsigned long long layout_tiles(Item *items, int n_items, int rays_per_lane) {
+  unsigned long long tiles = 0;
+  const unsigned long long tile = 32ull * (unsigned long long)rays_per_lane;
+  for (int i = 0; i < n_items; ++i) {
+    Item &it = items[i];
+    it.tile_begin = tiles;
+    it.tiles_x = 0;
+    unsigned long long t = (it.n + tile - 1) / tile;
+    if (it.width >= 8u && !it.perm) {
+      const unsigned long long tx = (it.width + 7ull) / 8ull, rows = (it.n + it.width - 1) / it.width;
+      const unsigned long long band = 4ull * (unsigned long long)rays_per_lane;
+      const unsigned long long t2 = tx * ((rows + band - 1) / band);
+      if (t2 < (1ull << 32)) {
+        t = t2;
+        it.tiles_x = (uint32_t)tx;
+      }
+    }
+    tiles += t;
+  }
+  return tiles;
+}
 
 struct TraceLaunch {
   TraceItem items[kMaxBatchItems];

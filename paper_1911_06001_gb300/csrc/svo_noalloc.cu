@@ -97,6 +97,7 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   TraceLaunch launch;  // on the stack: no host heap either
   TraceLaunch *L = &launch;
   L->items[0] = scene_item(s, rays, n, hits, ray_flags);
+  if (flags & SVO_TRACE_IMAGE_TILES) L->items[0].width = flags >> 16;
   L->n_items = 1;
   L->flags = flags;
   L->stats = nullptr;
@@ -104,8 +105,7 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   scene_trace_config(s, &block, &rpl);
   L->block = block;
   L->rays_per_lane = rpl;
-  const unsigned long long tile = 32ull * rpl;
-  L->n_tiles = (n + tile - 1) / tile;
+  L->n_tiles = layout_tiles(L->items, 1, rpl);
   L->tile_counter = reinterpret_cast<unsigned long long *>(base);
   L->fix_count = reinterpret_cast<unsigned int *>(base + sizeof(unsigned long long));
   L->fix_list = reinterpret_cast<unsigned long long *>(base + kCounterBytes);

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import TRACE_DEFAULT, Context
+from . import TRACE_DEFAULT, Context, trace_image
 
 RAY_BYTES = 32
 HIT_BYTES = 16
@@ -179,7 +179,7 @@ class Server:
             hits = s.hits[t.offset:t.offset + t.n_rays]
             self.ctx.raygen(tuple(float(v) for v in r.eye), tuple(float(v) for v in r.target), int(r.width),
                             int(r.height), 60.0, rays=rays, stream=s.stream)
-            items.append((inst, rays, hits, None))
+            items.append((inst, rays, hits, None, int(r.width)))
             t.hits = hits
             t.slot = si
             t.submitted = now
@@ -222,7 +222,7 @@ def render_alone(ctx: Context, scene_handle, request, flags: int = TRACE_DEFAULT
     scene_handle.refit(stream=stream)
     rays = ctx.raygen(tuple(float(v) for v in request.eye), tuple(float(v) for v in request.target),
                       int(request.width), int(request.height), 60.0, stream=stream)
-    hits = scene_handle.trace(rays, flags=flags, stream=stream)
+    hits = scene_handle.trace(rays, flags=flags | trace_image(int(request.width)), stream=stream)
     return rays, hits
 
 

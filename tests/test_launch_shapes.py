@@ -53,6 +53,43 @@ def test_every_launch_shape_gives_identical_hits(ctx):
         ctx.set_trace_config(128, 3)
 
 
+def test_image_tiles_give_identical_hits(ctx):
+    """Warp tiles of 8 x 4*rays_per_lane pixels (rays given as a row-major
+    image) on ragged widths and a ragged last row, alone and per batch item:
+    every ray is traced exactly once with the same result."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    s = synthetic.pr1_scene()
+    gs = GpuScene(ctx, s)
+    rng = np.random.default_rng(9)
+    rays = np.concatenate([synthetic.pr1_rays(s)[:11000], synthetic.random_rays(2117, rng, (-3,) * 3, (3,) * 3)])
+    ctx.set_trace_config(128, 4)
+    ref = gs.trace(rays, g.TRACE_DEFAULT)
+    for width in (1, 7, 8, 13, 128, 333, 4096, 65535):
+        for rpl in (1, 2, 8):
+            ctx.set_trace_config(64, rpl)
+            _same(gs.trace(rays, g.TRACE_DEFAULT | g.trace_image(width)), ref)
+    # the ordering flags take precedence over the image layout
+    _same(gs.trace(rays, g.TRACE_DEFAULT | g.TRACE_ORDER_DIR | g.trace_image(128)), ref)
+    ctx.set_trace_config(128, 1)
+    rt = torch.from_numpy(np.ascontiguousarray(rays, dtype=np.float32)).cuda()
+    items, outs = [], []
+    for lo, hi, w in ((0, 5000, 100), (5000, 5001, 8), (5001, rays.shape[0], 0)):
+        h = torch.empty((hi - lo, 2), dtype=torch.int64, device="cuda")
+        f = torch.zeros(hi - lo, dtype=torch.int32, device="cuda")
+        items.append((gs.sc, rt[lo:hi], h, f, w))
+    ctx.trace_batch(items)
+    torch.cuda.synchronize()
+    got = {k: np.concatenate([g.decode_hits(it[2])[k] for it in items]) for k in ("t", "part", "voxel")}
+    got["flags"] = np.concatenate([it[3].cpu().numpy().astype(np.uint32) for it in items])
+    _same(got, ref)
+    ctx.set_trace_config(128, 4)
+    with pytest.raises(ValueError):
+        g.trace_image(0)
+
+
 def test_autotune_picks_a_valid_shape_and_caches_it(ctx, tmp_path):
     import torch
 
