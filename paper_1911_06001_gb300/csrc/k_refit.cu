@@ -59,40 +59,89 @@ __device__ __forceinline__ unsigned int spread10(unsigned int v) {
   return v;
 }
 
+// Shared-memory layout of one refit: every per-part intermediate stays on
+// chip, so the phases below chain no global-memory round trips (the block
+// is alone on its SM and latency-bound).
+struct RefitSmem {
+  double *world;             // P x 12
+  float4 *sph;               // P
+  float4 *cl;                // clusters
+  unsigned long long *key;   // P
+  float *na;                 // P
+  int32_t *ord;              // P
+  int32_t *parent;           // P
+  int32_t *lorder;           // P
+  int32_t *lstart;           // levels + 1
+  float *red;                // 6 x threads
+};
+
+__host__ __device__ inline size_t refit_smem_bytes(int P, int NC, int L, int nthr) {
+  return (size_t)P * (12 * sizeof(double) + sizeof(unsigned long long) + sizeof(float4) + sizeof(float) +
+                      3 * sizeof(int32_t)) +
+         (size_t)NC * sizeof(float4) + (size_t)(L + 1) * sizeof(int32_t) + 6 * (size_t)nthr * sizeof(float) + 64;
+}
+
+__device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L, int nthr) {
+  RefitSmem m;
+  // 16-byte items first: every offset stays aligned for any P
+  m.world = reinterpret_cast<double *>(base);
+  m.sph = reinterpret_cast<float4 *>(m.world + 12 * P);
+  m.cl = m.sph + P;
+  m.key = reinterpret_cast<unsigned long long *>(m.cl + NC);
+  m.na = reinterpret_cast<float *>(m.key + P);
+  m.ord = reinterpret_cast<int32_t *>(m.na + P);
+  m.parent = m.ord + P;
+  m.lorder = m.parent + P;
+  m.lstart = m.lorder + P;
+  m.red = reinterpret_cast<float *>(m.lstart + L + 1);
+  return m;
+}
+
 template <bool INLINE>
 __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses poses) {
   const int P = a.n_parts;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
-  __shared__ unsigned long long s_key[kMaxParts];
-  __shared__ float s_red[6][kRefitThreads];
+  extern __shared__ __align__(16) unsigned char refit_smem[];
+  const RefitSmem sm = carve(refit_smem, P, a.n_clusters, a.n_levels, nthr);
   if (INLINE) {
     // keep the device copy of the local poses in step with what is composed
     for (int k = tid; k < P * 12; k += nthr) const_cast<double *>(a.local)[k] = poses.local[k];
   }
   const double *local = INLINE ? poses.local : a.local;
+  // tree topology to shared memory (independent loads, one round trip)
+  for (int i = tid; i < P; i += nthr) {
+    sm.parent[i] = a.stat[i].parent;
+    sm.lorder[i] = a.level_order[i];
+  }
+  for (int i = tid; i <= a.n_levels; i += nthr) sm.lstart[i] = a.level_start[i];
+  __syncthreads();
 
   // 1. compose, level by level (parents are on earlier levels)
   for (int L = 0; L < a.n_levels; ++L) {
-    const int b = a.level_start[L], e = a.level_start[L + 1];
+    const int b = sm.lstart[L], e = sm.lstart[L + 1];
     for (int j = b + tid; j < e; j += nthr) {
-      const int i = a.level_order[j];
-      const int p = a.stat[i].parent;
+      const int i = sm.lorder[j];
+      const int p = sm.parent[i];
       const double *Li = local + 12 * i;
-      double *Wi = a.world + 12 * i;
+      double *Wi = sm.world + 12 * i;
+      double out[12];
       if (p < 0) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) Wi[k] = Li[k];
+        for (int k = 0; k < 12; ++k) out[k] = Li[k];
       } else {
-        double Wp[12], L12[12], out[12];
+        double Wp[12], L12[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-          Wp[k] = a.world[12 * p + k];
+          Wp[k] = sm.world[12 * p + k];
           L12[k] = Li[k];
         }
         compose_affine(Wp, L12, out);
+      }
 #pragma unroll
-        for (int k = 0; k < 12; ++k) Wi[k] = out[k];
+      for (int k = 0; k < 12; ++k) {
+        Wi[k] = out[k];
+        a.world[12 * i + k] = out[k];
       }
     }
     __syncthreads();
@@ -103,7 +152,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
   for (int i = tid; i < P; i += nthr) {
     double m[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) m[k] = a.world[12 * i + k];
+    for (int k = 0; k < 12; ++k) m[k] = sm.world[12 * i + k];
     const double A0 = m[0], A1 = m[1], A2 = m[2], A3 = m[4], A4 = m[5], A5 = m[6], A6 = m[8], A7 = m[9],
                  A8 = m[10];
     const double c00 = A4 * A8 - A5 * A7, c01 = A5 * A6 - A3 * A8, c02 = A3 * A7 - A4 * A6;
@@ -182,6 +231,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     // a singular pose or an empty asset disables the sphere: no ray tests the part
     h.sphere = make_float4(cfx, cfy, cfz, (ok && ps.n_nodes > 0) ? __double2float_ru(rr) : -1.0f);
     a.hot[i] = h;
+    sm.sph[i] = h.sphere;
     PartAux x;
     x.nodes = a.stat[i].nodes;
     x.n_nodes = a.stat[i].n_nodes;
@@ -199,6 +249,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       x.hdiag = (float)(sqrt(dg) * ldexp(1.0, -a.stat[i].depth));
     }
     a.aux[i] = x;
+    sm.na[i] = x.n_ainv;
     mn[0] = fminf(mn[0], cfx);
     mn[1] = fminf(mn[1], cfy);
     mn[2] = fminf(mn[2], cfz);
@@ -209,37 +260,38 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
   // bounding box of the sphere centres (block reduction)
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    s_red[k][tid] = mn[k];
-    s_red[3 + k][tid] = mx[k];
+    sm.red[k * nthr + tid] = mn[k];
+    sm.red[(3 + k) * nthr + tid] = mx[k];
   }
   __syncthreads();
   for (int w = nthr / 2; w > 0; w >>= 1) {
     if (tid < w) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        s_red[k][tid] = fminf(s_red[k][tid], s_red[k][tid + w]);
-        s_red[3 + k][tid] = fmaxf(s_red[3 + k][tid], s_red[3 + k][tid + w]);
+        sm.red[k * nthr + tid] = fminf(sm.red[k * nthr + tid], sm.red[k * nthr + tid + w]);
+        sm.red[(3 + k) * nthr + tid] = fmaxf(sm.red[(3 + k) * nthr + tid], sm.red[(3 + k) * nthr + tid + w]);
       }
     }
     __syncthreads();
   }
-  const float bx0 = s_red[0][0], by0 = s_red[1][0], bz0 = s_red[2][0];
-  const float ex = fmaxf(s_red[3][0] - bx0, 1e-30f), ey = fmaxf(s_red[4][0] - by0, 1e-30f),
-              ez = fmaxf(s_red[5][0] - bz0, 1e-30f);
+  const float bx0 = sm.red[0], by0 = sm.red[nthr], bz0 = sm.red[2 * nthr];
+  const float bx1 = sm.red[3 * nthr], by1 = sm.red[4 * nthr], bz1 = sm.red[5 * nthr];
+  const float ex = fmaxf(bx1 - bx0, 1e-30f), ey = fmaxf(by1 - by0, 1e-30f), ez = fmaxf(bz1 - bz0, 1e-30f);
   // 5. Morton keys and a rank sort (P <= kMaxParts)
   for (int i = tid; i < P; i += nthr) {
-    const float4 s = a.hot[i].sphere;
+    const float4 s = sm.sph[i];
     const unsigned int qx = (unsigned int)fminf(fmaxf((s.x - bx0) / ex * 1023.0f, 0.0f), 1023.0f);
     const unsigned int qy = (unsigned int)fminf(fmaxf((s.y - by0) / ey * 1023.0f, 0.0f), 1023.0f);
     const unsigned int qz = (unsigned int)fminf(fmaxf((s.z - bz0) / ez * 1023.0f, 0.0f), 1023.0f);
     const unsigned int mc = spread10(qx) | (spread10(qy) << 1) | (spread10(qz) << 2);
-    s_key[i] = ((unsigned long long)mc << 11) | (unsigned long long)i;
+    sm.key[i] = ((unsigned long long)mc << 11) | (unsigned long long)i;
   }
   __syncthreads();
   for (int i = tid; i < P; i += nthr) {
-    const unsigned long long k = s_key[i];
+    const unsigned long long k = sm.key[i];
     int rank = 0;
-    for (int j = 0; j < P; ++j) rank += (s_key[j] < k) ? 1 : 0;
+    for (int j = 0; j < P; ++j) rank += (sm.key[j] < k) ? 1 : 0;
+    sm.ord[rank] = i;
     a.order[rank] = i;
   }
   __syncthreads();
@@ -250,8 +302,8 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     float na = 0.f;
     bool any = false;
     for (int k = 0; k < cnt; ++k) {
-      const int p = a.order[first + k];
-      const float4 s = a.hot[p].sphere;
+      const int p = sm.ord[first + k];
+      const float4 s = sm.sph[p];
       if (s.w < 0.f) continue;
       any = true;
       lo[0] = fmin(lo[0], (double)s.x - s.w);
@@ -260,7 +312,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       hi[0] = fmax(hi[0], (double)s.x + s.w);
       hi[1] = fmax(hi[1], (double)s.y + s.w);
       hi[2] = fmax(hi[2], (double)s.z + s.w);
-      na = fmaxf(na, a.aux[p].n_ainv);
+      na = fmaxf(na, sm.na[p]);
     }
     Cluster cl;
     if (any) {
@@ -268,8 +320,8 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       const float Cx = (float)C[0], Cy = (float)C[1], Cz = (float)C[2];
       double R = 0.0;
       for (int k = 0; k < cnt; ++k) {
-        const int p = a.order[first + k];
-        const float4 s = a.hot[p].sphere;
+        const int p = sm.ord[first + k];
+        const float4 s = sm.sph[p];
         if (s.w < 0.f) continue;
         const double dx = (double)s.x - Cx, dy = (double)s.y - Cy, dz = (double)s.z - Cz;
         R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz) + (double)s.w);
@@ -280,14 +332,15 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     }
     cl.aux = make_float4(na, 0.f, 0.f, __uint_as_float((unsigned int)first | ((unsigned int)cnt << 16)));
     a.clusters[cidx] = cl;
+    sm.cl[cidx] = cl.sphere;
   }
   __syncthreads();
   if (tid == 0) {
     // a sphere around all cluster spheres: the frame of origin-based ray ordering
-    const float Cx = 0.5f * (bx0 + s_red[3][0]), Cy = 0.5f * (by0 + s_red[4][0]), Cz = 0.5f * (bz0 + s_red[5][0]);
+    const float Cx = 0.5f * (bx0 + bx1), Cy = 0.5f * (by0 + by1), Cz = 0.5f * (bz0 + bz1);
     float R = 0.f;
     for (int c = 0; c < a.n_clusters; ++c) {
-      const float4 s = a.clusters[c].sphere;
+      const float4 s = sm.cl[c];
       if (s.w < 0.f) continue;
       const float dx = s.x - Cx, dy = s.y - Cy, dz = s.z - Cz;
       R = fmaxf(R, sqrtf(dx * dx + dy * dy + dz * dz) + s.w);
@@ -300,13 +353,18 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
 
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
   const int threads = a.n_parts <= 32 ? 32 : kRefitThreads;
+  const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, threads);
   if (host_local && a.n_parts <= kInlinePoseParts) {
     InlinePoses p;
     for (int k = 0; k < a.n_parts * 12; ++k) p.local[k] = host_local[k];
-    k_refit<true><<<1, threads, 0, stream>>>(a, p);
+    cudaError_t e = cudaFuncSetAttribute(k_refit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_refit<true><<<1, threads, smem, stream>>>(a, p);
   } else {
     static const InlinePoses none = {};
-    k_refit<false><<<1, threads, 0, stream>>>(a, none);
+    cudaError_t e = cudaFuncSetAttribute(k_refit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_refit<false><<<1, threads, smem, stream>>>(a, none);
   }
   return cudaGetLastError();
 }

@@ -887,12 +887,41 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
 
 // ------------------------------------------------------------- FP64 pass
 
+// Lexicographic minimum of (t, part, voxel) across the warp (every lane
+// returns it).
+__device__ __forceinline__ void warp_min(ExactState &s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ExactState x;
+    x.t = __shfl_xor_sync(0xffffffffu, s.t, o);
+    x.part = __shfl_xor_sync(0xffffffffu, s.part, o);
+    x.vox = __shfl_xor_sync(0xffffffffu, s.vox, o);
+    offer(s, x.t, x.part, x.vox);
+  }
+}
+
+__device__ __forceinline__ void write_fixed(const TraceItem &I, unsigned long long ray, const ExactState &st,
+                                            uint32_t why) {
+  uint4 hv;
+  hv.x = __float_as_uint((float)st.t);
+  hv.y = st.part;
+  hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
+  hv.w = (uint32_t)(st.vox >> 32);
+  I.hits[ray] = hv;
+  if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
+}
+
 // Re-intersects the rays the FP32 pass flagged, in FP64 and without
-// certification: every part whose (conservative FP32) bounding-sphere test
-// passes and whose sphere entry is not beyond the best hit so far is descended
-// with the exact closed-box rule, keeping the lexicographic minimum of
-// (t, part, voxel).  List entries are dealt round-robin over the blocks so
-// that a short list still spreads over the whole GPU.
+// certification.  One warp per flagged ray:
+//   * with a contender list (the leaves that may still be the closest hit),
+//     lane q intersects contender q with the exact closed-box rule and a warp
+//     reduction keeps the lexicographic minimum of (t, part, voxel);
+//   * without one (the list overflowed), lane 0 re-traces the ray: the FP32
+//     descent with inflated boxes, every leaf reached decided in FP64.
+// GB300 issues FP64 at 2 lanes per clock per SM, so spreading a ray's
+// contenders over lanes (instead of one lane looping over them) cuts the
+// pass's latency by the contender count.  List entries are dealt round-robin
+// over the warps so that a short list still spreads over the whole GPU.
 template <int NI>
 __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLaunchT<NI> L) {
   __shared__ __align__(16) Tables tab;
@@ -901,8 +930,10 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   unsigned int err = 0;
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   const unsigned long long n = min((unsigned long long)*L.fix_count, L.fix_capacity);
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = blockIdx.x + (unsigned long long)gridDim.x * threadIdx.x; i < n; i += stride) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
+  const unsigned long long warp = blockIdx.x + (unsigned long long)gridDim.x * (threadIdx.x >> 5);
+  for (unsigned long long i = warp; i < n; i += n_warps) {
     const unsigned long long e = L.fix_list[i];
     const int nc = (int)(e >> 48);
     const uint32_t why = ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN;
@@ -911,62 +942,53 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     const TraceItem &I = L.items[it];
     const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
     if (nc > 0) {
-      // the FP32 pass narrowed the ray to nc contender leaves: intersect each in FP64
+      // the FP32 pass narrowed the ray to nc contender leaves: one per lane
       ExactState st;
       st.t = Num<double>::inf();
       st.part = kMissPart;
       st.vox = kMissVoxel;
-      for (int q = 0; q < nc; ++q) {
-        const uint4 cv = L.fix_cand[i * kContenders + q];
+      if (lane < nc && lane < kContenders) {
+        const uint4 cv = L.fix_cand[i * kContenders + lane];
         const uint32_t p = cv.x;
         const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
         double tq;
         if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
       }
-      uint4 hv;
-      hv.x = __float_as_uint((float)st.t);
-      hv.y = st.part;
-      hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
-      hv.w = (uint32_t)(st.vox >> 32);
-      I.hits[ray] = hv;
-      if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
+      warp_min(st);
+      if (lane == 0) write_fixed(I, ray, st, why);
       continue;
     }
-    RayW r;
-    r.ox = o.x;
-    r.oy = o.y;
-    r.oz = o.z;
-    r.tmin = o.w;
-    r.dx = d.x;
-    r.dy = d.y;
-    r.dz = d.z;
-    r.tmax = d.w;
-    r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
-    r.inv_len = 0.f;
-    r.onorm = 0.f;
-    HybridState hs;
-    hs.ex.t = Num<double>::inf();
-    hs.ex.part = kMissPart;
-    hs.ex.vox = kMissVoxel;
-    hs.o = o;
-    hs.d = d;
-    uint2 stk_local[kMaxDepth];
-    for (int p = 0; p < I.n_parts; ++p) {
-      float tin, tref;
-      if (!part_cull(r, I.hot[p], tin, tref)) continue;
-      if (tin > __double2float_ru(hs.ex.t)) continue;  // every candidate of p starts after the best hit
-      hs.inv64 = I.inv64 + 12 * p;
-      trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, &tab, stk_local, hs, nullptr,
-                                            err, cnt);
+    if (lane == 0) {  // the other lanes wait: the next entry is warp-wide again
+      RayW r;
+      r.ox = o.x;
+      r.oy = o.y;
+      r.oz = o.z;
+      r.tmin = o.w;
+      r.dx = d.x;
+      r.dy = d.y;
+      r.dz = d.z;
+      r.tmax = d.w;
+      r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
+      r.inv_len = 0.f;
+      r.onorm = 0.f;
+      HybridState hs;
+      hs.ex.t = Num<double>::inf();
+      hs.ex.part = kMissPart;
+      hs.ex.vox = kMissVoxel;
+      hs.o = o;
+      hs.d = d;
+      uint2 stk_local[kMaxDepth];
+      for (int p = 0; p < I.n_parts; ++p) {
+        float tin, tref;
+        if (!part_cull(r, I.hot[p], tin, tref)) continue;
+        if (tin > __double2float_ru(hs.ex.t)) continue;  // every candidate of p starts after the best hit
+        hs.inv64 = I.inv64 + 12 * p;
+        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, &tab, stk_local, hs, nullptr,
+                                              err, cnt);
+      }
+      write_fixed(I, ray, hs.ex, why);
     }
-    const ExactState &st = hs.ex;
-    uint4 hv;
-    hv.x = __float_as_uint((float)st.t);
-    hv.y = st.part;
-    hv.z = (uint32_t)(st.vox & 0xFFFFFFFFull);
-    hv.w = (uint32_t)(st.vox >> 32);
-    I.hits[ray] = hv;
-    if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
+    __syncwarp();
   }
   // count fixed rays once per launch
   if (L.stats && blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);
