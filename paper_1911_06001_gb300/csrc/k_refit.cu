@@ -31,9 +31,12 @@ namespace {
 
 constexpr int kRefitThreads = 256;  // block size for large scenes; one warp for <= 32 parts
 
-// Poses passed by value in the kernel parameters (no host-to-device copy).
+// Poses passed by value in the kernel parameters (no host-to-device copy),
+// in size classes so that a small scene's launch carries a small parameter
+// block (the whole block is fetched before the kernel starts).
+template <int CAP>
 struct InlinePoses {
-  double local[kInlinePoseParts * 12];
+  double local[CAP * 12];
 };
 
 __device__ __forceinline__ void compose_affine(const double *p, const double *q, double *out) {
@@ -97,8 +100,8 @@ __device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L, int
   return m;
 }
 
-template <bool INLINE>
-__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses poses) {
+template <bool INLINE, int CAP>
+__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses<CAP> poses) {
   const int P = a.n_parts;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
@@ -351,22 +354,26 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
 
 }  // namespace
 
+template <bool INLINE, int CAP>
+cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, int threads, size_t smem,
+                           cudaStream_t stream) {
+  InlinePoses<CAP> p;
+  if (INLINE)
+    for (int k = 0; k < a.n_parts * 12; ++k) p.local[k] = host_local[k];
+  cudaError_t e = cudaFuncSetAttribute(k_refit<INLINE, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_refit<INLINE, CAP><<<1, threads, smem, stream>>>(a, p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
+  static_assert(kInlinePoseParts == 256, "size classes below");
   const int threads = a.n_parts <= 32 ? 32 : kRefitThreads;
   const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, threads);
-  if (host_local && a.n_parts <= kInlinePoseParts) {
-    InlinePoses p;
-    for (int k = 0; k < a.n_parts * 12; ++k) p.local[k] = host_local[k];
-    cudaError_t e = cudaFuncSetAttribute(k_refit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_refit<true><<<1, threads, smem, stream>>>(a, p);
-  } else {
-    static const InlinePoses none = {};
-    cudaError_t e = cudaFuncSetAttribute(k_refit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_refit<false><<<1, threads, smem, stream>>>(a, none);
-  }
-  return cudaGetLastError();
+  if (host_local && a.n_parts <= 16) return launch_refit_t<true, 16>(a, host_local, threads, smem, stream);
+  if (host_local && a.n_parts <= 64) return launch_refit_t<true, 64>(a, host_local, threads, smem, stream);
+  if (host_local && a.n_parts <= 256) return launch_refit_t<true, 256>(a, host_local, threads, smem, stream);
+  return launch_refit_t<false, 1>(a, nullptr, threads, smem, stream);
 }
 
 }  // namespace svo
