@@ -13,11 +13,19 @@
 //     from the pose).  The sphere bounds the asset's occupied box (the
 //     smallest grid-aligned box holding its leaves, found at upload) rather
 //     than its whole unit cube: centre = image of the box centre, radius =
-//     farthest image of a box corner, rounded outward to FP32.  Any sphere
-//     that holds every leaf culls no hit; the tighter one culls more rays;
+//     farthest image of a box corner.  Any sphere that holds every leaf culls
+//     no hit; the tighter one culls more rays;
 //  5. rebuild the cluster level of the sphere hierarchy: parts sorted by the
 //     Morton code of their sphere centres, runs of 8 enclosed by one sphere
 //     (the scene-level structure the paper proposes for many parts, Sec. V-E).
+//
+// GB300 issues FP64 at about two lanes per clock per SM, so one warp's FP64
+// instruction occupies a sub-partition for ~64 clocks whatever its active
+// lanes.  The kernel therefore (a) spreads the FP64 work of a part over
+// three lanes (one matrix row each) and the parts over all eight warps, and
+// (b) keeps FP64 for what must be exact -- compose, inverse, sphere centre
+// and its local coordinates -- and computes the radii and norms in FP32 with
+// upward-rounded error bounds, which only ever enlarge them.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -29,7 +37,10 @@ namespace svo {
 
 namespace {
 
-constexpr int kRefitThreads = 256;  // block size for large scenes; one warp for <= 32 parts
+constexpr int kRefitThreads = 256;  // 8 warps: every FP64 sub-partition of the SM gets work
+constexpr int kRefitWarps = kRefitThreads / 32;
+constexpr int kQuadsPerPass = kRefitThreads / 4;  // parts handled at once (4 lanes each, 3 busy)
+constexpr float kRelSlack = 9.5367431640625e-7f;   // 2^-20: covers FP32 rounding of the norms below
 
 // Poses passed by value in the kernel parameters (no host-to-device copy),
 // in size classes so that a small scene's launch carries a small parameter
@@ -39,20 +50,6 @@ struct InlinePoses {
   double local[CAP * 12];
 };
 
-__device__ __forceinline__ void compose_affine(const double *p, const double *q, double *out) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    double r0 = p[i * 4 + 0] * q[0] + p[i * 4 + 1] * q[4] + p[i * 4 + 2] * q[8];
-    double r1 = p[i * 4 + 0] * q[1] + p[i * 4 + 1] * q[5] + p[i * 4 + 2] * q[9];
-    double r2 = p[i * 4 + 0] * q[2] + p[i * 4 + 1] * q[6] + p[i * 4 + 2] * q[10];
-    double r3 = p[i * 4 + 0] * q[3] + p[i * 4 + 1] * q[7] + p[i * 4 + 2] * q[11] + p[i * 4 + 3];
-    out[i * 4 + 0] = r0;
-    out[i * 4 + 1] = r1;
-    out[i * 4 + 2] = r2;
-    out[i * 4 + 3] = r3;
-  }
-}
-
 __device__ __forceinline__ unsigned int spread10(unsigned int v) {
   v &= 0x3FFu;
   v = (v | (v << 16)) & 0x030000FFu;
@@ -60,6 +57,15 @@ __device__ __forceinline__ unsigned int spread10(unsigned int v) {
   v = (v | (v << 4)) & 0x030C30C3u;
   v = (v | (v << 2)) & 0x09249249u;
   return v;
+}
+
+// Thread of the j-th item (part) of a pass: item j -> warp j % 8, lane group
+// j / 8, so that even a handful of parts lands on every warp.  Returns the
+// item handled by thread t and the lane r (0..3) inside its group of four.
+__device__ __forceinline__ int quad_item(int t, int &r) {
+  const int w = t >> 5, l = t & 31;
+  r = l & 3;
+  return (l >> 2) * kRefitWarps + w;
 }
 
 // Shared-memory layout of one refit: every per-part intermediate stays on
@@ -84,7 +90,7 @@ __host__ __device__ inline size_t refit_smem_bytes(int P, int NC, int L, int nth
          (size_t)NC * sizeof(float4) + (size_t)(L + 1) * sizeof(int32_t) + 6 * (size_t)nthr * sizeof(float) + 64;
 }
 
-__device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L, int nthr) {
+__device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L) {
   RefitSmem m;
   // 16-byte items first: every offset stays aligned for any P
   m.world = reinterpret_cast<double *>(base);
@@ -100,188 +106,198 @@ __device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L, int
   return m;
 }
 
+// Upper bound of |x| for x = a - b evaluated in FP32.
+__device__ __forceinline__ float abs_diff_up(float a, float b) {
+  return fmaxf(fabsf(__fsub_ru(a, b)), fabsf(__fsub_rd(a, b)));
+}
+
+// Upper bound of sqrt(x^2 + y^2 + z^2) for non-negative x, y, z.
+__device__ __forceinline__ float norm_up(float x, float y, float z) {
+  return __fsqrt_ru(__fmaf_ru(x, x, __fmaf_ru(y, y, __fmul_ru(z, z))));
+}
+
 template <bool INLINE, int CAP>
 __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses<CAP> poses) {
   const int P = a.n_parts;
   const int tid = threadIdx.x;
-  const int nthr = blockDim.x;
+  const int lane = tid & 31;
   extern __shared__ __align__(16) unsigned char refit_smem[];
-  const RefitSmem sm = carve(refit_smem, P, a.n_clusters, a.n_levels, nthr);
+  const RefitSmem sm = carve(refit_smem, P, a.n_clusters, a.n_levels);
   if (INLINE) {
     // keep the device copy of the local poses in step with what is composed
-    for (int k = tid; k < P * 12; k += nthr) const_cast<double *>(a.local)[k] = poses.local[k];
+    for (int k = tid; k < P * 12; k += kRefitThreads) const_cast<double *>(a.local)[k] = poses.local[k];
   }
   const double *local = INLINE ? poses.local : a.local;
   // tree topology to shared memory (independent loads, one round trip)
-  for (int i = tid; i < P; i += nthr) {
+  for (int i = tid; i < P; i += kRefitThreads) {
     sm.parent[i] = a.stat[i].parent;
     sm.lorder[i] = a.level_order[i];
   }
-  for (int i = tid; i <= a.n_levels; i += nthr) sm.lstart[i] = a.level_start[i];
+  for (int i = tid; i <= a.n_levels; i += kRefitThreads) sm.lstart[i] = a.level_start[i];
   __syncthreads();
 
-  // 1. compose, level by level (parents are on earlier levels)
+  int r;  // lane inside the part's group of four: rows 0..2, lane 3 helps with the FP32 bounds
+  const int q = quad_item(tid, r);
+  const unsigned int qmask = 0xFu << (lane & ~3);
+
+  // 1. compose, level by level (parents are on earlier levels); lane r
+  //    computes row r of W_i = W_parent o L_i
   for (int L = 0; L < a.n_levels; ++L) {
     const int b = sm.lstart[L], e = sm.lstart[L + 1];
-    for (int j = b + tid; j < e; j += nthr) {
+    for (int j = b + q; j < e; j += kQuadsPerPass) {
+      if (r == 3) continue;
       const int i = sm.lorder[j];
       const int p = sm.parent[i];
       const double *Li = local + 12 * i;
-      double *Wi = sm.world + 12 * i;
-      double out[12];
+      double out[4];
       if (p < 0) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) out[k] = Li[k];
+        for (int c = 0; c < 4; ++c) out[c] = Li[4 * r + c];
       } else {
-        double Wp[12], L12[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          Wp[k] = sm.world[12 * p + k];
-          L12[k] = Li[k];
-        }
-        compose_affine(Wp, L12, out);
+        const double *Wp = sm.world + 12 * p + 4 * r;
+        const double p0 = Wp[0], p1 = Wp[1], p2 = Wp[2], p3 = Wp[3];
+        out[0] = p0 * Li[0] + p1 * Li[4] + p2 * Li[8];
+        out[1] = p0 * Li[1] + p1 * Li[5] + p2 * Li[9];
+        out[2] = p0 * Li[2] + p1 * Li[6] + p2 * Li[10];
+        out[3] = p0 * Li[3] + p1 * Li[7] + p2 * Li[11] + p3;
       }
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        Wi[k] = out[k];
-        a.world[12 * i + k] = out[k];
+      for (int c = 0; c < 4; ++c) {
+        sm.world[12 * i + 4 * r + c] = out[c];
+        a.world[12 * i + 4 * r + c] = out[c];
       }
     }
     __syncthreads();
   }
 
-  // 2-4. per part: invert, FP32 rows, norms, sphere
+  // 2-4. per part: lane r < 3 inverts row r in FP64; all four lanes share the
+  //      FP32 bounds (radius, norms) through quad shuffles
   float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  for (int i = tid; i < P; i += nthr) {
-    double m[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) m[k] = sm.world[12 * i + k];
+  const int rr = r < 3 ? r : 2;  // lane 3 repeats row 2 (its FP64 results are not stored)
+  for (int p = q; p < P; p += kQuadsPerPass) {
+    const double *m = sm.world + 12 * p;
     const double A0 = m[0], A1 = m[1], A2 = m[2], A3 = m[4], A4 = m[5], A5 = m[6], A6 = m[8], A7 = m[9],
                  A8 = m[10];
     const double c00 = A4 * A8 - A5 * A7, c01 = A5 * A6 - A3 * A8, c02 = A3 * A7 - A4 * A6;
     const double det = A0 * c00 + A1 * c01 + A2 * c02;
-    double inv[12];
+    // row r of adj(A) = cofactors of column r of A
+    const double P1 = rr == 0 ? A2 : (rr == 1 ? A0 : A1), Q1 = rr == 0 ? A7 : (rr == 1 ? A8 : A6);
+    const double R1 = rr == 0 ? A1 : (rr == 1 ? A2 : A0), S1 = rr == 0 ? A8 : (rr == 1 ? A6 : A7);
+    const double P2 = rr == 0 ? A1 : (rr == 1 ? A2 : A0), Q2 = rr == 0 ? A5 : (rr == 1 ? A3 : A4);
+    const double R2 = rr == 0 ? A2 : (rr == 1 ? A0 : A1), S2 = rr == 0 ? A4 : (rr == 1 ? A5 : A3);
+    const double e0 = rr == 0 ? c00 : (rr == 1 ? c01 : c02);
+    const double e1 = P1 * Q1 - R1 * S1;
+    const double e2 = P2 * Q2 - R2 * S2;
     bool ok = isfinite(det) && fabs(det) > 0.0;
+    double iv[4] = {0.0, 0.0, 0.0, 0.0};
     if (ok) {
       const double rd = 1.0 / det;
-      inv[0] = c00 * rd;
-      inv[1] = (A2 * A7 - A1 * A8) * rd;
-      inv[2] = (A1 * A5 - A2 * A4) * rd;
-      inv[4] = c01 * rd;
-      inv[5] = (A0 * A8 - A2 * A6) * rd;
-      inv[6] = (A2 * A3 - A0 * A5) * rd;
-      inv[8] = c02 * rd;
-      inv[9] = (A1 * A6 - A0 * A7) * rd;
-      inv[10] = (A0 * A4 - A1 * A3) * rd;
+      iv[0] = e0 * rd;
+      iv[1] = e1 * rd;
+      iv[2] = e2 * rd;
+      iv[3] = -(iv[0] * m[3] + iv[1] * m[7] + iv[2] * m[11]);
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        inv[r * 4 + 3] = -(inv[r * 4 + 0] * m[3] + inv[r * 4 + 1] * m[7] + inv[r * 4 + 2] * m[11]);
-      for (int k = 0; k < 12; ++k) ok = ok && isfinite(inv[k]);
+      for (int k = 0; k < 4; ++k) ok = ok && isfinite(iv[k]);
     }
+    ok = __all_sync(qmask, ok);
     if (!ok) {
-      atomicOr(a.err, kErrSingular);
-      for (int k = 0; k < 12; ++k) inv[k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) iv[k] = 0.0;
+      if (r == 0) atomicOr(a.err, kErrSingular);
     }
+    if (r < 3) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) a.inv64[12 * i + k] = inv[k];
-
-    float f[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) f[k] = (float)inv[k];
-    double rowsum = 0.0;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      double s = fabs((double)f[r * 4]) + fabs((double)f[r * 4 + 1]) + fabs((double)f[r * 4 + 2]);
-      rowsum = fmax(rowsum, s);
+      for (int k = 0; k < 4; ++k) a.inv64[12 * p + 4 * r + k] = iv[k];
     }
-    // sphere of the occupied box [lo, hi] (it holds every leaf of the part):
-    // centre = W (lo + hi) / 2, radius = farthest image of a box corner
-    const PartStatic &ps = a.stat[i];
-    double mid[3], ext[3];
+    // sphere centre c = W (lo + hi) / 2 in FP64 (row r), its FP32 rounding,
+    // and the local coordinates of that FP32 point (FP64, rounded once)
+    const PartStatic &ps = a.stat[p];
+    const float lo0 = ps.box_lo[0], lo1 = ps.box_lo[1], lo2 = ps.box_lo[2];
+    const float hi0 = ps.box_hi[0], hi1 = ps.box_hi[1], hi2 = ps.box_hi[2];
+    const double mid0 = 0.5 * ((double)lo0 + (double)hi0), mid1 = 0.5 * ((double)lo1 + (double)hi1),
+                 mid2 = 0.5 * ((double)lo2 + (double)hi2);
+    const double cr = m[4 * rr] * mid0 + m[4 * rr + 1] * mid1 + m[4 * rr + 2] * mid2 + m[4 * rr + 3];
+    const float cfr = (float)cr;
+    const float cfx = __shfl_sync(qmask, cfr, 0, 4), cfy = __shfl_sync(qmask, cfr, 1, 4),
+                cfz = __shfl_sync(qmask, cfr, 2, 4);
+    const float lcr = (float)(iv[0] * (double)cfx + iv[1] * (double)cfy + iv[2] * (double)cfz + iv[3]);
+    const float f0 = (float)iv[0], f1 = (float)iv[1], f2 = (float)iv[2];
+    if (r < 3) reinterpret_cast<float4 *>(&a.hot[p])[r] = make_float4(f0, f1, f2, lcr);
+    // FP32 bounds, every sum of squares rounded up.  Box half extents and
+    // the corner offsets +-e are exact in FP32 (multiples of 2^-depth).
+    const bool row = r < 3;
+    float rs = row ? __fadd_ru(__fadd_ru(fabsf(f0), fabsf(f1)), fabsf(f2)) : 0.f;  // row of |Ainv|
+    const float ex0 = 0.5f * (hi0 - lo0), ex1 = 0.5f * (hi1 - lo1), ex2 = 0.5f * (hi2 - lo2);
+    const float a0 = (float)m[4 * rr], a1 = (float)m[4 * rr + 1], a2 = (float)m[4 * rr + 2];
+    const float u0 = a0 * ex0, u1 = a1 * ex1, u2 = a2 * ex2;
+    float s[7];
+    s[0] = u0 + u1 + u2;  // the four corner directions (the other four are their negatives)
+    s[1] = u0 + u1 - u2;
+    s[2] = u0 - u1 + u2;
+    s[3] = u0 - u1 - u2;
+    s[4] = fabsf(u0) + fabsf(u1) + fabsf(u2);  // |A| e: scale of every rounding error above
+    s[5] = a0 + a1 + a2;                          // A (1,1,1): the leaf diagonal direction
+    s[6] = (float)fabs(cr - (double)cfr);         // centre rounding
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      mid[q] = 0.5 * ((double)ps.box_lo[q] + (double)ps.box_hi[q]);
-      ext[q] = 0.5 * ((double)ps.box_hi[q] - (double)ps.box_lo[q]);
+    for (int k = 0; k < 7; ++k) {
+      float v = row ? __fmul_ru(s[k], s[k]) : 0.f;
+      v = __fadd_ru(v, __shfl_xor_sync(qmask, v, 1, 4));
+      v = __fadd_ru(v, __shfl_xor_sync(qmask, v, 2, 4));
+      s[k] = v;
     }
-    double c[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) c[r] = m[r * 4] * mid[0] + m[r * 4 + 1] * mid[1] + m[r * 4 + 2] * mid[2] + m[r * 4 + 3];
-    double r2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const double qx = (k & 1) ? ext[0] : -ext[0], qy = (k & 2) ? ext[1] : -ext[1], qz = (k & 4) ? ext[2] : -ext[2];
-      double s = 0.0;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const double v = m[r * 4] * qx + m[r * 4 + 1] * qy + m[r * 4 + 2] * qz;
-        s += v * v;
-      }
-      r2 = fmax(r2, s);
+    rs = fmaxf(rs, __shfl_xor_sync(qmask, rs, 1, 4));
+    rs = fmaxf(rs, __shfl_xor_sync(qmask, rs, 2, 4));
+    if (r == 0) {
+      // |A q - c| <= computed + rounding (<= 2^-20 |A| e) for every corner q,
+      // plus the distance of the FP32 centre from the exact one
+      const float rfl = __fsqrt_ru(fmaxf(fmaxf(s[0], s[1]), fmaxf(s[2], s[3])));
+      const float rad = __fadd_ru(__fadd_ru(__fmul_ru(rfl, 1.0f + kRelSlack), __fmul_ru(__fsqrt_ru(s[4]), kRelSlack)),
+                                  __fmul_ru(__fsqrt_ru(s[6]), 1.0f + kRelSlack));
+      // a singular pose or an empty asset disables the sphere: no ray tests the part
+      const float4 sph = make_float4(cfx, cfy, cfz, (ok && ps.n_nodes > 0) ? rad : -1.0f);
+      reinterpret_cast<float4 *>(&a.hot[p])[3] = sph;
+      sm.sph[p] = sph;
+      PartAux x;
+      x.nodes = ps.nodes;
+      x.n_nodes = ps.n_nodes;
+      x.depth = ps.depth;
+      x.n_ainv = rs;
+      x.hdiag = sqrtf(s[5]) * __int_as_float((127 - ps.depth) << 23);
+      x.spare0 = 0.f;
+      x.spare1 = 0.f;
+      a.aux[p] = x;
+      sm.na[p] = rs;
+      mn[0] = fminf(mn[0], cfx);
+      mn[1] = fminf(mn[1], cfy);
+      mn[2] = fminf(mn[2], cfz);
+      mx[0] = fmaxf(mx[0], cfx);
+      mx[1] = fmaxf(mx[1], cfy);
+      mx[2] = fmaxf(mx[2], cfz);
     }
-    const float cfx = (float)c[0], cfy = (float)c[1], cfz = (float)c[2];
-    const double dcx = c[0] - cfx, dcy = c[1] - cfy, dcz = c[2] - cfz;
-    const double rr = (sqrt(r2) + sqrt(dcx * dcx + dcy * dcy + dcz * dcz)) * (1.0 + 1e-12);
-    // local coordinates of the FP32 centre (close to the box centre)
-    float lc[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      lc[q] = (float)(inv[q * 4] * (double)cfx + inv[q * 4 + 1] * (double)cfy + inv[q * 4 + 2] * (double)cfz +
-                      inv[q * 4 + 3]);
-    PartHot h;
-    h.r0 = make_float4(f[0], f[1], f[2], lc[0]);
-    h.r1 = make_float4(f[4], f[5], f[6], lc[1]);
-    h.r2 = make_float4(f[8], f[9], f[10], lc[2]);
-    // a singular pose or an empty asset disables the sphere: no ray tests the part
-    h.sphere = make_float4(cfx, cfy, cfz, (ok && ps.n_nodes > 0) ? __double2float_ru(rr) : -1.0f);
-    a.hot[i] = h;
-    sm.sph[i] = h.sphere;
-    PartAux x;
-    x.nodes = a.stat[i].nodes;
-    x.n_nodes = a.stat[i].n_nodes;
-    x.depth = a.stat[i].depth;
-    x.n_ainv = __double2float_ru(rowsum * (1.0 + 1e-12));
-    x.spare0 = 0.f;
-    x.spare1 = 0.f;
-    {
-      double dg = 0.0;
-#pragma unroll
-      for (int rr2 = 0; rr2 < 3; ++rr2) {
-        const double v = m[rr2 * 4] + m[rr2 * 4 + 1] + m[rr2 * 4 + 2];
-        dg += v * v;
-      }
-      x.hdiag = (float)(sqrt(dg) * ldexp(1.0, -a.stat[i].depth));
-    }
-    a.aux[i] = x;
-    sm.na[i] = x.n_ainv;
-    mn[0] = fminf(mn[0], cfx);
-    mn[1] = fminf(mn[1], cfy);
-    mn[2] = fminf(mn[2], cfz);
-    mx[0] = fmaxf(mx[0], cfx);
-    mx[1] = fmaxf(mx[1], cfy);
-    mx[2] = fmaxf(mx[2], cfz);
   }
   // bounding box of the sphere centres (block reduction)
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sm.red[k * nthr + tid] = mn[k];
-    sm.red[(3 + k) * nthr + tid] = mx[k];
+    sm.red[k * kRefitThreads + tid] = mn[k];
+    sm.red[(3 + k) * kRefitThreads + tid] = mx[k];
   }
   __syncthreads();
-  for (int w = nthr / 2; w > 0; w >>= 1) {
+  for (int w = kRefitThreads / 2; w > 0; w >>= 1) {
     if (tid < w) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        sm.red[k * nthr + tid] = fminf(sm.red[k * nthr + tid], sm.red[k * nthr + tid + w]);
-        sm.red[(3 + k) * nthr + tid] = fmaxf(sm.red[(3 + k) * nthr + tid], sm.red[(3 + k) * nthr + tid + w]);
+        float *lo = sm.red + k * kRefitThreads, *hi = sm.red + (3 + k) * kRefitThreads;
+        lo[tid] = fminf(lo[tid], lo[tid + w]);
+        hi[tid] = fmaxf(hi[tid], hi[tid + w]);
       }
     }
     __syncthreads();
   }
-  const float bx0 = sm.red[0], by0 = sm.red[nthr], bz0 = sm.red[2 * nthr];
-  const float bx1 = sm.red[3 * nthr], by1 = sm.red[4 * nthr], bz1 = sm.red[5 * nthr];
+  const float bx0 = sm.red[0], by0 = sm.red[kRefitThreads], bz0 = sm.red[2 * kRefitThreads];
+  const float bx1 = sm.red[3 * kRefitThreads], by1 = sm.red[4 * kRefitThreads], bz1 = sm.red[5 * kRefitThreads];
   const float ex = fmaxf(bx1 - bx0, 1e-30f), ey = fmaxf(by1 - by0, 1e-30f), ez = fmaxf(bz1 - bz0, 1e-30f);
   // 5. Morton keys and a rank sort (P <= kMaxParts)
-  for (int i = tid; i < P; i += nthr) {
+  for (int i = tid; i < P; i += kRefitThreads) {
     const float4 s = sm.sph[i];
     const unsigned int qx = (unsigned int)fminf(fmaxf((s.x - bx0) / ex * 1023.0f, 0.0f), 1023.0f);
     const unsigned int qy = (unsigned int)fminf(fmaxf((s.y - by0) / ey * 1023.0f, 0.0f), 1023.0f);
@@ -290,7 +306,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     sm.key[i] = ((unsigned long long)mc << 11) | (unsigned long long)i;
   }
   __syncthreads();
-  for (int i = tid; i < P; i += nthr) {
+  for (int i = tid; i < P; i += kRefitThreads) {
     const unsigned long long k = sm.key[i];
     int rank = 0;
     for (int j = 0; j < P; ++j) rank += (sm.key[j] < k) ? 1 : 0;
@@ -298,10 +314,11 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     a.order[rank] = i;
   }
   __syncthreads();
-  for (int cidx = tid; cidx < a.n_clusters; cidx += nthr) {
+  // clusters: a sphere around the member spheres, in FP32 rounded outward
+  for (int cidx = tid; cidx < a.n_clusters; cidx += kRefitThreads) {
     const int first = cidx * kClusterSize;
     const int cnt = min(kClusterSize, P - first);
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     float na = 0.f;
     bool any = false;
     for (int k = 0; k < cnt; ++k) {
@@ -309,27 +326,25 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       const float4 s = sm.sph[p];
       if (s.w < 0.f) continue;
       any = true;
-      lo[0] = fmin(lo[0], (double)s.x - s.w);
-      lo[1] = fmin(lo[1], (double)s.y - s.w);
-      lo[2] = fmin(lo[2], (double)s.z - s.w);
-      hi[0] = fmax(hi[0], (double)s.x + s.w);
-      hi[1] = fmax(hi[1], (double)s.y + s.w);
-      hi[2] = fmax(hi[2], (double)s.z + s.w);
+      lo[0] = fminf(lo[0], __fsub_rd(s.x, s.w));
+      lo[1] = fminf(lo[1], __fsub_rd(s.y, s.w));
+      lo[2] = fminf(lo[2], __fsub_rd(s.z, s.w));
+      hi[0] = fmaxf(hi[0], __fadd_ru(s.x, s.w));
+      hi[1] = fmaxf(hi[1], __fadd_ru(s.y, s.w));
+      hi[2] = fmaxf(hi[2], __fadd_ru(s.z, s.w));
       na = fmaxf(na, sm.na[p]);
     }
     Cluster cl;
     if (any) {
-      double C[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
-      const float Cx = (float)C[0], Cy = (float)C[1], Cz = (float)C[2];
-      double R = 0.0;
+      // any centre works: the radius is measured from it with upward rounding
+      const float Cx = 0.5f * lo[0] + 0.5f * hi[0], Cy = 0.5f * lo[1] + 0.5f * hi[1], Cz = 0.5f * lo[2] + 0.5f * hi[2];
+      float R = 0.f;
       for (int k = 0; k < cnt; ++k) {
-        const int p = sm.ord[first + k];
-        const float4 s = sm.sph[p];
+        const float4 s = sm.sph[sm.ord[first + k]];
         if (s.w < 0.f) continue;
-        const double dx = (double)s.x - Cx, dy = (double)s.y - Cy, dz = (double)s.z - Cz;
-        R = fmax(R, sqrt(dx * dx + dy * dy + dz * dz) + (double)s.w);
+        R = fmaxf(R, __fadd_ru(norm_up(abs_diff_up(s.x, Cx), abs_diff_up(s.y, Cy), abs_diff_up(s.z, Cz)), s.w));
       }
-      cl.sphere = make_float4(Cx, Cy, Cz, __double2float_ru(R * (1.0 + 1e-12)));
+      cl.sphere = make_float4(Cx, Cy, Cz, R);
     } else {
       cl.sphere = make_float4(0.f, 0.f, 0.f, -1.0f);
     }
@@ -345,35 +360,32 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     for (int c = 0; c < a.n_clusters; ++c) {
       const float4 s = sm.cl[c];
       if (s.w < 0.f) continue;
-      const float dx = s.x - Cx, dy = s.y - Cy, dz = s.z - Cz;
-      R = fmaxf(R, sqrtf(dx * dx + dy * dy + dz * dz) + s.w);
+      R = fmaxf(R, __fadd_ru(norm_up(abs_diff_up(s.x, Cx), abs_diff_up(s.y, Cy), abs_diff_up(s.z, Cz)), s.w));
     }
     *a.bound = make_float4(Cx, Cy, Cz, R);
   }
 }
 
-}  // namespace
-
 template <bool INLINE, int CAP>
-cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, int threads, size_t smem,
-                           cudaStream_t stream) {
+cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, size_t smem, cudaStream_t stream) {
   InlinePoses<CAP> p;
   if (INLINE)
     for (int k = 0; k < a.n_parts * 12; ++k) p.local[k] = host_local[k];
   cudaError_t e = cudaFuncSetAttribute(k_refit<INLINE, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_refit<INLINE, CAP><<<1, threads, smem, stream>>>(a, p);
+  k_refit<INLINE, CAP><<<1, kRefitThreads, smem, stream>>>(a, p);
   return cudaGetLastError();
 }
 
+}  // namespace
+
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
   static_assert(kInlinePoseParts == 256, "size classes below");
-  const int threads = a.n_parts <= 32 ? 32 : kRefitThreads;
-  const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, threads);
-  if (host_local && a.n_parts <= 16) return launch_refit_t<true, 16>(a, host_local, threads, smem, stream);
-  if (host_local && a.n_parts <= 64) return launch_refit_t<true, 64>(a, host_local, threads, smem, stream);
-  if (host_local && a.n_parts <= 256) return launch_refit_t<true, 256>(a, host_local, threads, smem, stream);
-  return launch_refit_t<false, 1>(a, nullptr, threads, smem, stream);
+  const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, kRefitThreads);
+  if (host_local && a.n_parts <= 16) return launch_refit_t<true, 16>(a, host_local, smem, stream);
+  if (host_local && a.n_parts <= 64) return launch_refit_t<true, 64>(a, host_local, smem, stream);
+  if (host_local && a.n_parts <= 256) return launch_refit_t<true, 256>(a, host_local, smem, stream);
+  return launch_refit_t<false, 1>(a, nullptr, smem, stream);
 }
 
 }  // namespace svo

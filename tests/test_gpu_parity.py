@@ -69,7 +69,8 @@ def test_refit_matches_oracle(ctx, pr1):
     dc = np.linalg.norm(got["sphere"][:, :3].astype(np.float64) - sph[:, :3], axis=1)
     r = got["sphere"][:, 3].astype(np.float64)
     assert np.all(dc + sph[:, 3] <= r)  # the FP32 sphere encloses the exact one
-    assert np.all(r <= sph[:, 3] * (1 + 1e-6) + 2 * dc + 1e-30)
+    # the radius is an FP32 upper bound with 2^-20 slack on the corner norms and their rounding scale
+    assert np.all(r <= sph[:, 3] * (1 + 4e-6) + 2 * dc + 1e-30)
     cl = gs.sc.read_clusters()
     assert sorted(cl["order"].tolist()) == list(range(scene.n_parts))
     for c in range(cl["sphere"].shape[0]):
