@@ -728,59 +728,10 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
   }
 }
 
-// Next tile for the calling warp (lane 0 draws it, every lane gets it).
-__device__ __forceinline__ unsigned long long claim_tile(unsigned long long *counter, int lane) {
-  unsigned long long t = 0;
-  if (lane == 0) t = atomicAdd(counter, 1ull);
-  return __shfl_sync(0xffffffffu, t, 0);
-}
-
-// Ray of `lane` in step j of `tile` (an item's tiles are 32 * rpl consecutive
-// rays, or blocks of 8 x 4*rpl pixels of a row-major image).  Returns whether
-// the slot holds a ray; *ray is its index (through the visiting order, if any).
-__device__ __forceinline__ bool step_ray(const TraceItem &I, unsigned long long tile, int j, int lane, int rpl,
-                                         unsigned long long &ray) {
-  unsigned long long slot_i = (tile - I.tile_begin) * (unsigned long long)(32 * rpl) + (unsigned long long)(j * 32 + lane);
-  bool in_range = slot_i < I.n;
-  if (I.tiles_x) {
-    const uint32_t T = (uint32_t)(tile - I.tile_begin);
-    const uint32_t ty = T / I.tiles_x, tx = T - ty * I.tiles_x;
-    const uint32_t k = (uint32_t)(j * 32 + lane);
-    const uint32_t x = tx * 8u + (k & 7u);
-    const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);
-    slot_i = y * I.width + x;
-    in_range = x < I.width && slot_i < I.n;
-  }
-  ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
-  return in_range;
-}
-
-// Asynchronous copy of one ray (two 16-byte words, 16-byte aligned) into this
-// lane's shared-memory slot, bypassing L1; completion is awaited per group.
-__device__ __forceinline__ void copy_ray_async(float4 *dst, const float4 *src) {
-  const unsigned int s = (unsigned int)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s + 16u), "l"(src + 1) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// all but the most recent group complete
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Byte offset of the ray prefetch buffers (2 x 32 rays per warp, 64 B per
-// lane) in the trace kernel's shared memory, after the staged part tables.
-template <typename LT>
-__host__ __device__ inline size_t prefetch_offset(const LT &L, int block) {
-  const size_t sp = L.one_scene ? L.items[0].n_parts : 0, sc = L.one_scene ? L.items[0].n_clusters : 0;
-  const size_t off = kTablesBytes + (size_t)L.stack_levels * block * sizeof(uint2) +
-                     sp * (sizeof(PartHot) + sizeof(PartAux)) + sc * sizeof(Cluster) + sp * sizeof(int32_t);
-  return (off + 15) & ~size_t(15);
-}
-
 template <int NI, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // [tables | traversal stacks, level-major | staged part tables | ray prefetch]
+  // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
   uint2 *sStack = reinterpret_cast<uint2 *>(smem + kTablesBytes) + threadIdx.x;
   const int sp = L.one_scene ? L.items[0].n_parts : 0;
@@ -804,51 +755,41 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   uint32_t n_rays = 0, n_flag = 0;
   const int lane = threadIdx.x & 31;
-  // Warp-uniform walk over (tile, j) steps, one ray per lane per step.  The
-  // next step's rays are copied into shared memory (cp.async) while this
-  // step traces, so the ray load latency is off the critical path.
-  float4 *pf = reinterpret_cast<float4 *>(smem + prefetch_offset(L, BLOCK)) + (threadIdx.x >> 5) * 128 + lane * 2;
-  const int rpl = L.rays_per_lane;
-  const bool staged = L.one_scene != 0;
-  unsigned long long tile = claim_tile(L.tile_counter, lane);
-  int j = 0, buf = 0, it = 0;
-  unsigned long long ray = 0;
-  bool in_range = false;
-  if (tile < L.n_tiles) {
-    it = find_item(L, tile);
-    in_range = step_ray(L.items[it], tile, 0, lane, rpl, ray);
-    if (in_range) copy_ray_async(pf, &L.items[it].rays[2 * ray]);
-  }
-  cp_async_commit();
-  while (tile < L.n_tiles) {
-    unsigned long long ntile = tile;
-    int nj = j + 1;
-    if (nj == rpl) {
-      ntile = claim_tile(L.tile_counter, lane);
-      nj = 0;
-    }
-    int nit = it;
-    unsigned long long nray = 0;
-    bool nin = false;
-    if (ntile < L.n_tiles) {
-      nit = find_item(L, ntile);
-      nin = step_ray(L.items[nit], ntile, nj, lane, rpl, nray);
-      if (nin) copy_ray_async(pf + 64 * (buf ^ 1), &L.items[nit].rays[2 * nray]);
-    }
-    cp_async_commit();
-    cp_async_wait_prev();  // this step's copy has landed
-    {
-      const TraceItem &I = L.items[it];
-      const int P = I.n_parts, NC = I.n_clusters;
-      const PartHot *hot = staged ? sHot : I.hot;
-      const PartAux *aux = staged ? sAux : I.aux;
-      const Cluster *cls = staged ? sCl : I.clusters;
-      const int32_t *ord = staged ? sOrd : I.order;
+  for (;;) {
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= L.n_tiles) break;
+    const int it = find_item(L, tile);
+    const TraceItem &I = L.items[it];
+    const int P = I.n_parts, NC = I.n_clusters;
+    const bool staged = L.one_scene != 0;
+    const PartHot *hot = staged ? sHot : I.hot;
+    const PartAux *aux = staged ? sAux : I.aux;
+    const Cluster *cls = staged ? sCl : I.clusters;
+    const int32_t *ord = staged ? sOrd : I.order;
+    const int rpl = L.rays_per_lane;
+    const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
+#pragma unroll 1
+    for (int j = 0; j < rpl; ++j) {
+      unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
+      bool in_range = slot_i < I.n;
+      if (I.tiles_x) {
+        // image layout: the tile is a block of 8 x 4*rpl pixels
+        const uint32_t T = (uint32_t)(tile - I.tile_begin);
+        const uint32_t ty = T / I.tiles_x, tx = T - ty * I.tiles_x;
+        const uint32_t k = (uint32_t)(j * 32 + lane);
+        const uint32_t x = tx * 8u + (k & 7u);
+        const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);
+        slot_i = y * I.width + x;
+        in_range = x < I.width && slot_i < I.n;
+      }
+      const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
       bool active = in_range;
       RayW r;
       if (active) {
-        const float4 o = pf[64 * buf];
-        const float4 d = pf[64 * buf + 1];
+        const float4 o = __ldcs(&I.rays[2 * ray]);
+        const float4 d = __ldcs(&I.rays[2 * ray + 1]);
         r.ox = o.x;
         r.oy = o.y;
         r.oz = o.z;
@@ -939,14 +880,7 @@ __global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(con
         }
       }
     }
-    tile = ntile;
-    j = nj;
-    it = nit;
-    ray = nray;
-    in_range = nin;
-    buf ^= 1;
   }
-  cp_async_wait_all();
   if (STATS) flush_stats(L.stats, cnt, n_rays, n_flag);
   if (err) atomicOr(L.err, err);
 }
@@ -1061,15 +995,15 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-// [tables | stacks | staged part tables | ray prefetch buffers (64 B per thread)]
-template <typename LT>
-size_t trace_smem_bytes(const LT &L, int block) {
-  return prefetch_offset(L, block) + (size_t)block * 2 * sizeof(float4) * 2;
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block) {
+  return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
+         clusters * sizeof(Cluster) + parts * sizeof(int32_t);
 }
 
 template <int NI, int BLOCK>
 cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes(L, BLOCK);
+  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
+                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK);
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
   auto kern = stats ? k_trace<NI, true, BLOCK> : k_trace<NI, false, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
