@@ -88,6 +88,32 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_trace_articulated_1920x1080.md")
+TRACE_SOURCE = os.path.join(ROOT, "paper_1911_06001_gb300", "csrc", "k_trace.cu")
+
+
+def measured_traffic() -> tuple:
+    """DRAM bytes per trace launch from the committed ncu summary, if it was
+    taken on the trace kernel's current source (sha256 recorded beside it);
+    (None, reason) otherwise."""
+    import hashlib
+
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None, "no ncu summary"
+    fields = {}
+    with open(TRAFFIC_PROFILE) as f:
+        for line in f:
+            line = line.strip().strip("`")
+            for key in ("traffic_bytes_per_launch:", "k_trace_source_sha256:"):
+                if line.startswith(key):
+                    fields[key[:-1]] = line[len(key):].strip()
+    with open(TRACE_SOURCE, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if fields.get("k_trace_source_sha256") != sha or "traffic_bytes_per_launch" not in fields:
+        return None, "kernel changed since the ncu capture"
+    return float(fields["traffic_bytes_per_launch"]), f"ncu dram__bytes_read+write, k_trace.cu sha256 {sha[:12]}"
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -465,8 +491,10 @@ def main() -> None:
     alg_bytes = BYTES_PER_NODE * nodes + BYTES_PER_PART * parts + BYTES_PER_RAY_IO * N_RAYS
     peaks = measured_peaks()
     achieved = alg_bytes / (trace_ms.mean() / 1e3) / 1e9
+    traffic, traffic_src = measured_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_trace",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+                "kernel": "k_trace",
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                 "bytes_per_launch": alg_bytes, "launch_ms": float(trace_ms.mean())}
 
