@@ -193,6 +193,77 @@ def hit_colors(leaf_lists, part_asset, part, voxel, background: int = 0) -> np.n
     return out
 
 
+def shade(colors, part, voxel, depths, inv, rays, light, ambient: float, background: int = 0):
+    """Headless shading of hits (the hit buffer's colour and normal, Sec. IV-C),
+    in FP64.  Per hit: the entry face of the hit leaf's closed box (the axis
+    whose near-plane t is largest; the lower axis index on a tie) gives the
+    local normal -sign(d'_k) e_k, mapped to world space by the inverse
+    transpose (row k of A^-1) and normalised; a ray that starts inside the box
+    (entry before tmin) takes -d/|d|.  Lambert: s = ambient + (1 - ambient)
+    max(0, n . l) with l the unit light direction, and every 8-bit channel c
+    becomes min(255, floor(c s + 1/2)).  Misses keep ``background``, invalid
+    colours stay invalid.
+
+    ``colors``: hit_colors of the hits; ``depths``: asset depth per part;
+    ``inv``: [P,12] world->local poses.  Returns (rgb uint32, ambiguous bool):
+    a pixel is ambiguous when its face choice, its inside test or a channel's
+    rounding lies within 1e-9 (relative) of a decision boundary, where two
+    correct FP64 evaluations may round differently."""
+    colors = np.asarray(colors, dtype=np.uint32)
+    part = np.asarray(part, dtype=np.uint32)
+    voxel = np.asarray(voxel, dtype=np.uint64)
+    rays = np.asarray(rays, dtype=np.float64).reshape(-1, 8)
+    inv = np.asarray(inv, dtype=np.float64).reshape(-1, 12)
+    out = colors.copy()
+    amb = np.zeros(part.shape, dtype=bool)
+    hit = (part != MISS_PART) & (colors != COLOR_INVALID)
+    out[part == MISS_PART] = background
+    idx = np.nonzero(hit)[0]
+    if idx.size == 0:
+        return out, amb
+    L = np.asarray(light, dtype=np.float64)
+    L = L / np.linalg.norm(L)
+    p = part[idx].astype(np.int64)
+    D = np.asarray(depths, dtype=np.int64)[p]
+    m = (np.uint64(1) << D.astype(np.uint64)) - np.uint64(1)
+    v = voxel[idx]
+    cell = np.stack([v & m, (v >> D.astype(np.uint64)) & m, (v >> (2 * D).astype(np.uint64)) & m], 1).astype(np.float64)
+    size = np.ldexp(1.0, -D)[:, None]
+    lo = cell * size
+    hi = lo + size
+    M = inv[p].reshape(-1, 3, 4)
+    o = rays[idx, 0:3]
+    d = rays[idx, 4:7]
+    tmin = rays[idx, 3]
+    ol = np.einsum("nij,nj->ni", M[:, :, :3], o) + M[:, :, 3]
+    dl = np.einsum("nij,nj->ni", M[:, :, :3], d)
+    near = np.where(dl > 0, lo, hi)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tk = np.where(dl != 0, (near - ol) / dl, -np.inf)
+    te = tk.max(1)
+    k = tk.argmax(1)  # first index of the maximum: the lower axis on a tie
+    scale = np.maximum(1.0, np.abs(te))
+    second = np.sort(tk, 1)[:, -2]
+    amb_face = te - second <= 1e-9 * scale
+    inside = te < tmin
+    amb_inside = np.abs(te - tmin) <= 1e-9 * np.maximum(1.0, np.abs(tmin))
+    sign = np.sign(dl[np.arange(idx.size), k])
+    n = -sign[:, None] * M[np.arange(idx.size), k, :3]
+    n = np.where(inside[:, None], -d, n)
+    n = n / np.linalg.norm(n, axis=1)[:, None]
+    s = ambient + (1.0 - ambient) * np.maximum(0.0, n @ L)
+    c = colors[idx]
+    chans = np.stack([(c >> 16) & 255, (c >> 8) & 255, c & 255], 1).astype(np.float64)
+    x = chans * s[:, None] + 0.5
+    q = np.minimum(255.0, np.floor(x))
+    frac = x - np.floor(x)
+    amb_round = (np.minimum(frac, 1.0 - frac) <= 1e-9 * np.maximum(1.0, x)).any(1)
+    qi = q.astype(np.uint32)
+    out[idx] = (qi[:, 0] << 16) | (qi[:, 1] << 8) | qi[:, 2]
+    amb[idx] = amb_face | amb_inside | amb_round
+    return out, amb
+
+
 class SceneOracle:
     """Oracle view of a ``synthetic.Scene``: assets built once, poses per frame."""
 
@@ -213,6 +284,12 @@ class SceneOracle:
     def hit_colors(self, hits: dict, background: int = 0) -> np.ndarray:
         leaf_lists = [(a.leaf_ids, a.rgb) for a in self.scene.assets]
         return hit_colors(leaf_lists, self.scene.part_asset, hits["part"], hits["voxel"], background)
+
+    def shade(self, hits: dict, rays, light, ambient: float, background: int = 0, local=None):
+        colors = self.hit_colors(hits, background)
+        _, inv = self.poses(local)
+        depths = [self.scene.assets[int(a)].depth for a in self.scene.part_asset]
+        return shade(colors, hits["part"], hits["voxel"], depths, inv, rays, light, ambient, background)
 
     def trace(self, rays, local=None, mode: int = 1, threads: int | None = None) -> dict:
         world, inv = self.poses(local)

@@ -68,10 +68,14 @@ constexpr int kCap = 4;  // candidate parts per pass (4: 1.5-2% faster than 8, f
 constexpr int kSmemParts = 256;                 // parts staged in shared memory
 constexpr int kBlock = 128;  // block size of the FP64 pass; the trace kernel takes 64, 128 or 256
 // Resident threads per SM the trace kernel's register allocation must allow
-// (512 = 16 warps: at most 128 registers a thread).  Measured on the
-// articulated-figure frame: 0.353 ms with the compiler's own 163 registers
-// (12 warps), 0.327 ms at 128; 102 registers spill and lose again.
-constexpr int kTraceThreadsPerSM = 512;
+// (768 = 24 warps: at most 80 registers a thread, no spills).  Measured per
+// frame:
+//   * articulated figure: 0.353 ms at the compiler's own 163 registers (12
+//     warps), 0.327 ms at 128 (16 warps), flat from 16 to 24 warps;
+//   * incoherent rays against ~120 parts: 9% faster at 24 warps than at 16;
+//   * 32 warps (64 registers) spill and lose.
+// The counting (STATS) build keeps 16 warps: its counters would spill at 80.
+constexpr int kTraceThreadsPerSM = 768;
 
 constexpr unsigned long long kRayBits = 40;
 
@@ -729,7 +733,7 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 }
 
 template <int NI, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, kTraceThreadsPerSM / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+__global__ void __launch_bounds__(BLOCK, (STATS ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);

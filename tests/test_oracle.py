@@ -482,3 +482,76 @@ def test_hit_colors_closed_form_and_first_occurrence():
     assert got.tolist() == [0xAA0000, 0x00BB00, 0x010203, oracle.COLOR_INVALID, oracle.COLOR_INVALID, 7]
     # an asset without colours gives 0 for its leaves
     assert oracle.hit_colors([(ids, None)], [0], part[:1], vox[:1]).tolist() == [0]
+
+
+def _shade_one(depth, cells, rgb, world12, rays, light, ambient, background=0):
+    ids = synthetic.pack_ids(*[np.array([c[i] for c in cells]) for i in range(3)], depth)
+    inv = oracle.invert(np.asarray(world12, np.float64)[None])
+    a = oracle.OracleAsset(depth, ids)
+    hits = oracle.trace([a], inv, rays)
+    colors = oracle.hit_colors([(ids, np.asarray(rgb, np.uint32))], [0], hits["part"], hits["voxel"], background)
+    return oracle.shade(colors, hits["part"], hits["voxel"], [depth], inv, rays, light, ambient, background), hits
+
+
+def test_shade_closed_forms():
+    """Shading of hits (Sec. IV-C hit buffer: colour + normal): an axis-aligned
+    ray entering through the -x face is lit fully by a light along -x and only
+    by the ambient term from +x; a ray starting inside its voxel faces the
+    viewer; a diagonal ray entering through an edge takes the lower axis."""
+    ident = synthetic.affine12(np.eye(3), np.zeros(3))
+    rgb = [0xC86432]  # (200, 100, 50)
+    ray = np.array([[-1.0, 0.3, 0.3, 0.0, 1.0, 0.0, 0.0, np.inf]])  # enters cell (0,0,0) of depth 1 through x = 0
+    (full, amb), hits = _shade_one(1, [(0, 0, 0)], rgb, ident, ray, [-1.0, 0.0, 0.0], 0.25)
+    assert hits["part"][0] == 0 and full[0] == 0xC86432 and not amb[0]
+    (dark, _), _ = _shade_one(1, [(0, 0, 0)], rgb, ident, ray, [1.0, 0.0, 0.0], 0.25)
+    assert dark[0] == (50 << 16) | (25 << 8) | 13  # floor(c/4 + 1/2): 50, 25, 12.5 -> 13
+    (side, _), _ = _shade_one(1, [(0, 0, 0)], rgb, ident, ray, [-1.0, 1.0, 0.0], 0.0)
+    cos45 = 1.0 / math.sqrt(2.0)
+    assert side[0] == (int(200 * cos45 + 0.5) << 16) | (int(100 * cos45 + 0.5) << 8) | int(50 * cos45 + 0.5)
+    # origin inside the voxel: the normal is -d, fully lit by a light along -d
+    inside = np.array([[0.2, 0.2, 0.2, 0.0, 0.0, 0.0, 2.0, np.inf]])
+    (ins, _), _ = _shade_one(1, [(0, 0, 0)], rgb, ident, inside, [0.0, 0.0, -1.0], 0.0)
+    assert ins[0] == 0xC86432
+    # entry through the edge x = y = 0 (equal near-plane t): ambiguous, and the x face is taken
+    diag = np.array([[-0.5, -0.5, 0.25, 0.0, 1.0, 1.0, 0.0, np.inf]])
+    (dg, amb), _ = _shade_one(1, [(0, 0, 0)], rgb, ident, diag, [-1.0, 0.0, 0.0], 0.0)
+    assert amb[0] and dg[0] == 0xC86432
+    # a miss keeps the background
+    miss = np.array([[-1.0, 5.0, 5.0, 0.0, 1.0, 0.0, 0.0, np.inf]])
+    (ms, _), _ = _shade_one(1, [(0, 0, 0)], rgb, ident, miss, [-1.0, 0.0, 0.0], 0.3, background=0x010203)
+    assert ms[0] == 0x010203
+
+
+def test_shade_rigid_invariance_and_scaled_normals():
+    """One rigid motion applied to the part, the rays and the light leaves the
+    shaded image unchanged; an anisotropic scale keeps face normals on the
+    axes (the inverse transpose, not the forward matrix, maps normals)."""
+    rng = np.random.default_rng(21)
+    scene = synthetic.pr1_scene(depth=4)
+    so = oracle.SceneOracle(scene)
+    rays = synthetic.pr1_rays(scene, 40, 40).astype(np.float64)
+    light = np.array([0.3, -0.8, 0.5])
+    hits = so.trace(rays)
+    base, amb0 = so.shade(hits, rays, light, 0.2)
+    R = _random_rotation(rng)
+    t = rng.uniform(-2, 2, 3)
+    G = np.eye(4)
+    G[:3, :3] = R
+    G[:3, 3] = t
+    local = scene.local.copy()
+    for i in np.nonzero(scene.parent < 0)[0]:
+        M = np.eye(4)
+        M[:3, :] = local[i].reshape(3, 4)
+        local[i] = (G @ M)[:3, :].reshape(12)
+    moved = rays.copy()
+    moved[:, 0:3] = rays[:, 0:3] @ R.T + t
+    moved[:, 4:7] = rays[:, 4:7] @ R.T
+    hits2 = so.trace(moved, local=local)
+    got, amb1 = so.shade(hits2, moved, R @ light, 0.2, local=local)
+    ok = ~(amb0 | amb1) & (hits["part"] == hits2["part"]) & (hits["voxel"] == hits2["voxel"])
+    assert ok.sum() > 300 and np.array_equal(got[ok], base[ok])
+    # anisotropic scale: a ray along +y into a cell of a part scaled (4, 1, 1) enters through -y
+    W = synthetic.affine12(np.diag([4.0, 1.0, 1.0]), np.zeros(3))
+    ray = np.array([[0.5, -1.0, 0.25, 0.0, 0.0, 1.0, 0.0, np.inf]])
+    (sh, amb), hits = _shade_one(1, [(0, 0, 0)], [0xFFFFFF], W, ray, [0.0, -1.0, 0.0], 0.0)
+    assert hits["part"][0] == 0 and sh[0] == 0xFFFFFF and not amb[0]
