@@ -459,6 +459,28 @@ def main() -> None:
     plain_ms = np.array([e[0].elapsed_time(e[1]) for e in plain_ms])
     plain_value = N_RAYS / (plain_ms.mean() / 1e3) / 1e6
 
+    # hit-buffer outputs of a traced frame: leaf colours, and the Lambert-shaded image (FP64 decisions)
+    rgb = torch.empty(N_RAYS, dtype=torch.int32, device=dev)
+    out_ms = {"colors": [], "shade": []}
+    with torch.cuda.stream(stream):
+        sc.set_transforms(poses[0], stream=stream)
+        sc.refit(stream=stream)
+        sc.trace(rays, hits, flags=g.TRACE_DEFAULT, stream=stream)
+        for s in range(10):
+            for name in ("colors", "shade"):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                flush.fill_(s & 0xFF)
+                ev[0].record(stream)
+                if name == "colors":
+                    sc.hit_colors(hits, out=rgb, stream=stream)
+                else:
+                    sc.shade(rays, hits, (0.4, 0.8, 0.45), 0.2, out=rgb, stream=stream)
+                ev[1].record(stream)
+                out_ms[name].append(ev)
+    torch.cuda.synchronize()
+    hit_outputs = {k: {"ms": float(np.mean([e[0].elapsed_time(e[1]) for e in v])), "unit": "ms per frame"}
+                   for k, v in out_ms.items()}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -520,6 +542,7 @@ def main() -> None:
             "breakdown_ms": {"refit": float(refit_ms.mean()), "trace": float(trace_ms.mean()),
                              "fp64_fix": float(fix_ms.mean())},
             "plain_trace": {"value": plain_value, "unit": "Mrays/s", "flags": "fp64_fix only (no cull, no sort)"},
+            "hit_outputs": hit_outputs,
             "graph": {"value": N_RAYS / (graph_ms.mean() / 1e3) / 1e6, "unit": "Mrays/s",
                       "ms_per_step": float(graph_ms.mean()), "p99_ms": float(np.percentile(graph_ms, 99))},
             "launch": {"block": tuned["block"], "rays_per_lane": tuned["rays_per_lane"], "order": tuned["order"],

@@ -295,6 +295,26 @@ svo_status svo_raygen_pinhole(svo_ctx *ctx, const svo_camera *cam, uint32_t widt
 svo_status trace_hit_colors(svo_scene *scene, const svo_hit *hits, uint64_t n, uint32_t background, uint32_t *rgb,
                             void *stream);
 
+/* Shaded image of hits (async): rgb[i] = the hit leaf's colour lit by a
+ * directional light, as 0x00RRGGBB; `background` for a miss; SVO_COLOR_INVALID
+ * where trace_hit_colors gives it.  The normal is the face of the leaf's box
+ * through which ray i enters (the axis whose near-plane parameter is largest,
+ * the lower axis on a tie), mapped to world space by the inverse transpose of
+ * the part's pose; a ray that starts inside the leaf takes -d.  Each channel c
+ * becomes min(255, floor(c * s + 1/2)) with s = ambient + (1 - ambient) *
+ * max(0, n . l), l = light / |light|, evaluated in FP64 (the shading inputs the
+ * paper's hit buffer carries, Sec. IV-C).
+ *   rays: device, n rays (8 floats, 16-byte aligned), those that were traced;
+ *   hits: device, n svo_hit (16-byte aligned), trace_rays' output after its
+ *         FP64 pass (issue both on the same stream);
+ *   light: host, 3 floats, the direction towards the light (any length > 0);
+ *   rgb:  device, n uint32 (4-byte aligned).
+ * SVO_ERR_ARG for NULL or misaligned buffers with n > 0, a zero or
+ * non-finite light, an ambient outside [0, 1] or a background above
+ * 0x00FFFFFF. */
+svo_status trace_shade(svo_scene *scene, const float *rays, const svo_hit *hits, uint64_t n, const float *light,
+                       float ambient, uint32_t background, uint32_t *rgb, void *stream);
+
 /* Run the FP64 re-intersection pass left pending by the last trace_rays /
  * trace_batch issued on `stream` with SVO_TRACE_FP64_FIX | SVO_TRACE_DEFER_FIX
  * (async).  No-op (SVO_OK) if nothing is pending on that stream. */

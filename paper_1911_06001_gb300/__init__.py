@@ -214,6 +214,22 @@ class Scene:
         _lib.check(self.lib.trace_hit_colors(self.h, _ptr(hits), n, int(background), _ptr(out), _stream_ptr(stream)))
         return out
 
+    def shade(self, rays, hits, light, ambient: float = 0.2, background: int = 0, out=None, stream=None):
+        """Lambert-shaded 0x00RRGGBB image (int32) of ``hits`` traced from ``rays`` (CUDA tensors)."""
+        import torch
+
+        if hits.dtype != torch.int64 or hits.dim() != 2 or hits.shape[1] != 2 or not hits.is_cuda:
+            raise ValueError("hits must be a CUDA int64 tensor [n, 2]")
+        if rays.dtype != torch.float32 or rays.shape != (hits.shape[0], RAY_FLOATS) or not rays.is_cuda:
+            raise ValueError("rays must be a CUDA float32 tensor [n, 8] matching hits")
+        n = hits.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=hits.device)
+        lv = (C.c_float * 3)(*[float(x) for x in light])
+        _lib.check(self.lib.trace_shade(self.h, _ptr(rays), _ptr(hits), n, lv, float(ambient), int(background),
+                                        _ptr(out), _stream_ptr(stream)))
+        return out
+
     def trace_host(self, rays_host, hits_host, flags: int = TRACE_DEFAULT, ray_flags_host=None, stream=None):
         """Trace rays held in host memory (CPU tensors, ideally pinned) into host hits (async on ``stream``)."""
         n = rays_host.shape[0]

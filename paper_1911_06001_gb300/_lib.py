@@ -49,6 +49,7 @@ EXPORTS = [
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
     "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole", "trace_hit_colors",
+    "trace_shade",
 ]
 
 
@@ -118,6 +119,7 @@ def load(path: str | None = None):
         "trace_rays_noalloc": ([vp, vp, u64, vp, vp, u32, vp], i32),
         "svo_raygen_pinhole": ([vp, C.POINTER(SvoCamera), u32, u32, vp, vp], i32),
         "trace_hit_colors": ([vp, vp, u64, u32, vp, vp], i32),
+        "trace_shade": ([vp, vp, vp, u64, vp, C.c_float, u32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

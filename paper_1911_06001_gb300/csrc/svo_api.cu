@@ -780,6 +780,31 @@ svo_status trace_hit_colors(svo_scene *s, const svo_hit *hits, uint64_t n, uint3
   return ok();
 }
 
+svo_status trace_shade(svo_scene *s, const float *rays, const svo_hit *hits, uint64_t n, const float *light,
+                       float ambient, uint32_t background, uint32_t *rgb, void *stream) {
+  if (!s || !light) return fail(SVO_ERR_ARG, "trace_shade: NULL argument");
+  if (background > 0x00FFFFFFu) return fail(SVO_ERR_ARG, "trace_shade: background 0x%x is not 0x00RRGGBB", background);
+  if (!(ambient >= 0.f && ambient <= 1.f)) return fail(SVO_ERR_ARG, "trace_shade: ambient outside [0, 1]");
+  ShadeArgs sa;
+  const double lx = light[0], ly = light[1], lz = light[2];
+  const double ll = std::sqrt(lx * lx + ly * ly + lz * lz);
+  if (!(ll > 0.0) || !std::isfinite(ll)) return fail(SVO_ERR_ARG, "trace_shade: light must be finite and non-zero");
+  sa.light[0] = lx / ll;
+  sa.light[1] = ly / ll;
+  sa.light[2] = lz / ll;
+  sa.ambient = ambient;
+  sa.background = background;
+  if (n == 0) return ok();
+  if (!rays || !hits || !rgb) return fail(SVO_ERR_ARG, "trace_shade: NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
+    return fail(SVO_ERR_ARG, "trace_shade: rays and hits must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(rgb) & 3) return fail(SVO_ERR_ARG, "trace_shade: rgb not 4-byte aligned");
+  CK(cudaSetDevice(s->ctx->device));
+  CK(launch_shade(reinterpret_cast<const float4 *>(rays), reinterpret_cast<const uint4 *>(hits), n, s->d_stat,
+                  s->d_inv64, s->P, sa, rgb, s->ctx->n_sm, (cudaStream_t)stream));
+  return ok();
+}
+
 svo_status svo_raygen_pinhole(svo_ctx *ctx, const svo_camera *cam, uint32_t width, uint32_t height, float *rays,
                               void *stream) {
   if (!ctx || !cam || !rays) return fail(SVO_ERR_ARG, "svo_raygen_pinhole: NULL argument");

@@ -136,6 +136,16 @@ cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream);
 cudaError_t launch_hit_colors(const uint4 *hits, unsigned long long n, const PartStatic *stat, int n_parts,
                               uint32_t background, uint32_t *rgb, int n_sm, cudaStream_t stream);
 
+// Lambert shading of n hits (k_color.cu); see trace_shade.
+struct ShadeArgs {
+  double light[3];  // unit direction towards the light
+  double ambient;   // in [0, 1]
+  uint32_t background;
+};
+cudaError_t launch_shade(const float4 *rays, const uint4 *hits, unsigned long long n, const PartStatic *stat,
+                         const double *inv64, int n_parts, const ShadeArgs &sa, uint32_t *rgb, int n_sm,
+                         cudaStream_t stream);
+
 struct RaygenArgs {
   float eye[3], f[3], r[3], u[3];  // camera origin and unit forward / right / up
   float tan_x, tan_y, inv_w, inv_h, tmin, tmax;

@@ -401,3 +401,54 @@ def test_hit_colors_match_oracle(ctx, pr1):
     with pytest.raises(g.SvoError):
         gs.sc.hit_colors(hits, background=0x1000000)
     torch.cuda.synchronize()
+
+
+def _shade_case(ctx, gs, so, rays, light, ambient, bg):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    light32 = np.asarray(light, dtype=np.float32).astype(np.float64)  # what the library receives
+    ora = so.trace(rays)
+    want, amb = so.shade(ora, rays, light32, float(np.float32(ambient)), bg)
+    r = torch.from_numpy(rays).cuda()
+    # the oracle's own hits, shaded on the GPU
+    oh = torch.from_numpy(_pack_hits(ora["t"], ora["part"], ora["voxel"])).cuda()
+    got = gs.sc.shade(r, oh, light, ambient, bg).cpu().numpy().view(np.uint32)
+    bad = np.nonzero((got != want) & ~amb)[0]
+    assert bad.size == 0, (bad[:5], got[bad[:5]], want[bad[:5]])
+    # the GPU's own trace: equal wherever the ids are certified
+    rf = torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")
+    h2 = gs.sc.trace(r, flags=g.TRACE_DEFAULT, ray_flags=rf)
+    got2 = gs.sc.shade(r, h2, light, ambient, bg).cpu().numpy().view(np.uint32)
+    certified = ((rf.cpu().numpy() & g.RAY_UNCERTAIN) == 0) & ~amb
+    assert np.array_equal(got2[certified], want[certified])
+    hit = ora["part"] != oracle.MISS_PART
+    return int(hit.sum()), int((amb & hit).sum())
+
+
+def test_shade_matches_oracle(ctx, pr1):
+    """Lambert shading from the hit leaf's colour and entry-face normal
+    (Sec. IV-C hit buffer): equal to the FP64 oracle on every pixel whose face
+    choice and channel rounding are not within rounding distance of a tie;
+    also on a sheared, anisotropically scaled scene."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    hits, amb = _shade_case(ctx, gs, so, synthetic.pr1_rays(scene), (0.5, -0.75, 0.25), 0.15, 0x203040)
+    assert hits > 1000 and amb < 0.01 * hits
+    bat = synthetic.batched_scenes(seed=8, n_scenes=1, parts=(8, 12), depths=range(5, 7), side=(96, 96), per_depth=2)
+    sc = bat.scenes[0]  # its assets are the pool's
+    gs2 = GpuScene(ctx, sc)
+    hits2, amb2 = _shade_case(ctx, gs2, oracle.SceneOracle(sc), bat.rays[0], (-0.25, 0.5, 1.0), 0.0, 0)
+    assert hits2 > 100 and amb2 < 0.05 * hits2
+    # argument checks
+    r = torch.zeros((4, 8), dtype=torch.float32, device="cuda")
+    h = torch.zeros((4, 2), dtype=torch.int64, device="cuda")
+    for light, ambient, bg in (((0, 0, 0), 0.1, 0), ((1, 0, 0), 1.5, 0), ((1, 0, 0), 0.1, 1 << 24)):
+        with pytest.raises(g.SvoError):
+            gs.sc.shade(r, h, light, ambient, bg)
+    torch.cuda.synchronize()
