@@ -234,6 +234,47 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(out))
 
 
+def hit_buffer_section(g, ctx, sc, fig, poses, rays, flags: int, stream, flush, frames: int = 60) -> dict:
+    """Static camera, only the three end parts animated (the rest hold frame 0's
+    pose): trace time per frame with and without hit buffer reuse (Sec. IV-C)."""
+    import torch
+
+    moving = (13, 14, 15)
+    partial = []
+    for f in range(frames):
+        p = poses[0].copy()
+        for k in moving:
+            p[k] = poses[f][k]
+        partial.append(p)
+    hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
+    out = {}
+    for name, extra in (("full_retrace", 0), ("reuse", g.TRACE_REUSE)):
+        st = g.new_stats(rays.device)
+        with torch.cuda.stream(stream):
+            sc.set_transforms(partial[0], stream=stream)
+            sc.refit(stream=stream)
+            sc.trace(rays, hits, flags=flags, stream=stream)  # the frame whose hits are reused next
+            evs = []
+            for f in range(1, frames):
+                flush.fill_(f & 0xFF)
+                sc.set_transforms(partial[f], stream=stream)
+                sc.refit(stream=stream)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(stream)
+                sc.trace(rays, hits, flags=flags | extra | (g.TRACE_STATS if f == frames - 1 else 0),
+                         stats=st if f == frames - 1 else None, stream=stream)
+                ev[1].record(stream)
+                evs.append(ev)
+        torch.cuda.synchronize()
+        ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+        out[name] = {"value": rays.shape[0] / (ms / 1e3) / 1e6, "unit": "Mrays/s", "trace_ms": ms}
+        if extra:
+            out[name]["reused_frac"] = g.read_stats(st)["reused"] / rays.shape[0]
+    ctx.check_device()
+    return {"workload": "articulated figure, static camera, parts 13-15 animated, 59 frames of 1920x1080",
+            **out}
+
+
 def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
     """The batched configuration: many uneven scenes traced in one persistent
     launch (trace_batch) against the same scenes traced one call each."""
@@ -520,9 +561,10 @@ def main() -> None:
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                 "bytes_per_launch": alg_bytes, "launch_ms": float(trace_ms.mean())}
 
-    batched = serving = None
+    batched = serving = hit_buffer = None
     if extra:
         pool_handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
+        hit_buffer = hit_buffer_section(g, ctx, sc, fig, poses, rays, g.TRACE_DEFAULT | order, stream, flush)
         batched = batched_section(g, ctx, bat, pool_handles, dev, reps=5, flush=flush)
         serving = serving_section(g, ctx, srv, pool_handles, args.serve_requests,
                                   warm=min(1000, args.serve_requests // 5),
@@ -547,6 +589,7 @@ def main() -> None:
                       "ms_per_step": float(graph_ms.mean()), "p99_ms": float(np.percentile(graph_ms, 99))},
             "launch": {"block": tuned["block"], "rays_per_lane": tuned["rays_per_lane"], "order": tuned["order"],
                        "autotuned_ms": tuned["ms"], "default_ms": tuned["default_ms"]},
+            "hit_buffer": hit_buffer,
             "batched": batched,
             "serving": serving,
             "flagged_frac": float(flagged / N_RAYS),

@@ -76,12 +76,20 @@ typedef int32_t svo_status;
                                       16..31 of flags: warps take 8 x 4 pixel tiles instead of 32
                                       consecutive rays (results unchanged; ignored with ORDER_*) */
 #define SVO_TRACE_IMAGE(width) (SVO_TRACE_IMAGE_TILES | ((uint32_t)(width) << 16))
+#define SVO_TRACE_REUSE 256u /* hit buffer reuse (Sec. IV-C, Fig. 5): the hits buffer holds this scene's
+                                result for the same rays from the scene's previous trace (a static
+                                camera); a ray whose only intersected part sphere belongs to the part it
+                                hit then, and that part's pose has not changed in any refit since that
+                                trace, keeps its hit without a descent (ray flag SVO_RAY_REUSED).  Needs
+                                CULL | SORT | FP64_FIX, as the previous trace must have had; every trace
+                                of a scene restarts its change tracking. */
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 
 /* per-ray flags written when ray_flags != NULL */
 #define SVO_RAY_UNCERTAIN 1u /* FP32 could not certify which leaf is hit first (near tie / grazing) */
 #define SVO_RAY_FIXED 2u     /* the hit was recomputed in FP64 */
 #define SVO_RAY_T_REFINED 4u /* the ids were certified but t was recomputed in FP64 for precision */
+#define SVO_RAY_REUSED 8u    /* SVO_TRACE_REUSE kept the previous hit (no descent) */
 
 typedef struct svo_ctx svo_ctx;
 typedef struct svo_scene svo_scene;
@@ -116,6 +124,7 @@ typedef struct {
   unsigned long long flag_winner;   /* flagged because the nearest candidate was not certainly hit */
   unsigned long long flag_overlap;  /* flagged because another candidate's entry bound reached it */
   unsigned long long flag_width;    /* ids certified, but the winner's t interval was too wide (T_REFINED) */
+  unsigned long long reused;        /* rays that kept their previous hit (SVO_TRACE_REUSE) */
 } svo_trace_stats;
 
 /* A pinhole camera for svo_raygen_pinhole. */

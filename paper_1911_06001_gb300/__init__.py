@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
     MAX_DEPTH,
     MAX_PARTS,
     RAY_FIXED,
+    RAY_REUSED,
     RAY_T_REFINED,
     RAY_UNCERTAIN,
     TRACE_CULL,
@@ -28,6 +29,7 @@ from ._lib import (  # noqa: F401
     TRACE_ORDER_ORIGIN,
     TRACE_FP64_FIX,
     TRACE_IMAGE_TILES,
+    TRACE_REUSE,
     TRACE_SORT,
     TRACE_STATS,
     SvoError,
@@ -256,11 +258,11 @@ def decode_hits(hits) -> dict:
 def new_stats(device="cuda"):
     import torch
 
-    return torch.zeros(11, dtype=torch.int64, device=device)
+    return torch.zeros(12, dtype=torch.int64, device=device)
 
 
 def read_stats(stats) -> dict:
     names = ("rays", "flagged", "fixed", "parts_tested", "parts_entered", "nodes_visited", "leaves_tested", "passes",
-             "flag_winner", "flag_overlap", "flag_width")
+             "flag_winner", "flag_overlap", "flag_width", "reused")
     v = stats.detach().cpu().numpy().astype(np.uint64)
     return {n: int(x) for n, x in zip(names, v)}

@@ -23,6 +23,7 @@ TRACE_DEFER_FIX = 16
 TRACE_ORDER_DIR = 32
 TRACE_ORDER_ORIGIN = 64
 TRACE_IMAGE_TILES = 128
+TRACE_REUSE = 256
 TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
 
 
@@ -35,6 +36,7 @@ def trace_image(width: int) -> int:
 RAY_UNCERTAIN = 1
 RAY_FIXED = 2
 RAY_T_REFINED = 4
+RAY_REUSED = 8
 
 MAX_DEPTH = 16
 MAX_PARTS = 1024
@@ -60,7 +62,7 @@ class SvoDesc(C.Structure):
 class SvoTraceStats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("rays", "flagged", "fixed", "parts_tested", "parts_entered",
                                              "nodes_visited", "leaves_tested", "passes", "flag_winner",
-                                             "flag_overlap", "flag_width")]
+                                             "flag_overlap", "flag_width", "reused")]
 
 
 class SvoCamera(C.Structure):

@@ -161,11 +161,14 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
         out[2] = p0 * Li[2] + p1 * Li[6] + p2 * Li[10];
         out[3] = p0 * Li[3] + p1 * Li[7] + p2 * Li[11] + p3;
       }
+      bool changed = false;  // against the pose of the previous refit (bitwise; NaN-filled at creation)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
+        changed |= __double_as_longlong(a.world[12 * i + 4 * r + c]) != __double_as_longlong(out[c]);
         sm.world[12 * i + 4 * r + c] = out[c];
         a.world[12 * i + 4 * r + c] = out[c];
       }
+      if (changed) a.dirty[i] = 1;
     }
     __syncthreads();
   }

@@ -316,7 +316,7 @@ __device__ __forceinline__ double rel_bound(const ExactState &s, double tmax, do
 
 struct Counters {
   uint32_t parts_tested, parts_entered, nodes, leaves, passes;
-  uint32_t f_winner, f_overlap, f_width;
+  uint32_t f_winner, f_overlap, f_width, reused;
 };
 
 // Front-to-back descent of one part in its local frame.  (o, d): local ray
@@ -610,7 +610,9 @@ template <bool STATS, int BLOCK>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
-                              uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt) {
+                              uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt,
+                              uint32_t reuse_part, const uint8_t *__restrict__ dirty, bool &reused) {
+  reused = false;
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
   st.cert1 = 0;
@@ -656,6 +658,15 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
             over_t = fminf(over_t, t);
           }
         }
+      }
+      // hit buffer reuse (Sec. IV-C, Fig. 5): the only sphere the ray meets is
+      // that of the part it hit last time, and that part has not moved, so
+      // the previous hit stands (other parts cannot occlude it)
+      if (need && last_p < 0 && reuse_part != kMissPart && ct[0] != Num<float>::inf() &&
+          ct[1] == Num<float>::inf() && over_t == Num<float>::inf() && (uint32_t)cp[0] == reuse_part &&
+          dirty[cp[0]] == 0) {
+        reused = true;
+        need = false;
       }
       if (need) {
         // visit in order of sphere entry, stop once the best hit is nearer
@@ -709,10 +720,10 @@ __device__ __forceinline__ int find_item(const TraceLaunchT<NI> &L, unsigned lon
 }
 
 __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters &c, uint32_t rays, uint32_t flagged) {
-  unsigned long long v[10] = {rays, flagged, c.parts_tested, c.parts_entered, c.nodes, c.leaves, c.passes,
-                              c.f_winner, c.f_overlap, c.f_width};
+  unsigned long long v[11] = {rays, flagged, c.parts_tested, c.parts_entered, c.nodes, c.leaves, c.passes,
+                              c.f_winner, c.f_overlap, c.f_width, c.reused};
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
+  for (int i = 0; i < 11; ++i) {
     unsigned long long x = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -729,6 +740,7 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
     atomicAdd(&st->flag_winner, v[7]);
     atomicAdd(&st->flag_overlap, v[8]);
     atomicAdd(&st->flag_width, v[9]);
+    atomicAdd(&st->reused, v[10]);
   }
 }
 
@@ -820,9 +832,16 @@ __global__ void __launch_bounds__(BLOCK, (STATS ? 512 : kTraceThreadsPerSM) / BL
       }
       CertState st;
       Contenders con;
-      trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt);
+      uint32_t reuse_part = kMissPart;
+      if ((L.flags & SVO_TRACE_REUSE) && active) reuse_part = reinterpret_cast<const uint32_t *>(&I.hits[ray])[1];
+      bool reused;
+      trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt,
+                                  reuse_part, I.dirty, reused);
       bool flagged = false, ids_ok = true;
-      if (in_range) {
+      if (in_range && reused) {
+        if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
+        if (STATS) ++cnt.reused;
+      } else if (in_range) {
         float t = Num<float>::inf();
         uint32_t part = kMissPart;
         unsigned long long vox = kMissVoxel;

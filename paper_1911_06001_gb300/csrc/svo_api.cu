@@ -101,6 +101,7 @@ struct svo_scene {
   PartStatic *d_stat = nullptr;
   int32_t *d_level_order = nullptr, *d_level_start = nullptr;
   float4 *d_bound = nullptr;
+  uint8_t *d_dirty = nullptr;  // per part: world pose changed since the scene's previous trace
   double *h_stage = nullptr;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
@@ -163,6 +164,7 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.hits = reinterpret_cast<uint4 *>(hits);
   it.ray_flags = flags;
   it.perm = nullptr;
+  it.dirty = s->d_dirty;
   it.n = n;
   it.tile_begin = 0;
   it.n_parts = s->P;
@@ -177,6 +179,9 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
 // bounds[i]: scene bound of item i (frame of origin-based ray ordering).
 svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays, const float4 *const *bounds,
                      void *stream) {
+  constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
+  if ((L.flags & SVO_TRACE_REUSE) && (L.flags & kReuseNeeds) != kReuseNeeds)
+    return fail(SVO_ERR_ARG, "SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
   cudaStream_t st = (cudaStream_t)stream;
   Slot *slot = nullptr;
   svo_status rc = get_slot(ctx, stream, total_rays, &slot);
@@ -218,6 +223,12 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.rays_per_lane = ctx->rays_per_lane;
   CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
   CK(launch_trace(L, ctx->n_sm, st));
+  // pose changes are tracked relative to each scene's latest trace
+  for (int i = 0; i < L.n_items; ++i) {
+    bool seen = false;
+    for (int j = 0; j < i; ++j) seen = seen || L.items[j].dirty == L.items[i].dirty;
+    if (!seen) CK(cudaMemsetAsync(const_cast<uint8_t *>(L.items[i].dirty), 0, (size_t)L.items[i].n_parts, st));
+  }
   delete slot->pending;
   slot->pending = nullptr;
   if (L.flags & SVO_TRACE_FP64_FIX) {
@@ -472,7 +483,8 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   size_t off_lo = al(off_stat + P * sizeof(PartStatic));
   size_t off_ls = al(off_lo + P * sizeof(int32_t));
   size_t off_bd = al(off_ls + (L + 1) * sizeof(int32_t));
-  size_t total = al(off_bd + sizeof(float4));
+  size_t off_dirty = al(off_bd + sizeof(float4));
+  size_t total = al(off_dirty + P);
   CK(cudaSetDevice(ctx->device));
   svo_scene *s = new svo_scene();
   s->ctx = ctx;
@@ -498,11 +510,15 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   s->d_level_order = reinterpret_cast<int32_t *>(s->d_mem + off_lo);
   s->d_level_start = reinterpret_cast<int32_t *>(s->d_mem + off_ls);
   s->d_bound = reinterpret_cast<float4 *>(s->d_mem + off_bd);
+  s->d_dirty = reinterpret_cast<uint8_t *>(s->d_mem + off_dirty);
   std::vector<double> ident(P * 12, 0.0);
   for (int i = 0; i < P; ++i) ident[12 * i + 0] = ident[12 * i + 5] = ident[12 * i + 10] = 1.0;
   e = cudaMallocHost(&s->h_stage, P * 12 * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_stage, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_local, ident.data(), P * 12 * sizeof(double), cudaMemcpyHostToDevice);
+  // no pose yet: NaN world poses make the first refit mark every part changed
+  if (e == cudaSuccess) e = cudaMemset(s->d_world, 0xFF, P * 12 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s->d_dirty, 1, P);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_stat, stat.data(), P * sizeof(PartStatic), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_level_order, lorder.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_level_start, lstart.data(), (L + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -599,6 +615,7 @@ svo_status scene_refit(svo_scene *s, void *stream) {
   a.order = s->d_order;
   a.n_clusters = s->NC;
   a.bound = s->d_bound;
+  a.dirty = s->d_dirty;
   a.err = s->ctx->d_err;
   CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
   s->host_pending = false;

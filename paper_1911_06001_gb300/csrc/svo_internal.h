@@ -74,6 +74,7 @@ struct TraceItem {
   uint4 *hits;          // svo_hit per ray
   uint32_t *ray_flags;  // or nullptr
   const uint32_t *perm; // visiting order of the rays (nullptr = index order)
+  const uint8_t *dirty; // per part: pose changed since the scene's previous trace (SVO_TRACE_REUSE)
   unsigned long long n;
   unsigned long long tile_begin;
   int32_t n_parts;
@@ -172,6 +173,7 @@ struct RefitArgs {
   int32_t *order;
   int32_t n_clusters;
   float4 *bound;  // sphere enclosing every part sphere (ray-ordering frame)
+  uint8_t *dirty; // set to 1 for every part whose world pose changes (cleared by each trace)
   unsigned int *err;
 };
 // host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses

@@ -84,6 +84,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: rays and hits must be 16-byte aligned");
   if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX))
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: STATS and DEFER_FIX are not supported");
+  constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
+  if ((flags & SVO_TRACE_REUSE) && (flags & kReuseNeeds) != kReuseNeeds)
+    return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
   const int dev = scene_device(s);
   if (dev < 0 || dev >= kMaxDevices) return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: bad device");
   cudaError_t e = cudaSetDevice(dev);
@@ -116,6 +119,8 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   // clear what the kernels expect at zero: the tile counter and the list count
   e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = launch_trace(*L, scene_sm_count(s), st);
+  if (e == cudaSuccess)  // pose changes are tracked relative to the scene's latest trace
+    e = cudaMemsetAsync(const_cast<uint8_t *>(L->items[0].dirty), 0, (size_t)L->items[0].n_parts, st);
   if (e == cudaSuccess && (flags & SVO_TRACE_FP64_FIX)) e = launch_fix(*L, scene_sm_count(s), st);
   if (e != cudaSuccess) {
     std::string m = std::string("trace_rays_noalloc: ") + cudaGetErrorString(e);
