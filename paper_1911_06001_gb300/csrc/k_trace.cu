@@ -947,9 +947,9 @@ __device__ __forceinline__ void write_fixed(const TraceItem &I, unsigned long lo
 // over the warps so that a short list still spreads over the whole GPU.
 template <int NI>
 __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLaunchT<NI> L) {
-  __shared__ __align__(16) Tables tab;
-  load_tables(&tab);
-  __syncthreads();
+  // the rare re-traces read the order tables from global memory (L1/L2), so
+  // blocks start without staging them
+  const Tables *tab = &g_tables;
   unsigned int err = 0;
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   const unsigned long long n = min((unsigned long long)*L.fix_count, L.fix_capacity);
@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
         if (!part_cull(r, I.hot[p], tin, tref)) continue;
         if (tin > __double2float_ru(hs.ex.t)) continue;  // every candidate of p starts after the best hit
         hs.inv64 = I.inv64 + 12 * p;
-        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, &tab, stk_local, hs, nullptr,
+        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs, nullptr,
                                               err, cnt);
       }
       write_fixed(I, ray, hs.ex, why);
