@@ -659,14 +659,24 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
           }
         }
       }
-      // hit buffer reuse (Sec. IV-C, Fig. 5): the only sphere the ray meets is
-      // that of the part it hit last time, and that part has not moved, so
-      // the previous hit stands (other parts cannot occlude it)
-      if (need && last_p < 0 && reuse_part != kMissPart && ct[0] != Num<float>::inf() &&
-          ct[1] == Num<float>::inf() && over_t == Num<float>::inf() && (uint32_t)cp[0] == reuse_part &&
-          dirty[cp[0]] == 0) {
-        reused = true;
-        need = false;
+      // hit buffer reuse (Sec. IV-C, Fig. 5).  The paper reuses a pixel whose
+      // ray meets one sphere, that of its unmoved previous part.  The same
+      // holds whenever every part whose sphere the ray meets is unmoved and
+      // the previous part is among them: unmoved parts keep their spheres and
+      // their closest leaves along the ray, so the candidates are a subset
+      // of the previous ones that still contains the previous winner.
+      if (need && last_p < 0 && reuse_part != kMissPart && over_t == Num<float>::inf()) {
+        bool clean = true, found = false;
+#pragma unroll
+        for (int i = 0; i < kCap; ++i) {
+          if (ct[i] == Num<float>::inf()) continue;
+          clean = clean && dirty[cp[i]] == 0;
+          found = found || (uint32_t)cp[i] == reuse_part;
+        }
+        if (clean && found) {
+          reused = true;
+          need = false;
+        }
       }
       if (need) {
         // visit in order of sphere entry, stop once the best hit is nearer
