@@ -79,9 +79,9 @@ typedef int32_t svo_status;
 #define SVO_TRACE_REUSE 256u /* hit buffer reuse (Sec. IV-C, Fig. 5): the hits buffer holds this scene's
                                 result for the same rays from the scene's previous trace (a static
                                 camera); a ray whose intersected part spheres (at most 4) all belong to
-                                parts whose poses have not changed in any refit since that trace, among
-                                them the part it hit then, keeps its hit without a descent (ray flag
-                                SVO_RAY_REUSED).  Needs CULL | SORT | FP64_FIX, as the previous trace
+                                parts whose poses have not changed in any refit since that trace, and
+                                whose previous hit was a miss or on such a part, keeps its hit without a
+                                descent (ray flag SVO_RAY_REUSED).  Needs CULL | SORT | FP64_FIX, as the previous trace
                                 must have had; every trace of a scene restarts its change tracking. */
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 

@@ -611,7 +611,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
                               uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt,
-                              uint32_t reuse_part, const uint8_t *__restrict__ dirty, bool &reused) {
+                              bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused) {
   reused = false;
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
@@ -662,18 +662,17 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       // hit buffer reuse (Sec. IV-C, Fig. 5).  The paper reuses a pixel whose
       // ray meets one sphere, that of its unmoved previous part.  The same
       // holds whenever every part whose sphere the ray meets is unmoved and
-      // the previous part is among them: unmoved parts keep their spheres and
-      // their closest leaves along the ray, so the candidates are a subset
-      // of the previous ones that still contains the previous winner.
-      if (need && last_p < 0 && reuse_part != kMissPart && over_t == Num<float>::inf()) {
-        bool clean = true, found = false;
+      // so is the previous winner (or there was none): unmoved parts keep
+      // their spheres and their closest leaves along the ray, so the
+      // candidates are a subset of the previous ones, and they contain the
+      // previous winner, whose sphere is still met.
+      if (need && reuse && last_p < 0 && ct[0] != Num<float>::inf() && over_t == Num<float>::inf() &&
+          (prev_part == kMissPart || (prev_part < (uint32_t)P && dirty[prev_part] == 0))) {
+        bool clean = true;
 #pragma unroll
-        for (int i = 0; i < kCap; ++i) {
-          if (ct[i] == Num<float>::inf()) continue;
-          clean = clean && dirty[cp[i]] == 0;
-          found = found || (uint32_t)cp[i] == reuse_part;
-        }
-        if (clean && found) {
+        for (int i = 0; i < kCap; ++i)
+          if (ct[i] != Num<float>::inf()) clean = clean && dirty[cp[i]] == 0;
+        if (clean) {
           reused = true;
           need = false;
         }
@@ -842,11 +841,11 @@ __global__ void __launch_bounds__(BLOCK, (STATS ? 512 : kTraceThreadsPerSM) / BL
       }
       CertState st;
       Contenders con;
-      uint32_t reuse_part = kMissPart;
-      if ((L.flags & SVO_TRACE_REUSE) && active) reuse_part = reinterpret_cast<const uint32_t *>(&I.hits[ray])[1];
+      const bool reuse = (L.flags & SVO_TRACE_REUSE) && active;
+      const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
       trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt,
-                                  reuse_part, I.dirty, reused);
+                                  reuse, prev_part, I.dirty, reused);
       bool flagged = false, ids_ok = true;
       if (in_range && reused) {
         if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
