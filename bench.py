@@ -536,7 +536,7 @@ def main() -> None:
                 ev[0].record(stream)
                 sc.set_transforms(poses[f], stream=stream)
                 sc.refit(stream=stream)
-                sc.trace_host(rays_h, hits_h, flags=g.TRACE_DEFAULT, stream=stream)
+                sc.trace_host(rays_h, hits_h, flags=g.TRACE_DEFAULT | order, stream=stream)
                 ev[1].record(stream)
                 if s >= args.warmup:
                     e2e_ev.append(ev)

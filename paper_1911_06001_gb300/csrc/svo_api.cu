@@ -67,6 +67,8 @@ struct Slot {
   unsigned long long cand_cap = 0;
   TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
   char *d_stage = nullptr;                   // rays | hits | flags staging of trace_rays_host
+  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};  // trace_rays_host: copy in, trace, copy out
+  std::vector<cudaEvent_t> pipe_ev;                    // 2 per chunk + 2
   unsigned long long stage_rays = 0;
   void *d_order = nullptr;                   // ray-ordering keys, histogram and permutations
   size_t order_cap = 0;
@@ -320,6 +322,9 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
     if (kv.second.d_cand) cudaFree(kv.second.d_cand);
     if (kv.second.d_stage) cudaFree(kv.second.d_stage);
     if (kv.second.d_order) cudaFree(kv.second.d_order);
+    for (cudaStream_t ps : kv.second.pipe)
+      if (ps) cudaStreamDestroy(ps);
+    for (cudaEvent_t e : kv.second.pipe_ev) cudaEventDestroy(e);
     delete kv.second.pending;
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -752,15 +757,30 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   if (n == 0) return ok();
   if (!rays_host || !hits_host) return fail(SVO_ERR_ARG, "trace_rays_host: rays/hits is NULL");
   if (flags & SVO_TRACE_STATS) return fail(SVO_ERR_ARG, "trace_rays_host: STATS needs a device stats buffer");
+  if (flags & SVO_TRACE_REUSE) return fail(SVO_ERR_ARG, "trace_rays_host: REUSE needs the previous hits on the device");
+  if (n > 0xFFFFFFFFull) return fail(SVO_ERR_LIMIT, "trace_rays_host: %llu rays", (unsigned long long)n);
   CK(cudaSetDevice(s->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  // Chunks of ~512 K rays (whole image rows with SVO_TRACE_IMAGE) are copied
+  // in, traced (with their FP64 pass) and copied out on three streams, so
+  // that the copies of one chunk overlap the trace of another.
+  constexpr unsigned long long kChunk = 1ull << 19;
+  unsigned long long chunk = kChunk;
+  if (flags & SVO_TRACE_IMAGE_TILES) {
+    const unsigned long long w = flags >> 16;
+    if (w > 0) chunk = (kChunk / w > 0 ? kChunk / w : 1) * w;
+  }
+  const unsigned long long n_chunks = (n + chunk - 1) / chunk;
   char *stage = nullptr;
+  Slot *slp = nullptr;
   {
     std::lock_guard<std::mutex> g(s->ctx->mu);
     Slot &sl = s->ctx->slots[stream];
     if (n > sl.stage_rays) {
       if (sl.d_stage) {
         CK(cudaStreamSynchronize(st));
+        for (cudaStream_t ps : sl.pipe)
+          if (ps) CK(cudaStreamSynchronize(ps));
         CK(cudaFree(sl.d_stage));
         sl.d_stage = nullptr;
         sl.stage_rays = 0;
@@ -769,17 +789,43 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
       if (e != cudaSuccess) return fail(SVO_ERR_OOM, "trace_rays_host: staging: %s", cudaGetErrorString(e));
       sl.stage_rays = n;
     }
+    for (cudaStream_t &ps : sl.pipe)
+      if (!ps) CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+    while (sl.pipe_ev.size() < 2 * n_chunks + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      sl.pipe_ev.push_back(e);
+    }
     stage = sl.d_stage;
+    slp = &sl;
   }
-  const unsigned long long cap = s->ctx->slots[stream].stage_rays;
+  const unsigned long long cap = slp->stage_rays;
   float *d_rays = reinterpret_cast<float *>(stage);
   svo_hit *d_hits = reinterpret_cast<svo_hit *>(stage + cap * 32);
   uint32_t *d_flags = ray_flags_host ? reinterpret_cast<uint32_t *>(stage + cap * 48) : nullptr;
-  CK(cudaMemcpyAsync(d_rays, rays_host, n * 32, cudaMemcpyHostToDevice, st));
-  svo_status rc = trace_rays(s, d_rays, n, d_hits, d_flags, flags & ~SVO_TRACE_DEFER_FIX, nullptr, stream);
-  if (rc != SVO_OK) return rc;
-  CK(cudaMemcpyAsync(hits_host, d_hits, n * 16, cudaMemcpyDeviceToHost, st));
-  if (d_flags) CK(cudaMemcpyAsync(ray_flags_host, d_flags, n * 4, cudaMemcpyDeviceToHost, st));
+  cudaStream_t h2d = slp->pipe[0], comp = slp->pipe[1], d2h = slp->pipe[2];
+  cudaEvent_t *ev = slp->pipe_ev.data();
+  // the pipeline starts after the caller's earlier work (poses, refit) ...
+  CK(cudaEventRecord(ev[0], st));
+  CK(cudaStreamWaitEvent(h2d, ev[0], 0));
+  CK(cudaStreamWaitEvent(comp, ev[0], 0));
+  CK(cudaStreamWaitEvent(d2h, ev[0], 0));
+  for (unsigned long long k = 0; k < n_chunks; ++k) {
+    const unsigned long long off = k * chunk, m = (n - off) < chunk ? (n - off) : chunk;
+    CK(cudaMemcpyAsync(d_rays + off * 8, rays_host + off * 8, m * 32, cudaMemcpyHostToDevice, h2d));
+    CK(cudaEventRecord(ev[2 + 2 * k], h2d));
+    CK(cudaStreamWaitEvent(comp, ev[2 + 2 * k], 0));
+    svo_status rc = trace_rays(s, d_rays + off * 8, m, d_hits + off, d_flags ? d_flags + off : nullptr,
+                               flags & ~SVO_TRACE_DEFER_FIX, nullptr, comp);
+    if (rc != SVO_OK) return rc;
+    CK(cudaEventRecord(ev[3 + 2 * k], comp));
+    CK(cudaStreamWaitEvent(d2h, ev[3 + 2 * k], 0));
+    CK(cudaMemcpyAsync(hits_host + off, d_hits + off, m * 16, cudaMemcpyDeviceToHost, d2h));
+    if (d_flags) CK(cudaMemcpyAsync(ray_flags_host + off, d_flags + off, m * 4, cudaMemcpyDeviceToHost, d2h));
+  }
+  // ... and the caller's stream continues once every chunk is back
+  CK(cudaEventRecord(ev[1], d2h));
+  CK(cudaStreamWaitEvent(st, ev[1], 0));
   return ok();
 }
 

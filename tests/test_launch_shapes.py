@@ -134,3 +134,39 @@ def test_frame_graph_replays_match_eager_frames(ctx):
         for k in ("t", "part", "voxel"):
             assert np.array_equal(got[k], ref[k]), (frame, k)
         assert (ref["part"] != 0xFFFFFFFF).sum() > 200
+
+
+def test_host_buffers_equal_device_trace(ctx):
+    """trace_rays_host pipelines chunks of rays through copy-in, trace and
+    copy-out streams: hits and flags equal the device trace, with and without
+    the image layout, pinned or pageable."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    s = synthetic.pr1_scene()
+    gs = GpuScene(ctx, s)
+    rng = np.random.default_rng(12)
+    n = 1_300_001  # three chunks and a ragged end
+    rays = synthetic.random_rays(n, rng, (-3,) * 3, (3,) * 3)
+    rays[: n // 2] = np.resize(synthetic.pr1_rays(s), (n // 2, 8))
+    ctx.set_trace_config(128, 1)
+    for flags in (g.TRACE_DEFAULT, g.TRACE_DEFAULT | g.trace_image(1000)):
+        ref = gs.trace(rays, flags)
+        rh = torch.from_numpy(np.ascontiguousarray(rays, dtype=np.float32)).pin_memory()
+        hh = torch.empty((n, 2), dtype=torch.int64).pin_memory()
+        fh = torch.zeros(n, dtype=torch.int32).pin_memory()
+        gs.sc.trace_host(rh, hh, flags=flags, ray_flags_host=fh)
+        torch.cuda.synchronize()
+        got = g.decode_hits(hh)
+        got["flags"] = fh.numpy().astype(np.uint32)
+        _same(got, ref)
+    hp = torch.empty((1000, 2), dtype=torch.int64)  # pageable
+    gs.sc.trace_host(torch.from_numpy(np.ascontiguousarray(rays[:1000], dtype=np.float32)), hp)
+    torch.cuda.synchronize()
+    ref = gs.trace(rays[:1000], g.TRACE_DEFAULT)
+    got = g.decode_hits(hp)
+    assert np.array_equal(got["part"], ref["part"]) and np.array_equal(got["voxel"], ref["voxel"])
+    with pytest.raises(g.SvoError):
+        gs.sc.trace_host(torch.zeros((8, 8)), torch.zeros((8, 2), dtype=torch.int64), flags=g.TRACE_DEFAULT | g.TRACE_REUSE)
+    ctx.set_trace_config(128, 4)
