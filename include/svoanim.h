@@ -253,16 +253,20 @@ svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *
 svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_items, uint32_t flags,
                        svo_trace_stats *stats, void *stream);
 
-/* trace_rays for rays and hits in HOST memory (async on `stream`): the library
- * copies rays to its per-stream device staging, traces, and copies hits (and
- * ray_flags, if not NULL) back.  The rays go in chunks of about 512 K (whole
- * image rows with SVO_TRACE_IMAGE) through three internal streams, so that
- * one chunk's copies overlap another's trace; `stream` resumes after the last
- * chunk is back.  With pinned (page-locked) host buffers the call returns
- * before the copies finish: synchronise `stream` before reading hits.
- * Pageable buffers are allowed (the copies then block the host).  Grows the
- * staging with cudaMalloc when n exceeds the largest n traced so far on this
- * stream.  SVO_TRACE_STATS and SVO_TRACE_REUSE are not supported here
+/* trace_rays for rays and hits in HOST memory (async on `stream`).
+ *   * Page-locked buffers mapped into the device's address space (e.g.
+ *     cudaHostAlloc'ed; on GB300 reached over the chip-to-chip link) are read
+ *     and written by the kernels directly, with no staging copy.
+ *   * Other buffers are staged: the library copies rays to its per-stream
+ *     device staging, traces, and copies hits (and ray_flags, if not NULL)
+ *     back, in chunks of about 512 K rays (whole image rows with
+ *     SVO_TRACE_IMAGE) through three internal streams so that one chunk's
+ *     copies overlap another's trace; `stream` resumes after the last chunk
+ *     is back.  Pageable buffers make the copies block the host.  The staging
+ *     grows with cudaMalloc when n exceeds the largest n staged so far on
+ *     this stream.
+ * The call returns before the work finishes: synchronise `stream` before
+ * reading hits.  SVO_TRACE_STATS and SVO_TRACE_REUSE are not supported here
  * (SVO_ERR_ARG); SVO_TRACE_DEFER_FIX is ignored. */
 svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n, svo_hit *hits_host,
                            uint32_t *ray_flags_host, uint32_t flags, void *stream);

@@ -751,6 +751,18 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
   return ok();
 }
 
+// Device address of page-locked host memory mapped into the device's address
+// space, or nullptr (pageable memory, or not mapped).
+static void *mapped_device_pointer(const void *host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unregistered pointer
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+  return at.devicePointer;
+}
+
 svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo_hit *hits_host,
                            uint32_t *ray_flags_host, uint32_t flags, void *stream) {
   if (!s) return fail(SVO_ERR_ARG, "trace_rays_host: scene is NULL");
@@ -761,7 +773,19 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   if (n > 0xFFFFFFFFull) return fail(SVO_ERR_LIMIT, "trace_rays_host: %llu rays", (unsigned long long)n);
   CK(cudaSetDevice(s->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  // Chunks of ~512 K rays (whole image rows with SVO_TRACE_IMAGE) are copied
+  // Page-locked buffers that the device can address (on GB300 over the
+  // chip-to-chip link) are read and written by the kernels directly: the
+  // trace streams its rays in and its hits out, with no staging copy.
+  {
+    const void *dev_rays = mapped_device_pointer(rays_host);
+    void *dev_hits = mapped_device_pointer(hits_host);
+    void *dev_flags = ray_flags_host ? mapped_device_pointer(ray_flags_host) : nullptr;
+    if (dev_rays && dev_hits && (!ray_flags_host || dev_flags) && !(reinterpret_cast<uintptr_t>(dev_rays) & 15) &&
+        !(reinterpret_cast<uintptr_t>(dev_hits) & 15))
+      return trace_rays(s, static_cast<const float *>(dev_rays), n, static_cast<svo_hit *>(dev_hits),
+                        static_cast<uint32_t *>(dev_flags), flags & ~SVO_TRACE_DEFER_FIX, nullptr, stream);
+  }
+  // Otherwise chunks of ~512 K rays (whole image rows with SVO_TRACE_IMAGE) are copied
   // in, traced (with their FP64 pass) and copied out on three streams, so
   // that the copies of one chunk overlap the trace of another.
   constexpr unsigned long long kChunk = 1ull << 19;

@@ -83,8 +83,10 @@ def test_reuse_keeps_unmoved_hits_and_matches_oracle(ctx):
     assert np.array_equal(got["part"][same], f2["part"][same])
     assert np.array_equal(got["voxel"][same], f2["voxel"][same])
 
-    # frame 2: a root pose change moves every part -> nothing is reused
+    # frame 2: a root translation moves every part -> nothing is reused
     pose2 = fig.pose(40)
+    pose2[0] = pose2[0].copy()
+    pose2[0][[3, 7, 11]] += (0.01, -0.02, 0.015)
     sc.set_transforms(pose2)
     sc.refit()
     st = g.new_stats()

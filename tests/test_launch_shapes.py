@@ -153,14 +153,17 @@ def test_host_buffers_equal_device_trace(ctx):
     ctx.set_trace_config(128, 1)
     for flags in (g.TRACE_DEFAULT, g.TRACE_DEFAULT | g.trace_image(1000)):
         ref = gs.trace(rays, flags)
-        rh = torch.from_numpy(np.ascontiguousarray(rays, dtype=np.float32)).pin_memory()
-        hh = torch.empty((n, 2), dtype=torch.int64).pin_memory()
-        fh = torch.zeros(n, dtype=torch.int32).pin_memory()
-        gs.sc.trace_host(rh, hh, flags=flags, ray_flags_host=fh)
-        torch.cuda.synchronize()
-        got = g.decode_hits(hh)
-        got["flags"] = fh.numpy().astype(np.uint32)
-        _same(got, ref)
+        for pinned in (True, False):  # mapped: kernels read/write host memory; pageable: staged chunks
+            rh = torch.from_numpy(np.ascontiguousarray(rays, dtype=np.float32))
+            hh = torch.empty((n, 2), dtype=torch.int64)
+            fh = torch.zeros(n, dtype=torch.int32)
+            if pinned:
+                rh, hh, fh = rh.pin_memory(), hh.pin_memory(), fh.pin_memory()
+            gs.sc.trace_host(rh, hh, flags=flags, ray_flags_host=fh)
+            torch.cuda.synchronize()
+            got = g.decode_hits(hh)
+            got["flags"] = fh.numpy().astype(np.uint32)
+            _same(got, ref)
     hp = torch.empty((1000, 2), dtype=torch.int64)  # pageable
     gs.sc.trace_host(torch.from_numpy(np.ascontiguousarray(rays[:1000], dtype=np.float32)), hp)
     torch.cuda.synchronize()
