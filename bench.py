@@ -598,7 +598,8 @@ def main() -> None:
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": (3 + (3 if order else 0)) * args.steps,
+            # per frame: k_refit, k_trace, k_fix, plus the three ray-ordering kernels for dir/origin orders
+            "gpu_launches": (3 + (3 if order & (g.TRACE_ORDER_DIR | g.TRACE_ORDER_ORIGIN) else 0)) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
         }
