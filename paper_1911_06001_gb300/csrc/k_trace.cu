@@ -165,18 +165,13 @@ struct Num<double> {
 };
 
 // t of the plane x_i = P along a mirrored axis with reciprocal direction inv
-// and b = -o*inv.  FP32 uses one FMA (its rounding is part of the error bound
-// behind eta); FP64 subtracts first so that the sign of P - o is exact, which
-// decides slabs of direction components that are exactly zero.
+// and b = -o*inv: one FMA, whose rounding is part of the error bound behind
+// eta.
 template <typename R>
 struct Slab;
 template <>
 struct Slab<float> {
   __device__ static float t(float P, float inv, float, float b) { return fmaf(P, inv, b); }
-};
-template <>
-struct Slab<double> {
-  __device__ static double t(double P, double inv, double o, double) { return (P - o) * inv; }
 };
 
 // FP32 per-ray state of the certified closest-hit search.
@@ -312,17 +307,17 @@ __device__ __forceinline__ float prune_bound(const CertState &s, float tmax) { r
 __device__ __forceinline__ float rel_bound(const CertState &s, float tmax_rel, float tshift) {
   return fminf(tmax_rel, __fsub_ru(s.hi_min, tshift));
 }
-__device__ __forceinline__ double rel_bound(const ExactState &s, double tmax, double) { return fmin(tmax, s.t); }
 
 struct Counters {
   uint32_t parts_tested, parts_entered, nodes, leaves, passes;
   uint32_t f_winner, f_overlap, f_width, reused;
 };
 
-// Front-to-back descent of one part in its local frame.  (o, d): local ray
-// whose parameter is t - tshift; tmin/tmax are in that shifted parameter;
-// eta: inflation (0 for the exact FP64 search, whose tshift is 0).  State S is
-// CertState (R = float, certified) or ExactState (R = double).
+// Front-to-back descent of one part in its local frame, in FP32 with boxes
+// inflated by eta.  (o, d): local ray whose parameter is t - tshift;
+// tmin/tmax are in that shifted parameter.  State S is CertState (the
+// certified search: leaves give entry bounds) or HybridState (the FP64 pass's
+// re-trace: every leaf reached is decided by leaf_entry64).
 template <typename R, typename S, bool STATS, int STRIDE>
 __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
                                              int D, R ox, R oy,
@@ -437,7 +432,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
             double tq;
             if (leaf_entry64(st.inv64, D, vox, st.o, st.d, tq)) offer(st.ex, tq, part, vox);
           } else {
-            offer(st, lo, part, vox);
+            static_assert(CERT || HYBRID, "descend_part: CertState or HybridState");
           }
         }
         break;
