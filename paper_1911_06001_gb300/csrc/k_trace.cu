@@ -74,7 +74,8 @@ constexpr int kBlock = 128;  // block size of the FP64 pass; the trace kernel ta
 //     warps), 0.327 ms at 128 (16 warps), flat from 16 to 24 warps;
 //   * incoherent rays against ~120 parts: 9% faster at 24 warps than at 16;
 //   * 32 warps (64 registers) spill and lose.
-// The counting (STATS) build keeps 16 warps: its counters would spill at 80.
+// The counting (STATS) and hit-buffer (REUSE) builds keep 16 warps: they would
+// spill at 80.
 constexpr int kTraceThreadsPerSM = 768;
 
 constexpr unsigned long long kRayBits = 40;
@@ -748,8 +749,10 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
   }
 }
 
-template <int NI, bool STATS, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (STATS ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+// REUSE: hit buffer reuse compiled in (a separate instantiation, so that the
+// common kernel carries none of its registers or tests).
+template <int NI, bool STATS, int BLOCK, bool REUSE>
+__global__ void __launch_bounds__(BLOCK, (STATS || REUSE ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
@@ -836,7 +839,7 @@ __global__ void __launch_bounds__(BLOCK, (STATS ? 512 : kTraceThreadsPerSM) / BL
       }
       CertState st;
       Contenders con;
-      const bool reuse = (L.flags & SVO_TRACE_REUSE) && active;
+      const bool reuse = REUSE && active;
       const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
       trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt,
@@ -1032,7 +1035,9 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
   const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
                                        L.one_scene ? L.items[0].n_clusters : 0, BLOCK);
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
-  auto kern = stats ? k_trace<NI, true, BLOCK> : k_trace<NI, false, BLOCK>;
+  const bool reuse = (L.flags & SVO_TRACE_REUSE) != 0;
+  auto kern = stats ? (reuse ? k_trace<NI, true, BLOCK, true> : k_trace<NI, true, BLOCK, false>)
+                    : (reuse ? k_trace<NI, false, BLOCK, true> : k_trace<NI, false, BLOCK, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
