@@ -26,6 +26,7 @@ from .scenes import (  # noqa: F401
     pr1_rays,
     ArticulatedFigure,
     articulated_figure,
+    static_union,
     random_rays,
     PoolAsset,
     asset_pool,

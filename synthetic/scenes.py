@@ -383,6 +383,49 @@ class ArticulatedFigure:
         return pinhole_rays(m["eye"], m["target"], width, height, 60.0)
 
 
+def _sorted_unique(ids: np.ndarray) -> np.ndarray:
+    s = np.sort(ids)
+    if s.size == 0:
+        return s
+    keep = np.empty(s.shape, dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
+def static_union(scene: Scene, world, depth: int = 12, origin: float = -4.0, extent: float = 8.0):
+    """The posed scene resampled into one static SVO in world space (the
+    paper's "static model" comparison scene): every leaf of every part is
+    sampled at 4 inset points (alternate corners of its 2x2x2 subcells), each mapped by
+    its part's world pose into a 2^depth grid over the cube [origin,
+    origin + extent]^3; occupied grid cells become the leaves (colour: the
+    spatial hash of the grid cell).  Returns (Asset, world pose of the grid's
+    unit cube as 12 float64)."""
+    world = np.asarray(world, dtype=np.float64).reshape(-1, 12)
+    n = 1 << depth
+    cell = extent / n
+    # four inset points of a leaf (alternate corners of its 2x2x2 subcells)
+    offs = np.array([[0.25, 0.25, 0.25], [0.75, 0.75, 0.25], [0.75, 0.25, 0.75], [0.25, 0.75, 0.75]])
+    per_part = []
+    for p in range(scene.n_parts):
+        a = scene.assets[int(scene.part_asset[p])]
+        if a.n_leaves == 0:
+            continue
+        x, y, z = unpack_ids(a.leaf_ids, a.depth)
+        base = np.stack([x, y, z], 1).astype(np.float64)
+        W = world[p].reshape(3, 4)
+        got = []
+        for o in offs:
+            loc = (base + o) / float(1 << a.depth)
+            g = np.floor((loc @ W[:, :3].T + W[:, 3] - origin) / cell).astype(np.int64)
+            ok = np.all((g >= 0) & (g < n), axis=1)
+            got.append(pack_ids(g[ok, 0], g[ok, 1], g[ok, 2], depth))
+        per_part.append(_sorted_unique(np.concatenate(got)))
+    ids = _sorted_unique(np.concatenate(per_part)) if per_part else np.zeros(0, np.uint64)
+    pose = affine12(np.eye(3) * extent, np.full(3, origin))
+    return Asset(depth=depth, leaf_ids=ids, rgb=rgb_hash(*unpack_ids(ids, depth))), pose
+
+
 def _rot_z_to(v) -> np.ndarray:
     """A rotation taking +z to the unit vector v."""
     v = np.asarray(v, dtype=np.float64)

@@ -555,3 +555,21 @@ def test_shade_rigid_invariance_and_scaled_normals():
     ray = np.array([[0.5, -1.0, 0.25, 0.0, 0.0, 1.0, 0.0, np.inf]])
     (sh, amb), hits = _shade_one(1, [(0, 0, 0)], [0xFFFFFF], W, ray, [0.0, -1.0, 0.0], 0.0)
     assert hits["part"][0] == 0 and sh[0] == 0xFFFFFF and not amb[0]
+
+
+def test_static_union_closed_forms():
+    """The static comparison scene (a posed scene resampled into one world
+    grid): a grid-aligned identity part reproduces its own leaves, and a
+    whole-cell translation shifts them."""
+    a = synthetic.make_asset(4, synthetic.noise_voxels(4, 0.05, np.random.default_rng(3)))
+    scene = synthetic.Scene("one", [a], np.array([0], np.int32), np.array([-1], np.int32),
+                            synthetic.affine12(np.eye(3), np.zeros(3))[None])
+    u, pose = synthetic.static_union(scene, scene.local, depth=4, origin=0.0, extent=1.0)
+    assert np.array_equal(u.leaf_ids, np.sort(a.leaf_ids))
+    assert np.allclose(pose, synthetic.affine12(np.eye(3), np.zeros(3)))
+    # translate by (2, 1, 0) cells of 1/16 inside a grid of twice the extent (cells of 1/8 at depth 4)
+    shifted = synthetic.affine12(np.eye(3), np.array([2, 1, 0]) / 16.0)[None]
+    u2, _ = synthetic.static_union(scene, shifted, depth=5, origin=0.0, extent=2.0)
+    x, y, z = synthetic.unpack_ids(a.leaf_ids, 4)
+    want = np.unique(synthetic.pack_ids(x + 2, y + 1, z, 5))
+    assert np.array_equal(u2.leaf_ids, want)
