@@ -161,7 +161,7 @@ const char *svo_status_string(svo_status s);
 /* Launch shape of the trace kernel for this context's later traces: threads
  * per block (64, 128 or 256) and rays per lane of a warp's tile (1, 2, 4 or 8;
  * a warp takes 32 * rays_per_lane rays at a time from the work counter).
- * Results do not depend on it; the autotuner picks it.  Default 128 / 4. */
+ * Results do not depend on it; the autotuner picks it.  Default 128 / 1. */
 svo_status svo_set_trace_config(svo_ctx *ctx, int32_t block, int32_t rays_per_lane);
 svo_status svo_get_trace_config(svo_ctx *ctx, int32_t *block, int32_t *rays_per_lane);
 /* Read and clear the context's device error word (synchronises the device).

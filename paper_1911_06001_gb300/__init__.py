@@ -98,7 +98,7 @@ class Context:
     def scene(self, part_assets, parent) -> "Scene":
         return Scene(self, part_assets, parent)
 
-    def set_trace_config(self, block: int = 128, rays_per_lane: int = 4) -> None:
+    def set_trace_config(self, block: int = 128, rays_per_lane: int = 1) -> None:
         _lib.check(self.lib.svo_set_trace_config(self.h, int(block), int(rays_per_lane)))
 
     def trace_config(self) -> tuple:

@@ -66,7 +66,7 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
         table.append({"block": b, "rays_per_lane": r, "order": o, "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
     best = min(table, key=lambda x: x["ms"])
-    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 4 and x["order"] == "none"), None)
+    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"), None)
     result = dict(best)
     result["default_ms"] = default["ms"] if default else None
     result["n_rays"] = int(rays.shape[0])

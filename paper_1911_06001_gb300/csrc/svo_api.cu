@@ -80,7 +80,7 @@ struct svo_ctx {
   int device = 0;
   int n_sm = 1;
   int block = 128;         // trace kernel block size
-  int rays_per_lane = 4;   // warp tile = 32 * rays_per_lane rays
+  int rays_per_lane = 1;   // warp tile = 32 * rays_per_lane rays (1: finest load balance)
   std::mutex mu;
   std::vector<AssetRec> assets;
   std::unordered_set<svo_scene *> scenes;

@@ -104,7 +104,7 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->n_items = 1;
   L->flags = flags;
   L->stats = nullptr;
-  int block = 128, rpl = 4;
+  int block = 128, rpl = 1;
   scene_trace_config(s, &block, &rpl);
   L->block = block;
   L->rays_per_lane = rpl;
