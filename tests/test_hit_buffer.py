@@ -110,6 +110,21 @@ def test_reuse_keeps_unmoved_hits_and_matches_oracle(ctx):
     compare(scene, pose3b, rays_np, got3, so.trace(rays_np, local=pose3b))
     assert ((got3["flags"] & g.RAY_REUSED) != 0).sum() > 0
 
+    # reuse composes with the ray order and the image layout (hits stay at each ray's own index)
+    for extra in (g.TRACE_ORDER_ORIGIN, g.trace_image(480)):
+        pose4 = pose3b.copy()
+        pose4[14] = fig.pose(60)[14]
+        sc.set_transforms(pose3b)
+        sc.refit()
+        sc.trace(rays, hits, flags=g.TRACE_DEFAULT | extra, ray_flags=rf)
+        sc.set_transforms(pose4)
+        sc.refit()
+        sc.trace(rays, hits, flags=flags | extra, ray_flags=rf)
+        torch.cuda.synchronize()
+        got4 = _decode(g, hits, rf)
+        compare(scene, pose4, rays_np, got4, so.trace(rays_np, local=pose4))
+        assert ((got4["flags"] & g.RAY_REUSED) != 0).sum() > 0
+
     with pytest.raises(g.SvoError):
         sc.trace(rays, hits, flags=g.TRACE_CULL | g.TRACE_FP64_FIX | g.TRACE_REUSE)
     sc.close()
