@@ -76,6 +76,12 @@ typedef int32_t svo_status;
                                       16..31 of flags: warps take 8 x 4 pixel tiles instead of 32
                                       consecutive rays (results unchanged; ignored with ORDER_*) */
 #define SVO_TRACE_IMAGE(width) (SVO_TRACE_IMAGE_TILES | ((uint32_t)(width) << 16))
+#define SVO_TRACE_GRID 512u  /* cull through the scene-level grid (scenes of 64+ parts, built by every
+                                refit; Sec. V-E): each ray walks the grid cells it crosses front to back,
+                                tests the parts listed there once each, descends them as found and stops
+                                once the next cell starts beyond its best hit.  Needs CULL | SORT; not
+                                with REUSE.  Falls back to the cluster level for smaller scenes or when
+                                the grid's lists overflowed (results are the same either way). */
 #define SVO_TRACE_REUSE 256u /* hit buffer reuse (Sec. IV-C, Fig. 5): the hits buffer holds this scene's
                                 result for the same rays from the scene's previous trace (a static
                                 camera); a ray whose intersected part spheres (at most 4) all belong to

@@ -28,6 +28,7 @@ from ._lib import (  # noqa: F401
     TRACE_ORDER_DIR,
     TRACE_ORDER_ORIGIN,
     TRACE_FP64_FIX,
+    TRACE_GRID,
     TRACE_IMAGE_TILES,
     TRACE_REUSE,
     TRACE_SORT,

@@ -24,6 +24,7 @@ TRACE_ORDER_DIR = 32
 TRACE_ORDER_ORIGIN = 64
 TRACE_IMAGE_TILES = 128
 TRACE_REUSE = 256
+TRACE_GRID = 512
 TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
 
 

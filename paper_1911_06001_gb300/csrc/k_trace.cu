@@ -56,6 +56,7 @@ struct TraceLaunchT {
   unsigned int *err;
   int32_t one_scene;     // every item traces the same scene: stage its tables in shared memory
   int32_t stack_levels;  // traversal stack levels per thread (max asset depth - 1)
+  int32_t mbox_words;    // grid walk: words of each thread's tested-part bitset (max parts / 32)
   int32_t block;         // threads per block of the trace kernel: 64, 128 or 256
   int32_t rays_per_lane; // rays per lane in a warp's tile (tile = 32 * rays_per_lane rays)
 };
@@ -602,12 +603,103 @@ __device__ __forceinline__ void list_insert(float (&ct)[kCap], float (&ce)[kCap]
   }
 }
 
+// Culling through the scene-level grid (Sec. V-E).  Each cell lists every
+// part whose sphere box comes within m = 2^-10 cells of it.  The ray walks the
+// cells it crosses front to back (a 3D DDA whose crossing parameters are
+// recomputed from each cell plane, so that they carry one rounding each and
+// increase along the walk); for t in the parameter interval of a visited cell
+// the exact ray point lies within the rounding error of that cell, and the
+// ray is only walked when that error is below m/2 (else false is returned and
+// the ray takes the cluster level).  The intervals of the visited cells
+// follow each other without gaps, so a part whose sphere the exact ray meets
+// at some t in them is listed in a visited cell.  Each listed part is
+// sphere-tested once (a bitset per thread) and descended at once unless its
+// entry is beyond the bound; the walk ends after the first cell whose interval
+// reaches past the bound, the segment or the grid box.
 template <bool STATS, int BLOCK>
+__device__ __forceinline__ bool grid_walk(const RayW &r, const SceneGrid &g, const int32_t *__restrict__ cstart,
+                                          const int32_t *__restrict__ cparts, const PartHot *__restrict__ hot,
+                                          const PartAux *__restrict__ aux, const Tables *tab, uint2 *stk,
+                                          uint32_t *mbox, int mwords, CertState &st, Contenders &con,
+                                          unsigned int &err, Counters &cnt) {
+  const int G = g.G;
+  const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  // the segment inside the grid box
+  float t0 = r.tmin, t1 = r.tmax;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float blo = g.lo[a], bhi = fmaf((float)G, g.cs[a], g.lo[a]);
+    if (d[a] == 0.f) {
+      if (o[a] < blo || o[a] > bhi) t1 = -Num<float>::inf();
+      continue;
+    }
+    float ta = (blo - o[a]) / d[a], tb = (bhi - o[a]) / d[a];
+    if (!isfinite(ta) || !isfinite(tb)) return false;  // a component too small for the walk's arithmetic
+    if (ta > tb) {
+      const float x = ta;
+      ta = tb;
+      tb = x;
+    }
+    t0 = fmaxf(t0, ta);
+    t1 = fminf(t1, tb);
+  }
+  if (!(t0 <= t1)) return true;  // the segment misses every sphere box
+  // the rounding allowance: a few units of roundoff of the largest magnitudes
+  // in the crossing and start-cell arithmetic, against m/2 = 2^-11 cells
+  int cur[3], step[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float mag = fabsf(o[a]) + fabsf(g.lo[a]) + (float)G * g.cs[a] + fabsf(t0 * d[a]);
+    if (!(8.0f * kU * mag <= g.cs[a] * 4.8828125e-4f)) return false;
+    const float f = (fmaf(t0, d[a], o[a]) - g.lo[a]) * g.inv_cs[a];
+    int i = (int)floorf(fminf(fmaxf(f, 0.f), (float)G));
+    cur[a] = i > G - 1 ? G - 1 : i;
+    step[a] = d[a] > 0.f ? 1 : (d[a] < 0.f ? -1 : 0);
+  }
+  for (int w = 0; w < mwords; ++w) mbox[w * BLOCK] = 0u;
+#pragma unroll 1
+  for (int iter = 0; iter < 3 * G + 1; ++iter) {
+    const int c = cur[0] + G * (cur[1] + G * cur[2]);
+    const int e = cstart[c + 1];
+    for (int k = cstart[c]; k < e; ++k) {
+      const int p = cparts[k];
+      uint32_t *wp = mbox + (p >> 5) * BLOCK;
+      const uint32_t bit = 1u << (p & 31), wv = *wp;
+      if (wv & bit) continue;
+      *wp = wv | bit;
+      float tin, tref;
+      if (STATS) ++cnt.parts_tested;
+      if (!part_cull(r, hot[p], tin, tref)) continue;
+      if (tin > prune_bound(st, r.tmax)) continue;  // the bound only shrinks
+      trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
+    }
+    // the cell's exit: the nearest crossing of a far cell plane
+    float tx = Num<float>::inf();
+    int ax = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (step[a] == 0) continue;
+      const float plane = fmaf((float)(cur[a] + (step[a] > 0 ? 1 : 0)), g.cs[a], g.lo[a]);
+      const float ta = (plane - o[a]) / d[a];
+      if (ta < tx) {
+        tx = ta;
+        ax = a;
+      }
+    }
+    if (ax < 0 || tx >= t1 || tx > prune_bound(st, r.tmax)) return true;
+    cur[ax] += step[ax];
+    if (cur[ax] < 0 || cur[ax] > G - 1) return true;
+  }
+  return true;  // not reached: each step moves one axis one cell towards the box's far side
+}
+
+template <bool STATS, int BLOCK, bool GRID>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
                               uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt,
-                              bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused) {
+                              bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused,
+                              const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords) {
   reused = false;
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
@@ -624,6 +716,14 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
     float last_t = -Num<float>::inf();
     int last_p = -1;
     bool need = active;
+    if (GRID && need && grid != nullptr && grid->valid != 0) {
+      // the grid walk needs no warp votes: lanes walk independently; a ray
+      // the walk cannot take safely goes on to the cluster level below
+      const SceneGrid &g = *grid;
+      need = !grid_walk<STATS, BLOCK>(r, g, g.cell_start, g.cell_parts, hot, aux, tab, stk, mbox, mwords, st, con,
+                                      err, cnt);
+      if (STATS && !need) ++cnt.passes;
+    }
     while (__any_sync(0xffffffffu, need)) {
       float ct[kCap], ce[kCap];
       int cp[kCap];
@@ -751,8 +851,9 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 
 // REUSE: hit buffer reuse compiled in (a separate instantiation, so that the
 // common kernel carries none of its registers or tests).
-template <int NI, bool STATS, int BLOCK, bool REUSE>
-__global__ void __launch_bounds__(BLOCK, (STATS || REUSE ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+// GRID: the scene-level grid walk compiled in (likewise).
+template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID>
+__global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
@@ -763,6 +864,7 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE ? 512 : kTraceThreadsPe
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
+  uint32_t *sMbox = reinterpret_cast<uint32_t *>(sOrd + sp) + threadIdx.x;  // word-major, stride BLOCK
   load_tables(tab);
   if (L.one_scene) {
     const TraceItem &I0 = L.items[0];
@@ -842,8 +944,9 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE ? 512 : kTraceThreadsPe
       const bool reuse = REUSE && active;
       const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
-      trace_ray_f32<STATS, BLOCK>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err, cnt,
-                                  reuse, prev_part, I.dirty, reused);
+      trace_ray_f32<STATS, BLOCK, GRID>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err,
+                                        cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr, sMbox,
+                                        L.mbox_words);
       bool flagged = false, ids_ok = true;
       if (in_range && reused) {
         if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
@@ -1025,19 +1128,26 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block) {
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, int mbox_words) {
   return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
-         clusters * sizeof(Cluster) + parts * sizeof(int32_t);
+         clusters * sizeof(Cluster) + parts * sizeof(int32_t) + (size_t)mbox_words * block * sizeof(uint32_t);
 }
 
 template <int NI, int BLOCK>
 cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
-                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK);
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
   const bool reuse = (L.flags & SVO_TRACE_REUSE) != 0;
-  auto kern = stats ? (reuse ? k_trace<NI, true, BLOCK, true> : k_trace<NI, true, BLOCK, false>)
-                    : (reuse ? k_trace<NI, false, BLOCK, true> : k_trace<NI, false, BLOCK, false>);
+  bool walk = (L.flags & SVO_TRACE_GRID) != 0 && !reuse;
+  if (walk) {
+    bool any = false;
+    for (int i = 0; i < L.n_items; ++i) any = any || L.items[i].grid != nullptr;
+    walk = any;
+  }
+  const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
+                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK, walk ? L.mbox_words : 0);
+  auto kern = walk ? (stats ? k_trace<NI, true, BLOCK, false, true> : k_trace<NI, false, BLOCK, false, true>)
+              : stats ? (reuse ? k_trace<NI, true, BLOCK, true, false> : k_trace<NI, true, BLOCK, false, false>)
+                      : (reuse ? k_trace<NI, false, BLOCK, true, false> : k_trace<NI, false, BLOCK, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1084,6 +1194,9 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   int lv = 1;
   for (int i = 0; i < src.n_items && i < NI; ++i) lv = src.items[i].max_depth - 1 > lv ? src.items[i].max_depth - 1 : lv;
   dst.stack_levels = lv;
+  int mp = 0;
+  for (int i = 0; i < src.n_items && i < NI; ++i) mp = src.items[i].n_parts > mp ? src.items[i].n_parts : mp;
+  dst.mbox_words = (mp + 31) / 32;
   dst.stats = src.stats;
   dst.err = src.err;
   dst.block = src.block;

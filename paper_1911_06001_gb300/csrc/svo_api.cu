@@ -91,6 +91,7 @@ struct svo_ctx {
 struct svo_scene {
   svo_ctx *ctx = nullptr;
   int P = 0, L = 0, NC = 0;
+  int grid_G = 0, grid_cap = 0;  // scene-level grid (0: none)
   int max_depth = 1;
   std::vector<int32_t> parent;
   std::vector<svo_handle> asset;
@@ -104,6 +105,8 @@ struct svo_scene {
   int32_t *d_level_order = nullptr, *d_level_start = nullptr;
   float4 *d_bound = nullptr;
   uint8_t *d_dirty = nullptr;  // per part: world pose changed since the scene's previous trace
+  SceneGrid *d_grid = nullptr;  // scene-level grid header, cell starts and part lists
+  int32_t *d_cell_start = nullptr, *d_cell_parts = nullptr;
   double *h_stage = nullptr;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
@@ -167,6 +170,7 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.ray_flags = flags;
   it.perm = nullptr;
   it.dirty = s->d_dirty;
+  it.grid = s->grid_G > 0 ? s->d_grid : nullptr;
   it.n = n;
   it.tile_begin = 0;
   it.n_parts = s->P;
@@ -184,6 +188,9 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
   if ((L.flags & SVO_TRACE_REUSE) && (L.flags & kReuseNeeds) != kReuseNeeds)
     return fail(SVO_ERR_ARG, "SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
+  if ((L.flags & SVO_TRACE_GRID) &&
+      ((L.flags & SVO_TRACE_REUSE) || (L.flags & (SVO_TRACE_CULL | SVO_TRACE_SORT)) != (SVO_TRACE_CULL | SVO_TRACE_SORT)))
+    return fail(SVO_ERR_ARG, "SVO_TRACE_GRID needs CULL | SORT and excludes REUSE");
   cudaStream_t st = (cudaStream_t)stream;
   Slot *slot = nullptr;
   svo_status rc = get_slot(ctx, stream, total_rays, &slot);
@@ -489,7 +496,18 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   size_t off_ls = al(off_lo + P * sizeof(int32_t));
   size_t off_bd = al(off_ls + (L + 1) * sizeof(int32_t));
   size_t off_dirty = al(off_bd + sizeof(float4));
-  size_t total = al(off_dirty + P);
+  // scene-level grid: G = 2 cbrt(P) cells per axis (at most 16) for scenes of
+  // kGridMinParts parts or more; lists sized for about 32 cells per part
+  int grid_G = 0, grid_cap = 0;
+  if (P >= kGridMinParts) {
+    grid_G = (int)std::ceil(2.0 * std::cbrt((double)P));
+    grid_G = grid_G < 2 ? 2 : (grid_G > kGridMaxG ? kGridMaxG : grid_G);
+    grid_cap = 32 * P + grid_G * grid_G * grid_G;
+  }
+  size_t off_grid = al(off_dirty + P);
+  size_t off_cstart = al(off_grid + sizeof(SceneGrid));
+  size_t off_cparts = al(off_cstart + (grid_G > 0 ? (size_t)(grid_G * grid_G * grid_G + 1) * sizeof(int32_t) : 0));
+  size_t total = al(off_cparts + (size_t)grid_cap * sizeof(int32_t));
   CK(cudaSetDevice(ctx->device));
   svo_scene *s = new svo_scene();
   s->ctx = ctx;
@@ -516,6 +534,11 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   s->d_level_start = reinterpret_cast<int32_t *>(s->d_mem + off_ls);
   s->d_bound = reinterpret_cast<float4 *>(s->d_mem + off_bd);
   s->d_dirty = reinterpret_cast<uint8_t *>(s->d_mem + off_dirty);
+  s->d_grid = reinterpret_cast<SceneGrid *>(s->d_mem + off_grid);
+  s->d_cell_start = reinterpret_cast<int32_t *>(s->d_mem + off_cstart);
+  s->d_cell_parts = reinterpret_cast<int32_t *>(s->d_mem + off_cparts);
+  s->grid_G = grid_G;
+  s->grid_cap = grid_cap;
   std::vector<double> ident(P * 12, 0.0);
   for (int i = 0; i < P; ++i) ident[12 * i + 0] = ident[12 * i + 5] = ident[12 * i + 10] = 1.0;
   e = cudaMallocHost(&s->h_stage, P * 12 * sizeof(double));
@@ -621,6 +644,11 @@ svo_status scene_refit(svo_scene *s, void *stream) {
   a.n_clusters = s->NC;
   a.bound = s->d_bound;
   a.dirty = s->d_dirty;
+  a.grid = s->grid_G > 0 ? s->d_grid : nullptr;
+  a.cell_start = s->d_cell_start;
+  a.cell_parts = s->d_cell_parts;
+  a.grid_G = s->grid_G;
+  a.grid_cap = s->grid_cap;
   a.err = s->ctx->d_err;
   CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
   s->host_pending = false;

@@ -63,6 +63,24 @@ struct Cluster {
   float4 aux;     // .x max n_ainv of the members, .w bits: first | count << 16
 };
 
+// Scene-level grid over the parts (the "larger structure" the paper suggests
+// for scenes of many parts, Sec. V-E): a uniform G^3 grid over the part
+// spheres, rebuilt by every refit.  Cell c lists, in increasing part order,
+// the parts whose sphere box (widened by 1e-3 cells) meets it:
+// cell_parts[cell_start[c] .. cell_start[c + 1]).
+struct SceneGrid {
+  float lo[3];      // grid corner
+  float cs[3];      // cell size per axis
+  float inv_cs[3];  // 1 / cs
+  int32_t G;        // cells per axis
+  int32_t valid;    // 0: no grid (small scene) or the lists overflowed: trace by clusters
+  int32_t pad;
+  const int32_t *cell_start;  // G^3 + 1
+  const int32_t *cell_parts;
+};
+constexpr int kGridMinParts = 64;  // scenes from this size on get a grid
+constexpr int kGridMaxG = 16;
+
 // One item of a trace launch (by value in the kernel parameters).
 struct TraceItem {
   const PartHot *hot;
@@ -75,6 +93,7 @@ struct TraceItem {
   uint32_t *ray_flags;  // or nullptr
   const uint32_t *perm; // visiting order of the rays (nullptr = index order)
   const uint8_t *dirty; // per part: pose changed since the scene's previous trace (SVO_TRACE_REUSE)
+  const SceneGrid *grid;  // scene-level grid (SVO_TRACE_GRID), or nullptr
   unsigned long long n;
   unsigned long long tile_begin;
   int32_t n_parts;
@@ -174,6 +193,11 @@ struct RefitArgs {
   int32_t n_clusters;
   float4 *bound;  // sphere enclosing every part sphere (ray-ordering frame)
   uint8_t *dirty; // set to 1 for every part whose world pose changes (cleared by each trace)
+  SceneGrid *grid;        // header written by the refit (nullptr: no grid)
+  int32_t *cell_start;    // G^3 + 1
+  int32_t *cell_parts;    // grid_cap entries
+  int32_t grid_G;         // 0: no grid
+  int32_t grid_cap;
   unsigned int *err;
 };
 // host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses

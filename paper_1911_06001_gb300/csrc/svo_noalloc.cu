@@ -87,6 +87,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
   if ((flags & SVO_TRACE_REUSE) && (flags & kReuseNeeds) != kReuseNeeds)
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
+  if ((flags & SVO_TRACE_GRID) &&
+      ((flags & SVO_TRACE_REUSE) || (flags & (SVO_TRACE_CULL | SVO_TRACE_SORT)) != (SVO_TRACE_CULL | SVO_TRACE_SORT)))
+    return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: SVO_TRACE_GRID needs CULL | SORT and excludes REUSE");
   const int dev = scene_device(s);
   if (dev < 0 || dev >= kMaxDevices) return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: bad device");
   cudaError_t e = cudaSetDevice(dev);
