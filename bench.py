@@ -414,6 +414,53 @@ def serving_section(g, ctx, srv, pool_handles, n_requests: int, warm: int, rate:
 
 
 SEED_SERVE = 1911_06001 + 4 * 1000 + 7
+SEED_MANY = 1911_06001 + 5 * 1000 + 3
+
+
+def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -> dict:
+    """A scene of 1024 parts (the largest a scene holds) traced by a
+    1920x1080 camera outside the part cube and by 1 M rays inside it, with
+    the cluster level and with the scene grid (Sec. V-E); refit included."""
+    import torch
+
+    scene, cam_np, inner_np = many
+    sc = ctx.scene([pool_handles[int(a)] for a in scene.part_asset], scene.parent)
+    sc.set_transforms(scene.local)
+    sc.refit()
+
+    def timed(fn):
+        evs = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record()
+            fn()
+            e[1].record()
+            evs.append(e)
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs[2:]]))
+
+    out = {"workload": f"{scene.n_parts} parts (depth 6-11 pool assets, affine with shear) in a cube of side "
+                       f"{scene.meta['box']:.1f}", "refit_ms": timed(lambda: sc.refit())}
+    for name, r_np, extra in (("camera_1920x1080", cam_np, g.trace_image(1920)), ("inner_1M", inner_np, 0)):
+        rays = torch.from_numpy(r_np).to(dev)
+        n = int(rays.shape[0])
+        hits = torch.empty((n, 2), dtype=torch.int64, device=dev)
+        row = {}
+        for label, cull in (("clusters", 0), ("grid", g.TRACE_GRID)):
+            f = g.TRACE_DEFAULT | extra | cull
+            ms = timed(lambda: sc.trace(rays, hits, flags=f))
+            st = g.new_stats(dev)
+            sc.trace(rays, hits, flags=f | g.TRACE_STATS, stats=st)
+            torch.cuda.synchronize()
+            s = g.read_stats(st)
+            row[label] = {"ms": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
+                          "parts_tested_per_ray": s["parts_tested"] / n}
+        row["grid_speedup"] = row["clusters"]["ms"] / row["grid"]["ms"]
+        out[name] = row
+    ctx.check_device()
+    sc.close()
+    return out
 
 
 def main() -> None:
@@ -436,6 +483,10 @@ def main() -> None:
         pool = synthetic.asset_pool(range(6, 12), 4, seed=synthetic.config_seed(2, 1))
         bat = synthetic.batched_scenes(pool=pool)
         srv = synthetic.serving_world(pool=pool, pool_indices=list(range(2 * 4, 6 * 4)))
+        m = synthetic.batched_scenes(seed=SEED_MANY, n_scenes=1, parts=(1024, 1024), pool=pool).scenes[0]
+        mbox = m.meta["box"]
+        many = (m, synthetic.pinhole_rays(np.array([0.9, 0.6, 1.4]) * mbox, np.zeros(3), 1920, 1080, fov_deg=50.0),
+                synthetic.random_rays(1 << 20, np.random.default_rng(SEED_MANY), (-mbox / 2,) * 3, (mbox / 2,) * 3))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(fig, poses)
@@ -629,12 +680,13 @@ def main() -> None:
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                 "bytes_per_launch": alg_bytes, "launch_ms": float(trace_ms.mean())}
 
-    batched = serving = hit_buffer = paper_experiment = None
+    batched = serving = hit_buffer = paper_experiment = many_parts = None
     if extra:
         pool_handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
         hit_buffer = hit_buffer_section(g, ctx, sc, fig, poses, rays, g.TRACE_DEFAULT | order, stream, flush)
         paper_experiment = paper_experiment_section(g, ctx, fig, poses, dev, stream, flush)
         batched = batched_section(g, ctx, bat, pool_handles, dev, reps=5, flush=flush)
+        many_parts = many_parts_section(g, ctx, many, pool_handles, dev, flush)
         serving = serving_section(g, ctx, srv, pool_handles, args.serve_requests,
                                   warm=min(1000, args.serve_requests // 5),
                                   rate=2000.0)
@@ -661,6 +713,7 @@ def main() -> None:
             "hit_buffer": hit_buffer,
             "paper_experiment": paper_experiment,
             "batched": batched,
+            "many_parts": many_parts,
             "serving": serving,
             "flagged_frac": float(flagged / N_RAYS),
             "nodes_per_ray": float(nodes / N_RAYS),

@@ -2,9 +2,10 @@
 
 Knobs that change only speed, never results: the trace kernel's block size
 (64 / 128 / 256 threads), the rays each lane takes per warp tile (1 / 2 / 4 /
-8) and the ray order (as given, grouped by direction, grouped by origin cell
+8), the ray order (as given, grouped by direction, grouped by origin cell
 then direction, or -- for rays that are the pixels of an image -- warp tiles
-of 8 x 4 pixels).  ``tune`` times every combination on the caller's rays with
+of 8 x 4 pixels) and, for scenes of 64 parts or more, the culling structure
+(the cluster level or the scene grid).  ``tune`` times every combination on the caller's rays with
 CUDA events (L2 flushed between repetitions), keeps the fastest, and can
 remember it in a JSON cache under a caller-chosen key (for example the scene
 and ray-batch shape).
@@ -18,12 +19,15 @@ import os
 
 import numpy as np
 
-from . import TRACE_DEFAULT, TRACE_IMAGE_TILES, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN, Context, trace_image
+from . import (TRACE_CULL, TRACE_DEFAULT, TRACE_GRID, TRACE_IMAGE_TILES, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN,
+               TRACE_REUSE, TRACE_SORT, Context, trace_image)
 
 BLOCKS = (64, 128, 256)
 RAYS_PER_LANE = (1, 2, 4, 8)
 ORDERS = {"none": 0, "dir": TRACE_ORDER_DIR, "origin": TRACE_ORDER_ORIGIN, "image": TRACE_IMAGE_TILES}
 _ORDER_BITS = TRACE_ORDER_DIR | TRACE_ORDER_ORIGIN | TRACE_IMAGE_TILES | 0xFFFF0000
+CULLS = {"clusters": 0, "grid": TRACE_GRID}
+GRID_MIN_PARTS = 64  # scenes from this size on carry a grid
 
 
 def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> float:
@@ -43,10 +47,12 @@ def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> floa
 
 def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, blocks=BLOCKS,
          rays_per_lane=RAYS_PER_LANE, orders=None, cache_path: str | None = None,
-         key: str | None = None, image_width: int = 0) -> dict:
-    """Time every (block, rays_per_lane, order) on ``rays`` (CUDA [n, 8]) traced
-    against ``scene``; apply and return the fastest.  The "image" order is
-    tried only when ``image_width`` (row-major pixels) is given."""
+         key: str | None = None, image_width: int = 0, culls=None) -> dict:
+    """Time every (block, rays_per_lane, order, cull) on ``rays`` (CUDA [n, 8])
+    traced against ``scene``; apply and return the fastest.  The "image" order
+    is tried only when ``image_width`` (row-major pixels) is given, the "grid"
+    culling only for scenes of GRID_MIN_PARTS parts or more traced with
+    CULL | SORT and without REUSE."""
     import torch
 
     if cache_path and key:
@@ -56,17 +62,23 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
             return cached
     if orders is None:
         orders = tuple(o for o in ORDERS if o != "image" or image_width > 0)
+    if culls is None:
+        cs = TRACE_CULL | TRACE_SORT
+        grid_ok = getattr(scene, "n_parts", 0) >= GRID_MIN_PARTS and (flags & cs) == cs and not (flags & TRACE_REUSE)
+        culls = ("clusters", "grid") if grid_ok else ("clusters",)
     hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
     old = ctx.trace_config()
     table = []
-    for b, r, o in itertools.product(blocks, rays_per_lane, orders):
+    for b, r, o, c in itertools.product(blocks, rays_per_lane, orders, culls):
         ctx.set_trace_config(b, r)
-        f = (flags & ~_ORDER_BITS) | _flag(o, image_width)
-        table.append({"block": b, "rays_per_lane": r, "order": o, "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
+        f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | _flag(o, image_width) | CULLS[c]
+        table.append({"block": b, "rays_per_lane": r, "order": o, "cull": c,
+                      "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
     best = min(table, key=lambda x: x["ms"])
-    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"), None)
+    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"
+                    and x["cull"] == "clusters"), None)
     result = dict(best)
     result["default_ms"] = default["ms"] if default else None
     result["n_rays"] = int(rays.shape[0])
@@ -88,13 +100,15 @@ def _flag(order: str, image_width: int) -> int:
 
 
 def apply(ctx: Context, cfg: dict) -> int:
-    """Set the tuned launch shape on ``ctx``; returns the order flag to OR into trace flags."""
+    """Set the tuned launch shape on ``ctx``; returns the flags (order, culling) to OR into trace flags."""
     ctx.set_trace_config(int(cfg["block"]), int(cfg["rays_per_lane"]))
     return order_flag(cfg)
 
 
 def order_flag(cfg: dict) -> int:
-    return _flag(cfg["order"], int(cfg.get("image_width", 0)))
+    """The tuned ray-order and culling flags (configurations cached before the
+    culling knob existed read as the cluster level)."""
+    return _flag(cfg["order"], int(cfg.get("image_width", 0))) | CULLS[cfg.get("cull", "clusters")]
 
 
 def load(cache_path: str) -> dict:

@@ -82,14 +82,12 @@ struct RefitSmem {
   int32_t *lorder;           // P
   int32_t *lstart;           // levels + 1
   float *red;                // 6 x threads
-  int32_t *gcnt;             // G^3 + 1 (scene grid counts, then cursors)
 };
 
-__host__ __device__ inline size_t refit_smem_bytes(int P, int NC, int L, int nthr, int G) {
+__host__ __device__ inline size_t refit_smem_bytes(int P, int NC, int L, int nthr) {
   return (size_t)P * (12 * sizeof(double) + sizeof(unsigned long long) + sizeof(float4) + sizeof(float) +
                       3 * sizeof(int32_t)) +
-         (size_t)NC * sizeof(float4) + (size_t)(L + 1) * sizeof(int32_t) + 6 * (size_t)nthr * sizeof(float) +
-         (G > 0 ? (size_t)(G * G * G + 1) * sizeof(int32_t) : 0) + 64;
+         (size_t)NC * sizeof(float4) + (size_t)(L + 1) * sizeof(int32_t) + 6 * (size_t)nthr * sizeof(float) + 64;
 }
 
 __device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L) {
@@ -105,7 +103,6 @@ __device__ inline RefitSmem carve(unsigned char *base, int P, int NC, int L) {
   m.lorder = m.parent + P;
   m.lstart = m.lorder + P;
   m.red = reinterpret_cast<float *>(m.lstart + L + 1);
-  m.gcnt = reinterpret_cast<int32_t *>(m.red + 6 * kRefitThreads);
   return m;
 }
 
@@ -117,156 +114,6 @@ __device__ __forceinline__ float abs_diff_up(float a, float b) {
 // Upper bound of sqrt(x^2 + y^2 + z^2) for non-negative x, y, z.
 __device__ __forceinline__ float norm_up(float x, float y, float z) {
   return __fsqrt_ru(__fmaf_ru(x, x, __fmaf_ru(y, y, __fmul_ru(z, z))));
-}
-
-// Cell range of a sphere box along one axis: every cell within 2^-10 cells of
-// the box (the walk's rounding allowance), plus 2^-12 cells for the rounding
-// of the index itself (at most 2^-13 cells while the grid is valid).
-__device__ __forceinline__ void cell_range(float c, float r, float lo, float inv, int G, int &i0, int &i1) {
-  constexpr float kPad = 9.765625e-4f + 2.44140625e-4f;  // 2^-10 + 2^-12
-  const float f0 = (__fsub_rd(c, r) - lo) * inv - kPad, f1 = (__fadd_ru(c, r) - lo) * inv + kPad;
-  i0 = (int)floorf(fmaxf(f0, 0.f));
-  i1 = (int)floorf(fminf(f1, (float)G - 0.5f));
-  i0 = i0 < 0 ? 0 : (i0 > G - 1 ? G - 1 : i0);
-  i1 = i1 < i0 ? i0 : (i1 > G - 1 ? G - 1 : i1);
-}
-
-// Scene-level grid (Sec. V-E): a G^3 grid over the enabled part spheres; each
-// cell lists the parts whose sphere box meets it, in increasing part order.
-__device__ void build_grid(const RefitArgs &a, const RefitSmem &sm, int P) {
-  const int tid = threadIdx.x, G = a.grid_G, NC3 = G * G * G;
-  // the spheres' box, rounded outward (block reduction)
-  float bl[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, bh[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  for (int i = tid; i < P; i += kRefitThreads) {
-    const float4 s = sm.sph[i];
-    if (s.w < 0.f) continue;
-    bl[0] = fminf(bl[0], __fsub_rd(s.x, s.w));
-    bl[1] = fminf(bl[1], __fsub_rd(s.y, s.w));
-    bl[2] = fminf(bl[2], __fsub_rd(s.z, s.w));
-    bh[0] = fmaxf(bh[0], __fadd_ru(s.x, s.w));
-    bh[1] = fmaxf(bh[1], __fadd_ru(s.y, s.w));
-    bh[2] = fmaxf(bh[2], __fadd_ru(s.z, s.w));
-  }
-  __syncthreads();  // sm.red is free again
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    sm.red[k * kRefitThreads + tid] = bl[k];
-    sm.red[(3 + k) * kRefitThreads + tid] = bh[k];
-  }
-  __syncthreads();
-  for (int w = kRefitThreads / 2; w > 0; w >>= 1) {
-    if (tid < w) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float *lo = sm.red + k * kRefitThreads, *hi = sm.red + (3 + k) * kRefitThreads;
-        lo[tid] = fminf(lo[tid], lo[tid + w]);
-        hi[tid] = fmaxf(hi[tid], hi[tid + w]);
-      }
-    }
-    __syncthreads();
-  }
-  // grid box: the spheres' box widened by m = 2^-10 of a cell on each side, so
-  // that every sphere box lies at least m inside it
-  float lo[3], cs[3], inv[3];
-  bool any = true, exact = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float l0 = sm.red[k * kRefitThreads], h0 = sm.red[(3 + k) * kRefitThreads];
-    any = any && h0 >= l0;
-    const float m = fmaxf(__fmul_ru(__fdiv_ru(__fsub_ru(h0, l0), (float)G), 9.765625e-4f), 1e-30f);
-    lo[k] = __fsub_rd(l0, m);
-    cs[k] = fmaxf(__fdiv_ru(__fsub_ru(__fadd_ru(h0, m), lo[k]), (float)G), 1e-30f);  // lo + G cs covers h0 + m
-    inv[k] = 1.0f / cs[k];
-    // the walk's and the lists' rounding stays below 2^-13 cells only for a
-    // grid not too far from the origin relative to its cell size
-    exact = exact && 16.0f * 5.9604644775390625e-8f * (fabsf(lo[k]) + (float)G * cs[k]) <= cs[k] * 2.44140625e-4f;
-  }
-  any = any && exact;
-  for (int c = tid; c <= NC3; c += kRefitThreads) sm.gcnt[c] = 0;
-  __syncthreads();
-  for (int i = tid; i < P && any; i += kRefitThreads) {
-    const float4 s = sm.sph[i];
-    if (s.w < 0.f) continue;
-    int x0, x1, y0, y1, z0, z1;
-    cell_range(s.x, s.w, lo[0], inv[0], G, x0, x1);
-    cell_range(s.y, s.w, lo[1], inv[1], G, y0, y1);
-    cell_range(s.z, s.w, lo[2], inv[2], G, z0, z1);
-    for (int z = z0; z <= z1; ++z)
-      for (int y = y0; y <= y1; ++y)
-        for (int x = x0; x <= x1; ++x) atomicAdd(&sm.gcnt[x + G * (y + G * z)], 1);
-  }
-  __syncthreads();
-  {  // exclusive scan of the counts: per-thread chunks, then warp and block offsets
-    const int chunk = (NC3 + kRefitThreads - 1) / kRefitThreads;
-    const int c0 = tid * chunk, c1 = min(c0 + chunk, NC3);
-    int sum = 0;
-    for (int c = c0; c < c1; ++c) sum += sm.gcnt[c];
-    const int lane = tid & 31, warp = tid >> 5;
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    int *wsum = reinterpret_cast<int *>(sm.red);  // 8 warp totals (sm.red is free here)
-    __syncthreads();
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
-    int run = base + incl - sum;
-    for (int c = c0; c < c1; ++c) {
-      const int n = sm.gcnt[c];
-      sm.gcnt[c] = run;
-      a.cell_start[c] = run;
-      run += n;
-    }
-    if (tid == kRefitThreads - 1) {
-      sm.gcnt[NC3] = run;
-      a.cell_start[NC3] = run;
-    }
-  }
-  __syncthreads();
-  const bool fits = any && sm.gcnt[NC3] <= a.grid_cap;
-  for (int i = tid; i < P && fits; i += kRefitThreads) {
-    const float4 s = sm.sph[i];
-    if (s.w < 0.f) continue;
-    int x0, x1, y0, y1, z0, z1;
-    cell_range(s.x, s.w, lo[0], inv[0], G, x0, x1);
-    cell_range(s.y, s.w, lo[1], inv[1], G, y0, y1);
-    cell_range(s.z, s.w, lo[2], inv[2], G, z0, z1);
-    for (int z = z0; z <= z1; ++z)
-      for (int y = y0; y <= y1; ++y)
-        for (int x = x0; x <= x1; ++x) a.cell_parts[atomicAdd(&sm.gcnt[x + G * (y + G * z)], 1)] = i;
-  }
-  __syncthreads();
-  // deterministic order inside each cell: increasing part id
-  for (int c = tid; c < NC3 && fits; c += kRefitThreads) {
-    const int b = a.cell_start[c], e = a.cell_start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-      const int v = a.cell_parts[i];
-      int j = i - 1;
-      while (j >= b && a.cell_parts[j] > v) {
-        a.cell_parts[j + 1] = a.cell_parts[j];
-        --j;
-      }
-      a.cell_parts[j + 1] = v;
-    }
-  }
-  if (tid == 0) {
-    SceneGrid g;
-    for (int k = 0; k < 3; ++k) {
-      g.lo[k] = lo[k];
-      g.cs[k] = cs[k];
-      g.inv_cs[k] = inv[k];
-    }
-    g.G = G;
-    g.valid = fits ? 1 : 0;
-    g.pad = 0;
-    g.cell_start = a.cell_start;
-    g.cell_parts = a.cell_parts;
-    *a.grid = g;
-  }
 }
 
 template <bool INLINE, int CAP>
@@ -520,7 +367,9 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
     }
     *a.bound = make_float4(Cx, Cy, Cz, R);
   }
-  if (a.grid_G > 0) build_grid(a, sm, P);
+  // the scene grid, if any, no longer matches the spheres: the next grid
+  // trace rebuilds it first
+  if (a.grid != nullptr && tid == 0) a.grid->stale = 1;
 }
 
 template <bool INLINE, int CAP>
@@ -538,7 +387,7 @@ cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, size_t 
 
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
   static_assert(kInlinePoseParts == 256, "size classes below");
-  const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, kRefitThreads, a.grid_G);
+  const size_t smem = refit_smem_bytes(a.n_parts, a.n_clusters, a.n_levels, kRefitThreads);
   if (host_local && a.n_parts <= 16) return launch_refit_t<true, 16>(a, host_local, smem, stream);
   if (host_local && a.n_parts <= 64) return launch_refit_t<true, 64>(a, host_local, smem, stream);
   if (host_local && a.n_parts <= 256) return launch_refit_t<true, 256>(a, host_local, smem, stream);

@@ -606,24 +606,29 @@ __device__ __forceinline__ void list_insert(float (&ct)[kCap], float (&ce)[kCap]
 // Culling through the scene-level grid (Sec. V-E).  Each cell lists every
 // part whose sphere box comes within m = 2^-10 cells of it.  The ray walks the
 // cells it crosses front to back (a 3D DDA whose crossing parameters are
-// recomputed from each cell plane, so that they carry one rounding each and
-// increase along the walk); for t in the parameter interval of a visited cell
-// the exact ray point lies within the rounding error of that cell, and the
-// ray is only walked when that error is below m/2 (else false is returned and
-// the ray takes the cluster level).  The intervals of the visited cells
-// follow each other without gaps, so a part whose sphere the exact ray meets
-// at some t in them is listed in a visited cell.  Each listed part is
-// sphere-tested once (a bitset per thread) and descended at once unless its
-// entry is beyond the bound; the walk ends after the first cell whose interval
-// reaches past the bound, the segment or the grid box.
+// computed afresh from each cell plane, (plane - o) * (1/d), three roundings
+// each, increasing along the walk); for t in the parameter interval of a visited cell
+// the exact ray point lies within the rounding error of that cell, and a ray
+// is only walked when that error is below m/2 (else the function returns
+// false for it and the ray takes the cluster level).  The intervals of the
+// visited cells follow each other without gaps, so a part whose sphere the
+// exact ray meets at some t in them is listed in a visited cell.  Each listed
+// part is sphere-tested once (a bitset per thread); the walk ends after the
+// first cell whose interval reaches past the bound, the segment or the box.
+//
+// Called by the whole warp (go: this lane's ray takes part).  Each round,
+// every walking lane gathers up to kCap candidates from its cell's list, and
+// then the lanes descend their candidates together, in order of entry, so
+// that the warp runs the descents side by side as on the cluster level.
 template <bool STATS, int BLOCK>
-__device__ __forceinline__ bool grid_walk(const RayW &r, const SceneGrid &g, const int32_t *__restrict__ cstart,
-                                          const int32_t *__restrict__ cparts, const PartHot *__restrict__ hot,
-                                          const PartAux *__restrict__ aux, const Tables *tab, uint2 *stk,
-                                          uint32_t *mbox, int mwords, CertState &st, Contenders &con,
-                                          unsigned int &err, Counters &cnt) {
+__device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGrid &g,
+                                          const int32_t *__restrict__ cstart, const int32_t *__restrict__ cparts,
+                                          const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
+                                          const Tables *tab, uint2 *stk, uint32_t *mbox, int mwords, CertState &st,
+                                          Contenders &con, unsigned int &err, Counters &cnt) {
   const int G = g.G;
   const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  bool ok = true, walking = go;
   // the segment inside the grid box
   float t0 = r.tmin, t1 = r.tmax;
 #pragma unroll
@@ -634,7 +639,9 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, const SceneGrid &g, con
       continue;
     }
     float ta = (blo - o[a]) / d[a], tb = (bhi - o[a]) / d[a];
-    if (!isfinite(ta) || !isfinite(tb)) return false;  // a component too small for the walk's arithmetic
+    // else a component too small for the walk's arithmetic (the crossings
+    // below stay within a few roundings of these, so they stay finite)
+    ok = ok && fabsf(ta) < 1e38f && fabsf(tb) < 1e38f;
     if (ta > tb) {
       const float x = ta;
       ta = tb;
@@ -643,54 +650,97 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, const SceneGrid &g, con
     t0 = fmaxf(t0, ta);
     t1 = fminf(t1, tb);
   }
-  if (!(t0 <= t1)) return true;  // the segment misses every sphere box
   // the rounding allowance: a few units of roundoff of the largest magnitudes
   // in the crossing and start-cell arithmetic, against m/2 = 2^-11 cells
   int cur[3], step[3];
+  float rd[3], tn[3];  // 1/d; the crossing of the current cell's far plane per axis
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float mag = fabsf(o[a]) + fabsf(g.lo[a]) + (float)G * g.cs[a] + fabsf(t0 * d[a]);
-    if (!(8.0f * kU * mag <= g.cs[a] * 4.8828125e-4f)) return false;
+    ok = ok && 8.0f * kU * mag <= g.cs[a] * 4.8828125e-4f;
     const float f = (fmaf(t0, d[a], o[a]) - g.lo[a]) * g.inv_cs[a];
-    int i = (int)floorf(fminf(fmaxf(f, 0.f), (float)G));
+    const int i = (int)floorf(fminf(fmaxf(f, 0.f), (float)G));
     cur[a] = i > G - 1 ? G - 1 : i;
     step[a] = d[a] > 0.f ? 1 : (d[a] < 0.f ? -1 : 0);
+    rd[a] = d[a] != 0.f ? 1.0f / d[a] : 0.f;
+    tn[a] = d[a] != 0.f ? (fmaf((float)(cur[a] + (step[a] > 0 ? 1 : 0)), g.cs[a], g.lo[a]) - o[a]) * rd[a]
+                        : Num<float>::inf();
   }
-  for (int w = 0; w < mwords; ++w) mbox[w * BLOCK] = 0u;
-#pragma unroll 1
-  for (int iter = 0; iter < 3 * G + 1; ++iter) {
+  walking = walking && ok && t0 <= t1;  // t0 > t1: the segment misses every sphere box
+  int k = 0, kend = 0;
+  if (walking) {
+    for (int w = 0; w < mwords; ++w) mbox[w * BLOCK] = 0u;
     const int c = cur[0] + G * (cur[1] + G * cur[2]);
-    const int e = cstart[c + 1];
-    for (int k = cstart[c]; k < e; ++k) {
-      const int p = cparts[k];
-      uint32_t *wp = mbox + (p >> 5) * BLOCK;
-      const uint32_t bit = 1u << (p & 31), wv = *wp;
-      if (wv & bit) continue;
-      *wp = wv | bit;
-      float tin, tref;
-      if (STATS) ++cnt.parts_tested;
-      if (!part_cull(r, hot[p], tin, tref)) continue;
-      if (tin > prune_bound(st, r.tmax)) continue;  // the bound only shrinks
-      trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
-    }
-    // the cell's exit: the nearest crossing of a far cell plane
-    float tx = Num<float>::inf();
-    int ax = -1;
+    k = cstart[c];
+    kend = cstart[c + 1];
+  }
+  while (__any_sync(0xffffffffu, walking)) {
+    float ct[kCap], ce[kCap];
+    int cp[kCap];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (step[a] == 0) continue;
-      const float plane = fmaf((float)(cur[a] + (step[a] > 0 ? 1 : 0)), g.cs[a], g.lo[a]);
-      const float ta = (plane - o[a]) / d[a];
-      if (ta < tx) {
-        tx = ta;
-        ax = a;
+    for (int i = 0; i < kCap; ++i) {
+      ct[i] = Num<float>::inf();
+      ce[i] = 0.f;
+      cp[i] = 0x7fffffff;
+    }
+    if (walking) {
+      // gather: the next candidates of this cell, up to kCap
+      int n = 0;
+      while (k < kend && n < kCap) {
+        const int p = cparts[k++];
+        uint32_t *wp = mbox + (p >> 5) * BLOCK;
+        const uint32_t bit = 1u << (p & 31), wv = *wp;
+        if (wv & bit) continue;
+        *wp = wv | bit;
+        float tin, tref;
+        if (STATS) ++cnt.parts_tested;
+        if (!part_cull(r, hot[p], tin, tref)) continue;
+        if (tin > prune_bound(st, r.tmax)) continue;  // the bound only shrinks: never needed
+        int pp = p;
+        list_insert(ct, ce, cp, tin, tref, pp);  // not full: nothing is pushed out
+        ++n;
       }
     }
-    if (ax < 0 || tx >= t1 || tx > prune_bound(st, r.tmax)) return true;
-    cur[ax] += step[ax];
-    if (cur[ax] < 0 || cur[ax] > G - 1) return true;
+    // descend, the warp's lanes side by side (the list shifts down each step)
+#pragma unroll 1
+    for (int i = 0; i < kCap && __any_sync(0xffffffffu, ct[0] != Num<float>::inf()); ++i) {
+      if (ct[0] != Num<float>::inf() && ct[0] <= prune_bound(st, r.tmax))
+        trace_part_f32<STATS, CertState, BLOCK>(r, hot[cp[0]], aux[cp[0]], ce[0], (uint32_t)cp[0], tab, stk, st,
+                                                &con, err, cnt);
+#pragma unroll
+      for (int j = 0; j < kCap - 1; ++j) {
+        ct[j] = ct[j + 1];
+        ce[j] = ce[j + 1];
+        cp[j] = cp[j + 1];
+      }
+      ct[kCap - 1] = Num<float>::inf();
+    }
+    if (walking && k >= kend) {
+      // the cell's exit: the nearest crossing of a far cell plane
+      const int ax = tn[0] <= tn[1] ? (tn[0] <= tn[2] ? 0 : 2) : (tn[1] <= tn[2] ? 1 : 2);
+      const float tx = fminf(fminf(tn[0], tn[1]), tn[2]);
+      if (!(tx < t1) || tx > prune_bound(st, r.tmax)) {  // also: no axis moves (tx infinite)
+        walking = false;
+      } else {
+        bool out = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {  // static indices keep the arrays in registers
+          if (a != ax) continue;
+          cur[a] += step[a];
+          out = cur[a] < 0 || cur[a] > G - 1;
+          tn[a] = (fmaf((float)(cur[a] + (step[a] > 0 ? 1 : 0)), g.cs[a], g.lo[a]) - o[a]) * rd[a];
+        }
+        if (out) {
+          walking = false;
+        } else {
+          const int c = cur[0] + G * (cur[1] + G * cur[2]);
+          k = cstart[c];
+          kend = cstart[c + 1];
+        }
+      }
+    }
   }
-  return true;  // not reached: each step moves one axis one cell towards the box's far side
+  return ok;
 }
 
 template <bool STATS, int BLOCK, bool GRID>
@@ -716,13 +766,13 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
     float last_t = -Num<float>::inf();
     int last_p = -1;
     bool need = active;
-    if (GRID && need && grid != nullptr && grid->valid != 0) {
-      // the grid walk needs no warp votes: lanes walk independently; a ray
-      // the walk cannot take safely goes on to the cluster level below
+    if (GRID && grid != nullptr && grid->valid != 0) {  // warp-uniform: one item per warp
+      // a ray the walk cannot take safely goes on to the cluster level below
       const SceneGrid &g = *grid;
-      need = !grid_walk<STATS, BLOCK>(r, g, g.cell_start, g.cell_parts, hot, aux, tab, stk, mbox, mwords, st, con,
-                                      err, cnt);
-      if (STATS && !need) ++cnt.passes;
+      const bool walked = grid_walk<STATS, BLOCK>(r, need, g, g.cell_start, g.cell_parts, hot, aux, tab, stk, mbox,
+                                                  mwords, st, con, err, cnt);
+      if (STATS && need && walked) ++cnt.passes;
+      need = need && !walked;
     }
     while (__any_sync(0xffffffffu, need)) {
       float ct[kCap], ce[kCap];

@@ -231,6 +231,10 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.block = ctx->block;
   L.rays_per_lane = ctx->rays_per_lane;
   CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
+  if (L.flags & SVO_TRACE_GRID) {
+    GridLaunch gl;
+    if (grid_jobs(L.items, L.n_items, gl) > 0) CK(launch_grid(gl, st));
+  }
   CK(launch_trace(L, ctx->n_sm, st));
   // pose changes are tracked relative to each scene's latest trace
   for (int i = 0; i < L.n_items; ++i) {
@@ -496,14 +500,10 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   size_t off_ls = al(off_lo + P * sizeof(int32_t));
   size_t off_bd = al(off_ls + (L + 1) * sizeof(int32_t));
   size_t off_dirty = al(off_bd + sizeof(float4));
-  // scene-level grid: G = 2 cbrt(P) cells per axis (at most 16) for scenes of
-  // kGridMinParts parts or more; lists sized for about 32 cells per part
-  int grid_G = 0, grid_cap = 0;
-  if (P >= kGridMinParts) {
-    grid_G = (int)std::ceil(2.0 * std::cbrt((double)P));
-    grid_G = grid_G < 2 ? 2 : (grid_G > kGridMaxG ? kGridMaxG : grid_G);
-    grid_cap = 32 * P + grid_G * grid_G * grid_G;
-  }
+  // scene-level grid for scenes of kGridMinParts parts or more; lists sized
+  // for about 32 cells per part
+  const int grid_G = grid_cells_per_axis(P);
+  const int grid_cap = grid_G > 0 ? 32 * P + grid_G * grid_G * grid_G : 0;
   size_t off_grid = al(off_dirty + P);
   size_t off_cstart = al(off_grid + sizeof(SceneGrid));
   size_t off_cparts = al(off_cstart + (grid_G > 0 ? (size_t)(grid_G * grid_G * grid_G + 1) * sizeof(int32_t) : 0));
@@ -544,6 +544,15 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   e = cudaMallocHost(&s->h_stage, P * 12 * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_stage, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_local, ident.data(), P * 12 * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && grid_G > 0) {  // built before the first grid trace
+    SceneGrid g = {};
+    g.G = grid_G;
+    g.cap = grid_cap;
+    g.stale = 1;
+    g.cell_start = s->d_cell_start;
+    g.cell_parts = s->d_cell_parts;
+    e = cudaMemcpy(s->d_grid, &g, sizeof(g), cudaMemcpyHostToDevice);
+  }
   // no pose yet: NaN world poses make the first refit mark every part changed
   if (e == cudaSuccess) e = cudaMemset(s->d_world, 0xFF, P * 12 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s->d_dirty, 1, P);
@@ -645,10 +654,6 @@ svo_status scene_refit(svo_scene *s, void *stream) {
   a.bound = s->d_bound;
   a.dirty = s->d_dirty;
   a.grid = s->grid_G > 0 ? s->d_grid : nullptr;
-  a.cell_start = s->d_cell_start;
-  a.cell_parts = s->d_cell_parts;
-  a.grid_G = s->grid_G;
-  a.grid_cap = s->grid_cap;
   a.err = s->ctx->d_err;
   CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
   s->host_pending = false;

@@ -65,18 +65,19 @@ struct Cluster {
 
 // Scene-level grid over the parts (the "larger structure" the paper suggests
 // for scenes of many parts, Sec. V-E): a uniform G^3 grid over the part
-// spheres, rebuilt by every refit.  Cell c lists, in increasing part order,
-// the parts whose sphere box (widened by 1e-3 cells) meets it:
-// cell_parts[cell_start[c] .. cell_start[c + 1]).
+// spheres, rebuilt on demand after each refit (k_grid.cu).  Cell c lists, in
+// increasing part order, the parts whose sphere box comes within 2^-10 cells
+// of it: cell_parts[cell_start[c] .. cell_start[c + 1]).
 struct SceneGrid {
   float lo[3];      // grid corner
   float cs[3];      // cell size per axis
   float inv_cs[3];  // 1 / cs
   int32_t G;        // cells per axis
-  int32_t valid;    // 0: no grid (small scene) or the lists overflowed: trace by clusters
-  int32_t pad;
-  const int32_t *cell_start;  // G^3 + 1
-  const int32_t *cell_parts;
+  int32_t valid;    // 0: the lists overflowed or the grid is too far from the origin: trace by clusters
+  int32_t cap;      // capacity of cell_parts
+  int32_t stale;    // 1: a refit changed the spheres since the last build
+  int32_t *cell_start;  // G^3 + 1
+  int32_t *cell_parts;
 };
 constexpr int kGridMinParts = 64;  // scenes from this size on get a grid
 constexpr int kGridMaxG = 16;
@@ -193,15 +194,52 @@ struct RefitArgs {
   int32_t n_clusters;
   float4 *bound;  // sphere enclosing every part sphere (ray-ordering frame)
   uint8_t *dirty; // set to 1 for every part whose world pose changes (cleared by each trace)
-  SceneGrid *grid;        // header written by the refit (nullptr: no grid)
-  int32_t *cell_start;    // G^3 + 1
-  int32_t *cell_parts;    // grid_cap entries
-  int32_t grid_G;         // 0: no grid
-  int32_t grid_cap;
+  SceneGrid *grid;        // marked stale by the refit (nullptr: no grid)
   unsigned int *err;
 };
 // host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses
 // travel in the kernel parameters instead of through a device copy.
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream);
+
+// Grid (re)builds before a trace with SVO_TRACE_GRID: one block per distinct
+// scene, each a no-op unless the scene's grid is stale.
+struct GridJob {
+  const PartHot *hot;
+  SceneGrid *grid;
+  int32_t n_parts;
+  int32_t G;
+};
+struct GridLaunch {
+  GridJob jobs[kMaxBatchItems];
+  int32_t n_jobs;
+};
+size_t grid_smem_bytes(int G);
+cudaError_t launch_grid(const GridLaunch &L, cudaStream_t stream);
+
+// Cells per axis of a scene's grid: about 2 P^(1/3) (8 cells per part), at
+// most kGridMaxG; 0 (no grid) below kGridMinParts parts.
+inline int grid_cells_per_axis(int n_parts) {
+  if (n_parts < kGridMinParts) return 0;
+  int G = 2;
+  while (G < kGridMaxG && G * G * G < 8 * n_parts) ++G;
+  return G;
+}
+
+// The grid jobs of a trace launch's items: one per distinct scene grid.
+inline int grid_jobs(const TraceItem *items, int n_items, GridLaunch &g) {
+  g.n_jobs = 0;
+  for (int i = 0; i < n_items; ++i) {
+    if (items[i].grid == nullptr) continue;
+    bool seen = false;
+    for (int j = 0; j < g.n_jobs; ++j) seen = seen || g.jobs[j].grid == items[i].grid;
+    if (seen) continue;
+    GridJob &job = g.jobs[g.n_jobs++];
+    job.hot = items[i].hot;
+    job.grid = const_cast<SceneGrid *>(items[i].grid);
+    job.n_parts = items[i].n_parts;
+    job.G = grid_cells_per_axis(items[i].n_parts);
+  }
+  return g.n_jobs;
+}
 
 }  // namespace svo

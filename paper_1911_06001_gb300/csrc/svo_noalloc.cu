@@ -121,6 +121,10 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->err = scene_err_word(s);
   // clear what the kernels expect at zero: the tile counter and the list count
   e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && (flags & SVO_TRACE_GRID)) {
+    GridLaunch gl;
+    if (grid_jobs(L->items, 1, gl) > 0) e = launch_grid(gl, st);
+  }
   if (e == cudaSuccess) e = launch_trace(*L, scene_sm_count(s), st);
   if (e == cudaSuccess)  // pose changes are tracked relative to the scene's latest trace
     e = cudaMemsetAsync(const_cast<uint8_t *>(L->items[0].dirty), 0, (size_t)L->items[0].n_parts, st);

@@ -225,3 +225,83 @@ def test_new_scene_traces_identity_poses(ctx):
     sc.close()
     for h in handles:
         ctx.release(h)
+
+
+def test_autotune_tries_the_grid(ctx):
+    import torch
+
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300 import autotune
+
+    rng = np.random.default_rng(76)
+    P = 100
+    box = 4.0 * P ** (1.0 / 3.0)
+    scene = _affine_scene(rng, P, box)
+    gs = GpuScene(ctx, scene)
+    rays_np = _outside_camera_rays(box, 128, 96)
+    rays = torch.from_numpy(rays_np).cuda()
+    old = ctx.trace_config()
+    cfg = autotune.tune(ctx, gs.sc, rays, reps=2, blocks=(128,), rays_per_lane=(1,), orders=("none",))
+    assert sorted(x["cull"] for x in cfg["table"]) == ["clusters", "grid"]
+    extra = autotune.order_flag(cfg)
+    assert bool(extra & g.TRACE_GRID) == (cfg["cull"] == "grid")
+    res = gs.trace(rays_np, DEFAULT | extra)
+    compare(scene, scene.local, rays_np, res, oracle.SceneOracle(scene).trace(rays_np))
+    # no grid knob for small scenes or with hit buffer reuse
+    small = GpuScene(ctx, _affine_scene(rng, 20, 8.0))
+    c2 = autotune.tune(ctx, small.sc, rays, reps=1, blocks=(128,), rays_per_lane=(1,), orders=("none",))
+    assert [x["cull"] for x in c2["table"]] == ["clusters"]
+    c3 = autotune.tune(ctx, gs.sc, rays, flags=DEFAULT | g.TRACE_REUSE, reps=1, blocks=(128,), rays_per_lane=(1,),
+                       orders=("none",))
+    assert [x["cull"] for x in c3["table"]] == ["clusters"]
+    ctx.set_trace_config(*old)
+
+
+def test_grid_rebuilt_in_graph_replays(ctx):
+    """The grid is rebuilt after every refit whether the refit and the trace
+    run eagerly or as CUDA-graph replays: a captured frame, and an eager grid
+    trace after a graph that only refits, both see the new poses."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300.graphs import FrameGraph
+
+    rng = np.random.default_rng(77)
+    P = 150
+    box = 4.0 * P ** (1.0 / 3.0)
+    scene = _affine_scene(rng, P, box)
+    gs = GpuScene(ctx, scene)
+    so = oracle.SceneOracle(scene)
+    rays_np = _outside_camera_rays(box, 96, 72)
+    rays = torch.from_numpy(rays_np).cuda()
+    hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device="cuda")
+    rf = torch.zeros(rays.shape[0], dtype=torch.int32, device="cuda")
+    fg = FrameGraph(ctx, gs.sc, rays, hits, flags=DEFAULT | GRID, ray_flags=rf)
+    poses = []
+    for k in range(3):
+        local = scene.local.copy()
+        local[:, [3, 7, 11]] += rng.uniform(-box / 4, box / 4, (P, 3))
+        poses.append(local)
+        fg.replay(local)
+        torch.cuda.synchronize()
+        d = g.decode_hits(hits)
+        d["flags"] = rf.cpu().numpy().astype(np.uint32)
+        compare(scene, local, rays_np, d, so.trace(rays_np, local=local))
+    # a graph holding only the pose upload and the refit, then an eager grid trace
+    dev_poses = torch.from_numpy(scene.local.copy()).cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gs.sc.set_transforms_device(dev_poses)
+        gs.sc.refit()
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        gs.sc.set_transforms_device(dev_poses)
+        gs.sc.refit()
+    for local in (poses[0], poses[1]):
+        res = gs.trace(rays_np, DEFAULT | GRID)  # builds the grid for the current poses
+        dev_poses.copy_(torch.from_numpy(local))
+        graph.replay()
+        torch.cuda.synchronize()
+        res = gs.trace(rays_np, DEFAULT | GRID)
+        compare(scene, local, rays_np, res, so.trace(rays_np, local=local))
