@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=11000,
                     help="served requests, the first min(1000, n/5) of them warm-up")
     ap.add_argument("--launch", default="", help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER instead of autotuning")
+    ap.add_argument("--many-parts-only", action="store_true",
+                    help="run only the 1024-part section (cluster level vs scene grid) and print its JSON")
     return ap.parse_args()
 
 
@@ -417,6 +419,35 @@ SEED_SERVE = 1911_06001 + 4 * 1000 + 7
 SEED_MANY = 1911_06001 + 5 * 1000 + 3
 
 
+def many_parts_inputs(pool) -> tuple:
+    """The 1024-part scene over the asset pool, its camera rays and its inner rays."""
+    import synthetic
+
+    m = synthetic.batched_scenes(seed=SEED_MANY, n_scenes=1, parts=(1024, 1024), pool=pool).scenes[0]
+    box = m.meta["box"]
+    return (m, synthetic.pinhole_rays(np.array([0.9, 0.6, 1.4]) * box, np.zeros(3), 1920, 1080, fov_deg=50.0),
+            synthetic.random_rays(1 << 20, np.random.default_rng(SEED_MANY), (-box / 2,) * 3, (box / 2,) * 3))
+
+
+def run_many_parts_only() -> None:
+    import synthetic
+    import torch
+
+    pool = synthetic.asset_pool(range(6, 12), 4, seed=synthetic.config_seed(2, 1))
+    many = many_parts_inputs(pool)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1911_06001_gb300 as g
+
+    dev = torch.device("cuda", 0)
+    ctx = g.Context(0)
+    handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    print(json.dumps({"many_parts": many_parts_section(g, ctx, many, handles, dev, flush)}))
+    ctx.close()
+
+
 def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -> dict:
     """A scene of 1024 parts (the largest a scene holds) traced by a
     1920x1080 camera outside the part cube and by 1 M rays inside it, with
@@ -474,6 +505,10 @@ def main() -> None:
 
     import synthetic
 
+    if args.many_parts_only:
+        run_many_parts_only()
+        return
+
     # host-side inputs and the CPU baseline come first: no process forks after CUDA is up
     fig = synthetic.articulated_figure()
     poses = [fig.pose(f) for f in range(FRAMES)]
@@ -483,10 +518,7 @@ def main() -> None:
         pool = synthetic.asset_pool(range(6, 12), 4, seed=synthetic.config_seed(2, 1))
         bat = synthetic.batched_scenes(pool=pool)
         srv = synthetic.serving_world(pool=pool, pool_indices=list(range(2 * 4, 6 * 4)))
-        m = synthetic.batched_scenes(seed=SEED_MANY, n_scenes=1, parts=(1024, 1024), pool=pool).scenes[0]
-        mbox = m.meta["box"]
-        many = (m, synthetic.pinhole_rays(np.array([0.9, 0.6, 1.4]) * mbox, np.zeros(3), 1920, 1080, fov_deg=50.0),
-                synthetic.random_rays(1 << 20, np.random.default_rng(SEED_MANY), (-mbox / 2,) * 3, (mbox / 2,) * 3))
+        many = many_parts_inputs(pool)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(fig, poses)
