@@ -213,6 +213,19 @@ svo_status scene_destroy(svo_scene *scene);
 svo_status scene_set_transforms(svo_scene *scene, const double *local_3x4, void *stream);
 /* Same from a device array (n_parts*12 doubles); no check for NaN. */
 svo_status scene_set_transforms_device(svo_scene *scene, const double *local_3x4_dev, void *stream);
+/* Poses in the form of Sec. III-B: a rigid motion plus per-axis octree
+ * dimensions.  Per part 15 doubles (host, copied before return): R (3x3,
+ * row-major, orthonormal: every entry of R R^T - I within 1e-9), t (3),
+ * s (3, each > 0): the part's octree spans [0,s_x] x [0,s_y] x [0,s_z] in the
+ * frame rotated by R and moved by t, i.e. the local pose is
+ * [R diag(s) | t] (x_parent = R (s * x_unit) + t).  The animation transform
+ * stays rigid (its inverse is R^T and -R^T t, Sec. III-A); the dimensions
+ * are the traversal's octree dimensions, which for the parametric descent
+ * equal scaling the rigidly mapped ray by 1/s per axis.  Results equal
+ * scene_set_transforms with that local pose.  SVO_ERR_NAN if any entry is
+ * not finite, SVO_ERR_ARG if R is not orthonormal or a dimension is not
+ * positive; nothing is changed then. */
+svo_status scene_set_transforms_trs(svo_scene *scene, const double *rts_15, void *stream);
 /* Per-frame pose pipeline (async, one small kernel): compose the transform
  * tree in FP64 (W_i = W_parent o L_i), invert in FP64 (Eq. 3; adjugate /
  * determinant, which reduces to transpose-and-negate for a rigid pose), emit

@@ -158,6 +158,67 @@ def trace(part_assets, inv, rays, mode: int = 1, threads: int | None = None) -> 
     return {"t": out_t, "part": out_p, "voxel": out_v, "second": out_s}
 
 
+def trs_to_local(rts) -> np.ndarray:
+    """Sec. III-B poses (rotation R, translation t, octree dimensions s; rows
+    ``R (9, row-major) | t | s``) as local 3x4 affines: x_parent = R (s * x) + t."""
+    rts = np.asarray(rts, dtype=np.float64).reshape(-1, 15)
+    out = np.zeros((rts.shape[0], 12))
+    for p, row in enumerate(rts):
+        R, t, s = row[:9].reshape(3, 3), row[9:12], row[12:15]
+        out[p] = np.hstack([R @ np.diag(s), t[:, None]]).ravel()
+    return out
+
+
+def trace_octree_dims(part_leaf_ids, part_depth, rts, rays) -> dict:
+    """Brute-force closest hit with the pose split as Sec. III-B describes,
+    for scenes whose parts are all roots: the ray goes to each part's frame by
+    the rigid inverse only (Eq. 2-3: R^T (o - t), R^T d), and the octree keeps
+    its dimensions s, so the leaf at cell v of a depth-D asset is the box
+    [v s / 2^D, (v + 1) s / 2^D] per axis.  Every leaf of every part is
+    slab-tested (closed box, t in [tmin, tmax]); the smallest (t, part,
+    voxel) wins.  Small inputs only."""
+    rays = np.asarray(rays, dtype=np.float64).reshape(-1, 8)
+    rts = np.asarray(rts, dtype=np.float64).reshape(-1, 15)
+    n = rays.shape[0]
+    best_t = np.full(n, np.inf)
+    best_p = np.full(n, MISS_PART, dtype=np.uint32)
+    best_v = np.full(n, MISS_VOXEL, dtype=np.uint64)
+    for p, row in enumerate(rts):
+        R, tv, dims = row[:9].reshape(3, 3), row[9:12], row[12:15]
+        ids = np.asarray(part_leaf_ids[p], dtype=np.uint64)
+        if ids.size == 0:
+            continue
+        D = int(part_depth[p])
+        m = np.uint64((1 << D) - 1)
+        cell = np.stack([(ids >> np.uint64(k * D)) & m for k in range(3)], axis=1).astype(np.float64)
+        lo = cell * dims / 2.0 ** D
+        hi = (cell + 1.0) * dims / 2.0 ** D
+        for r in range(n):
+            o = R.T @ (rays[r, 0:3] - tv)
+            d = R.T @ rays[r, 4:7]
+            a = np.full(ids.size, rays[r, 3])
+            b = np.full(ids.size, rays[r, 7])
+            ok = np.ones(ids.size, dtype=bool)
+            for k in range(3):
+                if d[k] == 0.0:
+                    ok &= (lo[:, k] <= o[k]) & (o[k] <= hi[:, k])
+                    continue
+                ta = (lo[:, k] - o[k]) / d[k]
+                tb = (hi[:, k] - o[k]) / d[k]
+                a = np.maximum(a, np.minimum(ta, tb))
+                b = np.minimum(b, np.maximum(ta, tb))
+            ok &= a <= b
+            if not ok.any():
+                continue
+            cand = np.nonzero(ok)[0]
+            # lexicographic (t, voxel) within the part; parts are visited in increasing order
+            order = np.lexsort((ids[cand], a[cand]))
+            j = cand[order[0]]
+            if a[j] < best_t[r]:
+                best_t[r], best_p[r], best_v[r] = a[j], p, ids[j]
+    return {"t": best_t, "part": best_p, "voxel": best_v}
+
+
 COLOR_INVALID = 0xFFFFFFFF
 
 

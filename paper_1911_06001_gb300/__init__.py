@@ -166,6 +166,12 @@ class Scene:
         m = np.ascontiguousarray(local, dtype=np.float64).reshape(self.n_parts, 12)
         _lib.check(self.lib.scene_set_transforms(self.h, m.ctypes.data, _stream_ptr(stream)))
 
+    def set_transforms_trs(self, rts, stream=None) -> None:
+        """Poses as rotation, translation and per-axis octree dimensions
+        (Sec. III-B): [P, 15] FP64 rows ``R (9, row-major) | t (3) | s (3)``."""
+        m = np.ascontiguousarray(rts, dtype=np.float64).reshape(self.n_parts, 15)
+        _lib.check(self.lib.scene_set_transforms_trs(self.h, m.ctypes.data, _stream_ptr(stream)))
+
     def set_transforms_device(self, local_dev, stream=None) -> None:
         _lib.check(self.lib.scene_set_transforms_device(self.h, _ptr(local_dev), _stream_ptr(stream)))
 

@@ -49,7 +49,8 @@ EXPORTS = [
     "svo_ctx_create", "svo_ctx_destroy", "svo_last_error", "svo_status_string", "svo_check_device",
     "svo_set_trace_config", "svo_get_trace_config",
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
-    "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device", "scene_refit",
+    "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device",
+    "scene_set_transforms_trs", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
     "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole", "trace_hit_colors",
     "trace_shade",
@@ -112,6 +113,7 @@ def load(path: str | None = None):
         "scene_destroy": ([vp], i32),
         "scene_set_transforms": ([vp, vp, vp], i32),
         "scene_set_transforms_device": ([vp, vp, vp], i32),
+        "scene_set_transforms_trs": ([vp, vp, vp], i32),
         "scene_refit": ([vp, vp], i32),
         "scene_read_poses": ([vp, vp, vp, vp, vp, vp], i32),
         "scene_read_clusters": ([vp, C.POINTER(i32), vp, vp, vp], i32),

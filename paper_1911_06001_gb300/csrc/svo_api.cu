@@ -625,6 +625,32 @@ svo_status scene_set_transforms(svo_scene *s, const double *local, void *stream)
   return ok();
 }
 
+svo_status scene_set_transforms_trs(svo_scene *s, const double *rts, void *stream) {
+  if (!s || !rts) return fail(SVO_ERR_ARG, "scene_set_transforms_trs: NULL argument");
+  const int P = s->P;
+  for (int i = 0; i < P * 15; ++i)
+    if (!std::isfinite(rts[i])) return fail(SVO_ERR_NAN, "scene_set_transforms_trs: entry %d is not finite", i);
+  std::vector<double> local((size_t)P * 12);
+  for (int p = 0; p < P; ++p) {
+    const double *R = rts + 15 * p, *t = R + 9, *d = R + 12;
+    for (int i = 0; i < 3; ++i) {
+      if (!(d[i] > 0.0)) return fail(SVO_ERR_ARG, "scene_set_transforms_trs: part %d: dimension %d is not positive", p, i);
+      for (int j = 0; j < 3; ++j) {
+        const double rr = R[3 * i] * R[3 * j] + R[3 * i + 1] * R[3 * j + 1] + R[3 * i + 2] * R[3 * j + 2];
+        if (std::fabs(rr - (i == j ? 1.0 : 0.0)) > 1e-9)
+          return fail(SVO_ERR_ARG, "scene_set_transforms_trs: part %d: R is not orthonormal", p);
+      }
+    }
+    // x_parent = R (d * x) + t: column j of the linear part is d_j R[:, j]
+    double *m = local.data() + 12 * p;
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) m[4 * i + j] = R[3 * i + j] * d[j];
+      m[4 * i + 3] = t[i];
+    }
+  }
+  return scene_set_transforms(s, local.data(), stream);
+}
+
 svo_status scene_set_transforms_device(svo_scene *s, const double *local_dev, void *stream) {
   if (!s || !local_dev) return fail(SVO_ERR_ARG, "scene_set_transforms_device: NULL argument");
   CK(cudaSetDevice(s->ctx->device));

@@ -452,3 +452,59 @@ def test_shade_matches_oracle(ctx, pr1):
         with pytest.raises(g.SvoError):
             gs.sc.shade(r, h, light, ambient, bg)
     torch.cuda.synchronize()
+
+
+def test_octree_dimension_poses(ctx):
+    """Sec. III-B poses (rotation, translation, per-axis octree dimensions)
+    through scene_set_transforms_trs: equal to the oracle, and bit-identical
+    to the same poses given as [R diag(s) | t] affines; a transform tree of
+    such poses composes like any affine one."""
+    import paper_1911_06001_gb300 as g
+
+    rng = np.random.default_rng(4040)
+    assets = []
+    for depth in (4, 5, 6):
+        n = 1 << depth
+        occ = np.nonzero(rng.random(n ** 3) < 0.05)[0]
+        assets.append(synthetic.make_asset(depth, (occ % n, (occ // n) % n, occ // (n * n))))
+    P = 24
+    parent = np.array([-1 if i < 8 else int(rng.integers(0, i)) for i in range(P)], np.int32)
+    rts = np.zeros((P, 15))
+    for p in range(P):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        rts[p, :9] = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                               [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                               [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]]).ravel()
+        rts[p, 9:12] = rng.uniform(-3, 3, 3) if parent[p] < 0 else rng.uniform(-1, 1, 3)
+        rts[p, 12:15] = rng.uniform(0.4, 2.5, 3)
+    local = oracle.trs_to_local(rts)
+    scene = synthetic.Scene("trs", assets, rng.integers(0, 3, P).astype(np.int32), parent, local)
+    gs = GpuScene(ctx, scene)
+    so = oracle.SceneOracle(scene)
+    rays = synthetic.random_rays(30000, rng, (-5,) * 3, (5,) * 3)
+    ref = gs.trace(rays, 7)  # poses set as affines by GpuScene
+    gs.sc.set_transforms_trs(rts)
+    gs.sc.refit()
+    got = gs.trace(rays, 7)
+    rep = compare(scene, local, rays, got, so.trace(rays, local=local))
+    assert rep["hits"] > 1000
+    for k in ("t", "part", "voxel", "flags"):
+        assert np.array_equal(got[k], ref[k]), k
+    # rejected poses change nothing
+    bad = rts.copy()
+    bad[3, 0] += 1e-6  # R no longer orthonormal
+    with pytest.raises(g.SvoError):
+        gs.sc.set_transforms_trs(bad)
+    bad = rts.copy()
+    bad[5, 13] = 0.0  # a zero dimension
+    with pytest.raises(g.SvoError):
+        gs.sc.set_transforms_trs(bad)
+    bad = rts.copy()
+    bad[1, 10] = np.nan
+    with pytest.raises(g.SvoError):
+        gs.sc.set_transforms_trs(bad)
+    gs.sc.refit()
+    again = gs.trace(rays, 7)
+    assert np.array_equal(again["part"], got["part"]) and np.array_equal(again["t"], got["t"])

@@ -573,3 +573,74 @@ def test_static_union_closed_forms():
     x, y, z = synthetic.unpack_ids(a.leaf_ids, 4)
     want = np.unique(synthetic.pack_ids(x + 2, y + 1, z, 5))
     assert np.array_equal(u2.leaf_ids, want)
+
+
+def _rot(rng):
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_trs_to_local_closed_forms():
+    """Sec. III-B poses: x_parent = R (s * x) + t, so column j of the linear
+    part is s_j times column j of R."""
+    rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    row = np.concatenate([rz.ravel(), [1.0, 2.0, 3.0], [2.0, 3.0, 5.0]])
+    m = oracle.trs_to_local(row).reshape(3, 4)
+    assert np.array_equal(m[:, :3], np.array([[0.0, -3.0, 0.0], [2.0, 0.0, 0.0], [0.0, 0.0, 5.0]]))
+    assert np.array_equal(m[:, 3], [1.0, 2.0, 3.0])
+    # the unit cube's far corner lands at R s + t
+    assert np.allclose(m[:, :3] @ np.ones(3) + m[:, 3], rz @ np.array([2.0, 3.0, 5.0]) + [1.0, 2.0, 3.0])
+
+
+def test_octree_dims_closed_form():
+    """One leaf, cell (1, 0, 0) of a depth-1 asset, dimensions (2, 4, 8) at
+    t = (1, 2, 3): the world box is [2, 3] x [2, 4] x [3, 7]."""
+    ids = synthetic.pack_ids(np.array([1]), np.array([0]), np.array([0]), 1)
+    row = np.concatenate([np.eye(3).ravel(), [1.0, 2.0, 3.0], [2.0, 4.0, 8.0]])
+    rays = np.array([[0.0, 3.0, 5.0, 0.0, 1.0, 0.0, 0.0, np.inf],
+                     [0.0, 3.0, 5.0, 0.0, 2.0, 0.0, 0.0, np.inf],
+                     [0.0, 4.5, 5.0, 0.0, 1.0, 0.0, 0.0, np.inf],    # above the box: miss
+                     [2.5, 3.0, 0.0, 0.0, 0.0, 0.0, 1.0, np.inf],    # along z from below: enters at z = 3
+                     [0.0, 3.0, 5.0, 0.0, 1.0, 0.0, 0.0, 1.5]])      # tmax before the box
+    out = oracle.trace_octree_dims([ids], [1], row, rays)
+    assert list(out["t"][:2]) == [2.0, 1.0]
+    assert out["part"][2] == oracle.MISS_PART and out["part"][4] == oracle.MISS_PART
+    assert out["t"][3] == 3.0 and out["voxel"][3] == ids[0]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_octree_dims_equal_the_affine_pose(seed):
+    """The Sec. III-B form (rigid inverse, octree of dimensions s) and the
+    general affine [R diag(s) | t] give the same closest hits: brute force
+    over every leaf against the oracle's descent."""
+    rng = np.random.default_rng(900 + seed)
+    assets, leaf_ids = [], []
+    for depth in (2, 3, 4):
+        n = 1 << depth
+        occ = np.nonzero(rng.random(n ** 3) < 0.15)[0]
+        a = synthetic.make_asset(depth, (occ % n, (occ // n) % n, occ // (n * n)))
+        assets.append(a)
+    P = 5
+    part_asset = rng.integers(0, 3, P).astype(np.int32)
+    rts = np.zeros((P, 15))
+    for p in range(P):
+        rts[p, :9] = _rot(rng).ravel()
+        rts[p, 9:12] = rng.uniform(-2, 2, 3)
+        rts[p, 12:15] = rng.uniform(0.3, 3.0, 3)
+    scene = synthetic.Scene("trs", assets, part_asset, np.full(P, -1, np.int32), oracle.trs_to_local(rts))
+    rays = synthetic.random_rays(300, rng, (-3,) * 3, (3,) * 3)
+    ref = oracle.SceneOracle(scene).trace(rays)
+    got = oracle.trace_octree_dims([assets[a].leaf_ids for a in part_asset], [assets[a].depth for a in part_asset],
+                                   rts, rays)
+    hit = ref["part"] != oracle.MISS_PART
+    assert hit.sum() > 30
+    assert np.array_equal(got["part"] != oracle.MISS_PART, hit)
+    assert np.allclose(got["t"][hit], ref["t"][hit], rtol=1e-12, atol=1e-12)
+    with np.errstate(invalid="ignore"):  # inf - inf where a ray meets one leaf
+        clear = hit & (ref["second"] - ref["t"] > 1e-9 * np.maximum(np.abs(ref["t"]), 1.0))
+    assert np.array_equal(got["part"][clear], ref["part"][clear])
+    assert np.array_equal(got["voxel"][clear], ref["voxel"][clear])
