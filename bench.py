@@ -471,6 +471,22 @@ def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -
         torch.cuda.synchronize()
         return float(np.median([a.elapsed_time(b) for a, b in evs[2:]]))
 
+    def timed_split(f):
+        """(trace ms, FP64 pass ms), medians: the pass deferred and run after an event."""
+        evs = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            sc.trace(rays, hits, flags=f | g.TRACE_DEFER_FIX)
+            e[1].record()
+            ctx.fix_pending()
+            e[2].record()
+            evs.append(e)
+        torch.cuda.synchronize()
+        return (float(np.median([a.elapsed_time(b) for a, b, _ in evs[2:]])),
+                float(np.median([b.elapsed_time(c) for _, b, c in evs[2:]])))
+
     out = {"workload": f"{scene.n_parts} parts (depth 6-11 pool assets, affine with shear) in a cube of side "
                        f"{scene.meta['box']:.1f}", "refit_ms": timed(lambda: sc.refit())}
     for name, r_np, extra in (("camera_1920x1080", cam_np, g.trace_image(1920)), ("inner_1M", inner_np, 0)):
@@ -481,12 +497,14 @@ def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -
         for label, cull in (("clusters", 0), ("grid", g.TRACE_GRID)):
             f = g.TRACE_DEFAULT | extra | cull
             ms = timed(lambda: sc.trace(rays, hits, flags=f))
+            trace_ms, fix_ms = timed_split(f)
             st = g.new_stats(dev)
             sc.trace(rays, hits, flags=f | g.TRACE_STATS, stats=st)
             torch.cuda.synchronize()
             s = g.read_stats(st)
-            row[label] = {"ms": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
-                          "parts_tested_per_ray": s["parts_tested"] / n}
+            row[label] = {"ms": ms, "mrays_per_s": n / (ms / 1e3) / 1e6, "trace_ms": trace_ms, "fp64_pass_ms": fix_ms,
+                          "parts_tested_per_ray": s["parts_tested"] / n, "flagged": s["flagged"],
+                          "fixed": s["fixed"]}
         row["grid_speedup"] = row["clusters"]["ms"] / row["grid"]["ms"]
         out[name] = row
     ctx.check_device()

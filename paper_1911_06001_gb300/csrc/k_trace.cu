@@ -1099,8 +1099,9 @@ __device__ __forceinline__ void write_fixed(const TraceItem &I, unsigned long lo
 //   * with a contender list (the leaves that may still be the closest hit),
 //     lane q intersects contender q with the exact closed-box rule and a warp
 //     reduction keeps the lexicographic minimum of (t, part, voxel);
-//   * without one (the list overflowed), lane 0 re-traces the ray: the FP32
-//     descent with inflated boxes, every leaf reached decided in FP64.
+//   * without one (the list overflowed), the warp re-traces the ray, the
+//     parts dealt over the lanes: the FP32 descent with inflated boxes, every
+//     leaf reached decided in FP64.
 // GB300 issues FP64 at 2 lanes per clock per SM, so spreading a ray's
 // contenders over lanes (instead of one lane looping over them) cuts the
 // pass's latency by the contender count.  List entries are dealt round-robin
@@ -1141,37 +1142,47 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
       if (lane == 0) write_fixed(I, ray, st, why);
       continue;
     }
-    if (lane == 0) {  // the other lanes wait: the next entry is warp-wide again
-      RayW r;
-      r.ox = o.x;
-      r.oy = o.y;
-      r.oz = o.z;
-      r.tmin = o.w;
-      r.dx = d.x;
-      r.dy = d.y;
-      r.dz = d.z;
-      r.tmax = d.w;
-      r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
-      r.inv_len = 0.f;
-      r.onorm = 0.f;
-      HybridState hs;
-      hs.ex.t = Num<double>::inf();
-      hs.ex.part = kMissPart;
-      hs.ex.vox = kMissVoxel;
-      hs.o = o;
-      hs.d = d;
-      uint2 stk_local[kMaxDepth];
-      for (int p = 0; p < I.n_parts; ++p) {
+    // no contender list (it overflowed): the warp re-traces the ray, lane q
+    // taking parts q, q + 32, ...; each lane keeps the exact minimum over its
+    // parts, the warp's best hit so far prunes whole parts, and a warp
+    // reduction gives the overall minimum
+    RayW r;
+    r.ox = o.x;
+    r.oy = o.y;
+    r.oz = o.z;
+    r.tmin = o.w;
+    r.dx = d.x;
+    r.dy = d.y;
+    r.dz = d.z;
+    r.tmax = d.w;
+    r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
+    r.inv_len = 0.f;
+    r.onorm = 0.f;
+    HybridState hs;
+    hs.ex.t = Num<double>::inf();
+    hs.ex.part = kMissPart;
+    hs.ex.vox = kMissVoxel;
+    hs.o = o;
+    hs.d = d;
+    uint2 stk_local[kMaxDepth];
+    double best = Num<double>::inf();  // the warp's best hit t after each round
+    for (int base = 0; base < I.n_parts; base += 32) {
+      const int p = base + lane;
+      if (p < I.n_parts) {
         float tin, tref;
-        if (!part_cull(r, I.hot[p], tin, tref)) continue;
-        if (tin > __double2float_ru(hs.ex.t)) continue;  // every candidate of p starts after the best hit
-        hs.inv64 = I.inv64 + 12 * p;
-        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs, nullptr,
-                                              err, cnt);
+        if (part_cull(r, I.hot[p], tin, tref) && !(tin > __double2float_ru(fmin(best, hs.ex.t)))) {
+          hs.inv64 = I.inv64 + 12 * p;
+          trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs,
+                                                nullptr, err, cnt);
+        }
       }
-      write_fixed(I, ray, hs.ex, why);
+      double b = hs.ex.t;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
+      best = b;
     }
-    __syncwarp();
+    warp_min(hs.ex);
+    if (lane == 0) write_fixed(I, ray, hs.ex, why);
   }
   // count fixed rays once per launch
   if (L.stats && blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);
