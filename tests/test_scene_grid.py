@@ -305,3 +305,62 @@ def test_grid_rebuilt_in_graph_replays(ctx):
         torch.cuda.synchronize()
         res = gs.trace(rays_np, DEFAULT | GRID)
         compare(scene, local, rays_np, res, so.trace(rays_np, local=local))
+
+
+def test_grid_in_batches_and_without_allocation(ctx):
+    """The grid flag in one persistent launch over scenes with and without a
+    grid (and one scene twice: its grid is built once), and through
+    trace_rays_noalloc: every result equals the same scene traced alone."""
+    import ctypes as C
+
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    rng = np.random.default_rng(78)
+    specs = [(40, 10.0), (100, 4.0 * 100 ** (1 / 3)), (300, 4.0 * 300 ** (1 / 3))]
+    scenes, items, outs = [], [], []
+    for P, box in specs:
+        sc = _affine_scene(rng, P, box)
+        gs = GpuScene(ctx, sc)
+        scenes.append((sc, gs, box))
+    for k in (0, 1, 2, 1):
+        sc, gs, box = scenes[k]
+        rays_np = _outside_camera_rays(box, 64 + 16 * k, 48)
+        rt = torch.from_numpy(rays_np).cuda()
+        ht = torch.empty((rt.shape[0], 2), dtype=torch.int64, device="cuda")
+        ft = torch.zeros(rt.shape[0], dtype=torch.int32, device="cuda")
+        items.append((gs.sc, rt, ht, ft))
+        outs.append((gs, rays_np, ht, ft))
+    # new poses after the last trace: the batch must rebuild the grids first
+    for sc, gs, box in scenes:
+        local = sc.local.copy()
+        local[:, [3, 7, 11]] += rng.uniform(-box / 8, box / 8, (sc.n_parts, 3))
+        gs.set_pose(local)
+    ctx.trace_batch(items, flags=DEFAULT | GRID)
+    torch.cuda.synchronize()
+    for gs, rays_np, ht, ft in outs:
+        got = g.decode_hits(ht)
+        got["flags"] = ft.cpu().numpy().astype(np.uint32)
+        ref = gs.trace(rays_np, DEFAULT)
+        compare(gs.scene, gs.local, rays_np, got, oracle.SceneOracle(gs.scene).trace(rays_np, local=gs.local))
+        both = ((got["flags"] | ref["flags"]) & 1) == 0
+        assert np.array_equal(got["part"][both], ref["part"][both])
+    # the no-allocation entry point with the grid
+    lib = g._lib.load()
+    sc, gs, box = scenes[2]
+    rays_np = _outside_camera_rays(box, 96, 64)
+    r = torch.from_numpy(rays_np).cuda()
+    hits = torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda")
+    rf = torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")
+    stream = C.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    local = sc.local.copy()
+    local[:, [3, 7, 11]] += 0.5
+    gs.set_pose(local)
+    rc = lib.trace_rays_noalloc(gs.sc.h, C.c_void_p(r.data_ptr()), r.shape[0], C.c_void_p(hits.data_ptr()),
+                                C.c_void_p(rf.data_ptr()), DEFAULT | GRID, stream)
+    assert rc == 0, lib.svo_last_error()
+    torch.cuda.synchronize()
+    got = g.decode_hits(hits)
+    got["flags"] = rf.cpu().numpy().astype(np.uint32)
+    compare(sc, local, rays_np, got, oracle.SceneOracle(sc).trace(rays_np, local=local))
