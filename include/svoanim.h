@@ -273,17 +273,27 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
                        svo_trace_stats *stats, void *stream);
 
 /* trace_rays for rays and hits in HOST memory (async on `stream`).
- *   * Page-locked buffers mapped into the device's address space (e.g.
- *     cudaHostAlloc'ed; on GB300 reached over the chip-to-chip link) are read
- *     and written by the kernels directly, with no staging copy.
- *   * Other buffers are staged: the library copies rays to its per-stream
- *     device staging, traces, and copies hits (and ray_flags, if not NULL)
- *     back, in chunks of about 512 K rays (whole image rows with
- *     SVO_TRACE_IMAGE) through three internal streams so that one chunk's
- *     copies overlap another's trace; `stream` resumes after the last chunk
- *     is back.  Pageable buffers make the copies block the host.  The staging
- *     grows with cudaMalloc when n exceeds the largest n staged so far on
- *     this stream.
+ *   * Batches of at most 262144 rays in page-locked buffers mapped into the
+ *     device's address space (e.g. cudaHostAlloc'ed; on GB300 reached over
+ *     the chip-to-chip link) are read and written by the kernels directly,
+ *     with no staging copy: the lowest latency for one call.
+ *   * Larger batches are copied in by the copy engines, to one of two
+ *     per-stream staging halves that successive calls alternate between.  A
+ *     call's copy-in waits only until its half is free (the call two before
+ *     has finished with it), not for earlier work on `stream`, so in a frame
+ *     loop the next frame's rays stream in while the current frame is
+ *     traced.  The trace waits for earlier work on `stream` (poses, refit).
+ *     The rays are therefore read at some time between the call and the
+ *     completion of its work on `stream`: leave them unchanged until then.
+ *     - Mapped page-locked hits (and ray_flags, if not NULL) are written by
+ *       the kernels directly, and the rays are traced in one launch.
+ *     - Other hits buffers are staged as well: chunks of about 512 K rays
+ *       (whole image rows with SVO_TRACE_IMAGE) are copied in, traced and
+ *       copied back through three internal streams, so that one chunk's
+ *       copies overlap another's trace.  Pageable buffers make the copies
+ *       block the host.
+ *     `stream` resumes once every hit is back.  The staging grows with
+ *     cudaMalloc when n exceeds the largest n staged so far on this stream.
  * The call returns before the work finishes: synchronise `stream` before
  * reading hits.  SVO_TRACE_STATS and SVO_TRACE_REUSE are not supported here
  * (SVO_ERR_ARG); SVO_TRACE_DEFER_FIX is ignored. */

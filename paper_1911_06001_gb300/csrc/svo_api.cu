@@ -59,6 +59,14 @@ struct AssetRec {
 };
 
 // Scratch of one stream: launch counters and the FP64 re-intersection list.
+// trace_rays_host: batches up to this size in mapped page-locked memory are
+// traced in place (zero copy); larger ones go through the staged pipeline
+constexpr unsigned long long kZeroCopyMaxRays = 1ull << 18;
+
+// One staging half of trace_rays_host for n rays: rays | hits | flags,
+// rounded so that the second half starts 256-byte aligned.
+inline size_t stage_half_bytes(unsigned long long n) { return ((size_t)n * (32 + 16 + 4) + 255) & ~(size_t)255; }
+
 struct Slot {
   unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
   unsigned long long *d_fix = nullptr;
@@ -66,10 +74,12 @@ struct Slot {
   uint4 *d_cand = nullptr;                   // contender leaves of the first cand_cap flagged rays
   unsigned long long cand_cap = 0;
   TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
-  char *d_stage = nullptr;                   // rays | hits | flags staging of trace_rays_host
+  char *d_stage = nullptr;                   // trace_rays_host: two halves of rays | hits | flags
   cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};  // trace_rays_host: copy in, trace, copy out
   std::vector<cudaEvent_t> pipe_ev;                    // 2 per chunk + 2
-  unsigned long long stage_rays = 0;
+  cudaEvent_t stage_free[2] = {nullptr, nullptr};      // a half's last reader (the copy out) is done
+  int stage_turn = 0;                                  // the half the next call uses
+  unsigned long long stage_rays = 0;                   // capacity of each half
   void *d_order = nullptr;                   // ray-ordering keys, histogram and permutations
   size_t order_cap = 0;
 };
@@ -336,6 +346,8 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
     for (cudaStream_t ps : kv.second.pipe)
       if (ps) cudaStreamDestroy(ps);
     for (cudaEvent_t e : kv.second.pipe_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : kv.second.stage_free)
+      if (e) cudaEventDestroy(e);
     delete kv.second.pending;
   }
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -832,10 +844,10 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   if (n > 0xFFFFFFFFull) return fail(SVO_ERR_LIMIT, "trace_rays_host: %llu rays", (unsigned long long)n);
   CK(cudaSetDevice(s->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  // Page-locked buffers that the device can address (on GB300 over the
-  // chip-to-chip link) are read and written by the kernels directly: the
-  // trace streams its rays in and its hits out, with no staging copy.
-  {
+  // Small batches in page-locked buffers that the device can address (on
+  // GB300 over the chip-to-chip link) are read and written by the kernels
+  // directly, with no staging copy: the lowest latency for one call.
+  if (n <= kZeroCopyMaxRays) {
     const void *dev_rays = mapped_device_pointer(rays_host);
     void *dev_hits = mapped_device_pointer(hits_host);
     void *dev_flags = ray_flags_host ? mapped_device_pointer(ray_flags_host) : nullptr;
@@ -844,12 +856,25 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
       return trace_rays(s, static_cast<const float *>(dev_rays), n, static_cast<svo_hit *>(dev_hits),
                         static_cast<uint32_t *>(dev_flags), flags & ~SVO_TRACE_DEFER_FIX, nullptr, stream);
   }
-  // Otherwise chunks of ~512 K rays (whole image rows with SVO_TRACE_IMAGE) are copied
-  // in, traced (with their FP64 pass) and copied out on three streams, so
-  // that the copies of one chunk overlap the trace of another.
+  // Otherwise the rays are copied in by the copy engines, to one of two
+  // staging halves that successive calls alternate between.  A call's
+  // copy-in waits only for its half to be free, not for the caller's earlier
+  // work, so in a frame loop the next frame's rays stream in while this
+  // frame is traced.
+  //   * Mapped page-locked hits (and flags) are written by the kernels
+  //     directly, and the rays are traced in one launch (split launches would
+  //     run their load-imbalance tails one after another).
+  //   * Other hits buffers are staged too: chunks of ~512 K rays (whole image
+  //     rows with SVO_TRACE_IMAGE) are copied in, traced (with their FP64
+  //     pass) and copied out on three streams, so that the copies of one
+  //     chunk overlap the trace of another.
+  void *dev_hits = mapped_device_pointer(hits_host);
+  void *dev_flags = ray_flags_host ? mapped_device_pointer(ray_flags_host) : nullptr;
+  const bool out_direct =
+      dev_hits && !(reinterpret_cast<uintptr_t>(dev_hits) & 15) && (!ray_flags_host || dev_flags);
   constexpr unsigned long long kChunk = 1ull << 19;
-  unsigned long long chunk = kChunk;
-  if (flags & SVO_TRACE_IMAGE_TILES) {
+  unsigned long long chunk = out_direct ? n : kChunk;
+  if (!out_direct && (flags & SVO_TRACE_IMAGE_TILES)) {
     const unsigned long long w = flags >> 16;
     if (w > 0) chunk = (kChunk / w > 0 ? kChunk / w : 1) * w;
   }
@@ -868,10 +893,12 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
         sl.d_stage = nullptr;
         sl.stage_rays = 0;
       }
-      cudaError_t e = cudaMalloc(&sl.d_stage, n * (32 + 16 + 4));
+      cudaError_t e = cudaMalloc(&sl.d_stage, 2 * stage_half_bytes(n));
       if (e != cudaSuccess) return fail(SVO_ERR_OOM, "trace_rays_host: staging: %s", cudaGetErrorString(e));
       sl.stage_rays = n;
     }
+    for (cudaEvent_t &e : sl.stage_free)
+      if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (cudaStream_t &ps : sl.pipe)
       if (!ps) CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
     while (sl.pipe_ev.size() < 2 * n_chunks + 2) {
@@ -883,31 +910,46 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
     slp = &sl;
   }
   const unsigned long long cap = slp->stage_rays;
+  const int half = slp->stage_turn;
+  slp->stage_turn ^= 1;
+  stage += (size_t)half * stage_half_bytes(cap);
   float *d_rays = reinterpret_cast<float *>(stage);
   svo_hit *d_hits = reinterpret_cast<svo_hit *>(stage + cap * 32);
   uint32_t *d_flags = ray_flags_host ? reinterpret_cast<uint32_t *>(stage + cap * 48) : nullptr;
-  cudaStream_t h2d = slp->pipe[0], comp = slp->pipe[1], d2h = slp->pipe[2];
+  // with direct hit writes there is one trace, run on the caller's stream
+  cudaStream_t h2d = slp->pipe[0], comp = out_direct ? st : slp->pipe[1], d2h = slp->pipe[2];
   cudaEvent_t *ev = slp->pipe_ev.data();
-  // the pipeline starts after the caller's earlier work (poses, refit) ...
-  CK(cudaEventRecord(ev[0], st));
-  CK(cudaStreamWaitEvent(h2d, ev[0], 0));
-  CK(cudaStreamWaitEvent(comp, ev[0], 0));
-  CK(cudaStreamWaitEvent(d2h, ev[0], 0));
+  // the copy-in waits for its staging half only; the traces wait for the
+  // caller's earlier work (poses, refit) ...
+  CK(cudaStreamWaitEvent(h2d, slp->stage_free[half], 0));
+  if (!out_direct) {
+    CK(cudaEventRecord(ev[0], st));
+    CK(cudaStreamWaitEvent(comp, ev[0], 0));
+    CK(cudaStreamWaitEvent(d2h, ev[0], 0));
+  }
   for (unsigned long long k = 0; k < n_chunks; ++k) {
     const unsigned long long off = k * chunk, m = (n - off) < chunk ? (n - off) : chunk;
     CK(cudaMemcpyAsync(d_rays + off * 8, rays_host + off * 8, m * 32, cudaMemcpyHostToDevice, h2d));
     CK(cudaEventRecord(ev[2 + 2 * k], h2d));
     CK(cudaStreamWaitEvent(comp, ev[2 + 2 * k], 0));
-    svo_status rc = trace_rays(s, d_rays + off * 8, m, d_hits + off, d_flags ? d_flags + off : nullptr,
-                               flags & ~SVO_TRACE_DEFER_FIX, nullptr, comp);
+    svo_hit *hits_k = out_direct ? static_cast<svo_hit *>(dev_hits) + off : d_hits + off;
+    uint32_t *flags_k = out_direct ? (dev_flags ? static_cast<uint32_t *>(dev_flags) + off : nullptr)
+                                   : (d_flags ? d_flags + off : nullptr);
+    svo_status rc = trace_rays(s, d_rays + off * 8, m, hits_k, flags_k, flags & ~SVO_TRACE_DEFER_FIX, nullptr, comp);
     if (rc != SVO_OK) return rc;
+    if (out_direct) continue;
     CK(cudaEventRecord(ev[3 + 2 * k], comp));
     CK(cudaStreamWaitEvent(d2h, ev[3 + 2 * k], 0));
     CK(cudaMemcpyAsync(hits_host + off, d_hits + off, m * 16, cudaMemcpyDeviceToHost, d2h));
     if (d_flags) CK(cudaMemcpyAsync(ray_flags_host + off, d_flags + off, m * 4, cudaMemcpyDeviceToHost, d2h));
   }
-  // ... and the caller's stream continues once every chunk is back
+  // ... and the caller's stream continues once every hit is back
+  if (out_direct) {
+    CK(cudaEventRecord(slp->stage_free[half], st));
+    return ok();
+  }
   CK(cudaEventRecord(ev[1], d2h));
+  CK(cudaEventRecord(slp->stage_free[half], d2h));
   CK(cudaStreamWaitEvent(st, ev[1], 0));
   return ok();
 }

@@ -164,6 +164,14 @@ def test_host_buffers_equal_device_trace(ctx):
             got = g.decode_hits(hh)
             got["flags"] = fh.numpy().astype(np.uint32)
             _same(got, ref)
+    # a small pinned batch is traced in place (zero copy)
+    m = 100_003
+    rh = torch.from_numpy(np.ascontiguousarray(rays[:m], dtype=np.float32)).pin_memory()
+    hh = torch.empty((m, 2), dtype=torch.int64).pin_memory()
+    gs.sc.trace_host(rh, hh, flags=g.TRACE_DEFAULT)
+    torch.cuda.synchronize()
+    got, ref = g.decode_hits(hh), gs.trace(rays[:m], g.TRACE_DEFAULT)
+    assert np.array_equal(got["part"], ref["part"]) and np.array_equal(got["voxel"], ref["voxel"])
     hp = torch.empty((1000, 2), dtype=torch.int64)  # pageable
     gs.sc.trace_host(torch.from_numpy(np.ascontiguousarray(rays[:1000], dtype=np.float32)), hp)
     torch.cuda.synchronize()
@@ -173,3 +181,36 @@ def test_host_buffers_equal_device_trace(ctx):
     with pytest.raises(g.SvoError):
         gs.sc.trace_host(torch.zeros((8, 8)), torch.zeros((8, 2), dtype=torch.int64), flags=g.TRACE_DEFAULT | g.TRACE_REUSE)
     ctx.set_trace_config(128, 4)
+
+
+def test_host_frame_loop_overlaps_calls(ctx):
+    """trace_rays_host in a frame loop with no synchronisation between frames:
+    each call's copy-in may run while the previous frame is still traced
+    (two staging halves).  Every frame, with its own poses, rays and hits,
+    must equal the device trace of that frame."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    fig = synthetic.articulated_figure(depth=7)
+    gs = GpuScene(ctx, fig.scene)
+    w, h = 640, 480  # 307,200 rays: above the zero-copy limit, one chunk
+    rng = np.random.default_rng(13)
+    ray_sets = [fig.rays(w, h), synthetic.random_rays(w * h, rng, (-2,) * 3, (2,) * 3)]
+    host_rays = [torch.from_numpy(np.ascontiguousarray(r)).pin_memory() for r in ray_sets]
+    frames = [(f, f % 2) for f in range(0, 50, 7)]
+    hits = [torch.empty((w * h, 2), dtype=torch.int64).pin_memory() for _ in frames]
+    flags = g.TRACE_DEFAULT
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for (f, k), hh in zip(frames, hits):
+        gs.sc.set_transforms(fig.pose(f), stream=stream)
+        gs.sc.refit(stream=stream)
+        gs.sc.trace_host(host_rays[k], hh, flags=flags, stream=stream)
+    stream.synchronize()
+    for (f, k), hh in zip(frames, hits):
+        gs.set_pose(fig.pose(f))
+        ref = gs.trace(ray_sets[k], flags)
+        got = g.decode_hits(hh)
+        for key in ("t", "part", "voxel"):
+            assert np.array_equal(got[key], ref[key]), (f, key)
