@@ -881,6 +881,7 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
   const unsigned long long n_chunks = (n + chunk - 1) / chunk;
   char *stage = nullptr;
   Slot *slp = nullptr;
+  int half = 0;
   {
     std::lock_guard<std::mutex> g(s->ctx->mu);
     Slot &sl = s->ctx->slots[stream];
@@ -908,10 +909,10 @@ svo_status trace_rays_host(svo_scene *s, const float *rays_host, uint64_t n, svo
     }
     stage = sl.d_stage;
     slp = &sl;
+    half = sl.stage_turn;
+    sl.stage_turn ^= 1;
   }
   const unsigned long long cap = slp->stage_rays;
-  const int half = slp->stage_turn;
-  slp->stage_turn ^= 1;
   stage += (size_t)half * stage_half_bytes(cap);
   float *d_rays = reinterpret_cast<float *>(stage);
   svo_hit *d_hits = reinterpret_cast<svo_hit *>(stage + cap * 32);
