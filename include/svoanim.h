@@ -197,6 +197,12 @@ svo_status svo_upload(svo_ctx *ctx, const svo_desc *desc, svo_handle *out);
 svo_status svo_release(svo_ctx *ctx, svo_handle h);
 /* Depth, interior node count and leaf count of an asset (any pointer may be NULL). */
 svo_status svo_asset_info(svo_ctx *ctx, svo_handle h, int32_t *depth, uint64_t *n_nodes, uint64_t *n_leaves);
+/* Copy an asset's device data back to the host (synchronous; the device
+ * synchronises with the copy): its n_nodes interior node descriptors (8 bytes
+ * each, the svo_build_host layout) into `nodes` and its n_leaves leaf colours
+ * into `rgb`.  Either pointer may be NULL to skip it.  Poses, refits and
+ * traces never write an asset: the data read back is what svo_upload stored. */
+svo_status svo_read_asset(svo_ctx *ctx, svo_handle h, void *nodes, uint32_t *rgb);
 
 /* ----------------------------------------------------------------- scenes */
 

@@ -96,6 +96,14 @@ class Context:
         _lib.check(self.lib.svo_asset_info(self.h, C.c_uint32(handle), C.byref(d), C.byref(nn), C.byref(nl)))
         return {"depth": d.value, "n_nodes": nn.value, "n_leaves": nl.value}
 
+    def read_asset(self, handle: int):
+        """An asset's device data: (nodes uint32[n_nodes, 2], leaf rgb uint32[n_leaves])."""
+        info = self.asset_info(handle)
+        nodes = np.zeros((info["n_nodes"], 2), dtype=np.uint32)
+        rgb = np.zeros(info["n_leaves"], dtype=np.uint32)
+        _lib.check(self.lib.svo_read_asset(self.h, C.c_uint32(handle), nodes.ctypes.data, rgb.ctypes.data))
+        return nodes, rgb
+
     def scene(self, part_assets, parent) -> "Scene":
         return Scene(self, part_assets, parent)
 

@@ -48,7 +48,7 @@ COLOR_INVALID = 0xFFFFFFFF
 EXPORTS = [
     "svo_ctx_create", "svo_ctx_destroy", "svo_last_error", "svo_status_string", "svo_check_device",
     "svo_set_trace_config", "svo_get_trace_config",
-    "svo_build_host", "svo_upload", "svo_release", "svo_asset_info",
+    "svo_build_host", "svo_upload", "svo_release", "svo_asset_info", "svo_read_asset",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device",
     "scene_set_transforms_trs", "scene_refit",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
@@ -109,6 +109,7 @@ def load(path: str | None = None):
         "svo_upload": ([vp, C.POINTER(SvoDesc), C.POINTER(u32)], i32),
         "svo_release": ([vp, u32], i32),
         "svo_asset_info": ([vp, u32, C.POINTER(i32), C.POINTER(u64), C.POINTER(u64)], i32),
+        "svo_read_asset": ([vp, u32, vp, vp], i32),
         "scene_create": ([vp, i32, vp, vp, pvp], i32),
         "scene_destroy": ([vp], i32),
         "scene_set_transforms": ([vp, vp, vp], i32),

@@ -58,7 +58,6 @@ struct AssetRec {
   int refs = 0;
 };
 
-// Scratch of one stream: launch counters and the FP64 re-intersection list.
 // trace_rays_host: batches up to this size in mapped page-locked memory are
 // traced in place (zero copy); larger ones go through the staged pipeline
 constexpr unsigned long long kZeroCopyMaxRays = 1ull << 18;
@@ -67,6 +66,7 @@ constexpr unsigned long long kZeroCopyMaxRays = 1ull << 18;
 // rounded so that the second half starts 256-byte aligned.
 inline size_t stage_half_bytes(unsigned long long n) { return ((size_t)n * (32 + 16 + 4) + 255) & ~(size_t)255; }
 
+// Scratch of one stream: launch counters and the FP64 re-intersection list.
 struct Slot {
   unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
   unsigned long long *d_fix = nullptr;
@@ -454,6 +454,26 @@ svo_status svo_asset_info(svo_ctx *ctx, svo_handle h, int32_t *depth, uint64_t *
   if (depth) *depth = a->depth;
   if (n_nodes) *n_nodes = a->n_nodes;
   if (n_leaves) *n_leaves = a->n_leaves;
+  return ok();
+}
+
+svo_status svo_read_asset(svo_ctx *ctx, svo_handle h, void *nodes, uint32_t *rgb) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_read_asset: ctx is NULL");
+  uint2 *d_nodes = nullptr;
+  uint32_t *d_rgb = nullptr;
+  uint64_t n_nodes = 0, n_leaves = 0;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    AssetRec *a = find_asset(ctx, h);
+    if (!a) return fail(SVO_ERR_HANDLE, "svo_read_asset: unknown handle %u", h);
+    d_nodes = a->d_nodes;
+    d_rgb = a->d_rgb;
+    n_nodes = a->n_nodes;
+    n_leaves = a->n_leaves;
+  }
+  CK(cudaSetDevice(ctx->device));
+  if (nodes && n_nodes) CK(cudaMemcpy(nodes, d_nodes, n_nodes * sizeof(uint2), cudaMemcpyDeviceToHost));
+  if (rgb && n_leaves) CK(cudaMemcpy(rgb, d_rgb, n_leaves * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   return ok();
 }
 

@@ -45,15 +45,94 @@ class Ticket:
     n_rays: int
     arrival: float          # host clock (perf_counter) of arrival
     submitted: float = 0.0  # host clock when its batch was launched
-    done: float = 0.0       # host clock when its completion was observed
+    done: float = 0.0       # host clock when its completion (or expiry, or cancellation) was observed
     slot: int = -1
     offset: int = 0         # first ray of the request in its slot's buffers
     instance: object = None
     hits: object = None     # CUDA int64 view [n, 2] into the slot's hit buffer (valid until the slot is reused)
+    status: str = "queued"  # queued -> running -> done, or queued -> timeout / cancelled
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
+
+
+class RequestQueue:
+    """The server's admission and batching policy (host only, no GPU).
+
+    * A request is refused at submission if it could never run: more rays
+      than a slot holds, or more bytes than the whole memory budget.
+    * Requests wait in arrival order.  A batch takes requests from the front
+      while they fit the slot and the bytes still free in the budget; a
+      request whose scene has no free instance keeps its place and the ones
+      behind it may go first.
+    * A request that has waited longer than ``max_wait`` seconds leaves the
+      queue with status "timeout"; ``cancel`` removes one with status
+      "cancelled".  Neither ever reaches the GPU.
+    """
+
+    def __init__(self, slot_rays: int, budget_bytes: int, bytes_per_ray: int, max_wait: float | None = None):
+        self.slot_rays = int(slot_rays)
+        self.budget = int(budget_bytes)
+        self.per_ray = int(bytes_per_ray)
+        self.max_wait = max_wait
+        self.waiting = collections.deque()
+        self.in_flight_bytes = 0
+
+    def __len__(self) -> int:
+        return len(self.waiting)
+
+    def submit(self, ticket: Ticket) -> Ticket:
+        if ticket.n_rays > self.slot_rays or ticket.n_rays * self.per_ray > self.budget:
+            raise AdmissionError(f"request of {ticket.n_rays} rays exceeds the slot capacity or the memory budget")
+        self.waiting.append(ticket)
+        return ticket
+
+    def cancel(self, ticket: Ticket, now: float) -> bool:
+        """Remove a waiting request; False if it is no longer waiting."""
+        try:
+            self.waiting.remove(ticket)
+        except ValueError:
+            return False
+        ticket.status, ticket.done = "cancelled", now
+        return True
+
+    def expire(self, now: float) -> list:
+        """Remove and return the requests that waited longer than max_wait."""
+        if self.max_wait is None:
+            return []
+        out = [t for t in self.waiting if now - t.arrival > self.max_wait]
+        for t in out:
+            self.waiting.remove(t)
+            t.status, t.done = "timeout", now
+        return out
+
+    def take_batch(self, capacity: int, lease) -> tuple:
+        """Requests for one slot of ``capacity`` rays: (tickets, total rays).
+        ``lease(ticket)`` returns an instance of the ticket's scene, or None
+        if all are busy; the taken tickets' bytes count as in flight."""
+        batch, total, skipped = [], 0, []
+        while self.waiting:
+            t = self.waiting[0]
+            if total + t.n_rays > capacity or self.in_flight_bytes + (total + t.n_rays) * self.per_ray > self.budget:
+                break
+            self.waiting.popleft()
+            inst = lease(t)
+            if inst is None:
+                skipped.append(t)  # keeps its place
+                continue
+            t.instance, t.offset, t.status = inst, total, "running"
+            total += t.n_rays
+            batch.append(t)
+        for t in reversed(skipped):
+            self.waiting.appendleft(t)
+        self.in_flight_bytes += total * self.per_ray
+        return batch, total
+
+    def release(self, tickets) -> None:
+        """The tickets' batch has finished: their bytes are free again."""
+        for t in tickets:
+            self.in_flight_bytes -= t.n_rays * self.per_ray
 
 
 @dataclass
@@ -71,7 +150,8 @@ class Server:
     """Render server over scenes given as (part asset handles, parent) pairs."""
 
     def __init__(self, ctx: Context, scenes, n_slots: int = 3, max_batch_rays: int = 8 << 20,
-                 memory_budget: int | None = None, instances_per_scene: int = 3, flags: int = TRACE_DEFAULT):
+                 memory_budget: int | None = None, instances_per_scene: int = 3, flags: int = TRACE_DEFAULT,
+                 max_wait: float | None = None):
         import torch
 
         self.ctx = ctx
@@ -89,8 +169,7 @@ class Server:
         per_ray = RAY_BYTES + HIT_BYTES + SCRATCH_BYTES_PER_RAY
         self.budget = memory_budget if memory_budget is not None else n_slots * max_batch_rays * per_ray
         self.per_ray = per_ray
-        self.in_flight_bytes = 0
-        self.queue = collections.deque()
+        self.queue = RequestQueue(max_batch_rays, self.budget, per_ray, max_wait)
         self.completed = []
         self.max_batch_rays = max_batch_rays
         self.on_done = None  # called for every completed ticket before its slot is reused
@@ -111,11 +190,14 @@ class Server:
     # ------------------------------------------------------------- requests
     def submit(self, request, arrival: float | None = None) -> Ticket:
         n = int(request.width) * int(request.height)
-        if n > self.max_batch_rays or n * self.per_ray > self.budget:
-            raise AdmissionError(f"request of {n} rays exceeds the slot capacity or the memory budget")
-        t = Ticket(request, n, time.perf_counter() if arrival is None else arrival)
-        self.queue.append(t)
-        return t
+        return self.queue.submit(Ticket(request, n, time.perf_counter() if arrival is None else arrival))
+
+    def cancel(self, ticket: Ticket) -> bool:
+        """Withdraw a request that is still waiting (status "cancelled")."""
+        ok = self.queue.cancel(ticket, time.perf_counter())
+        if ok:
+            self.completed.append(ticket)
+        return ok
 
     def poll(self) -> list:
         """Retire finished batches; returns the tickets completed by this call."""
@@ -125,9 +207,10 @@ class Server:
             if s.busy and s.event.query():
                 for t in s.tickets:
                     t.done = now
+                    t.status = "done"
                     self.instances[t.request.scene].append(t.instance)
-                    self.in_flight_bytes -= t.n_rays * self.per_ray
                     out.append(t)
+                self.queue.release(s.tickets)
                 s.busy = False
                 s.tickets = []
         self.completed.extend(out)
@@ -137,32 +220,27 @@ class Server:
         return out
 
     def step(self) -> int:
-        """Poll, then launch batches on free slots; returns the number of batches launched."""
+        """Poll, launch batches on free slots, then expire the requests still
+        waiting past the maximum wait; returns the number of batches launched."""
         self.poll()
         launched = 0
+
+        def lease(t):
+            free = self.instances[t.request.scene]
+            return free.popleft() if free else None
+
         for si, s in enumerate(self.slots):
-            if s.busy or not self.queue:
+            if s.busy or not len(self.queue):
                 continue
-            batch, total, skipped = [], 0, collections.deque()
-            while self.queue:
-                t = self.queue[0]
-                fits = total + t.n_rays <= s.capacity and \
-                    self.in_flight_bytes + (total + t.n_rays) * self.per_ray <= self.budget
-                if not fits:
-                    break
-                self.queue.popleft()
-                if not self.instances[t.request.scene]:
-                    skipped.append(t)  # every instance of its scene is busy: keep its place
-                    continue
-                t.instance = self.instances[t.request.scene].popleft()
-                t.offset = total
-                total += t.n_rays
-                batch.append(t)
-            while skipped:
-                self.queue.appendleft(skipped.pop())
+            batch, total = self.queue.take_batch(s.capacity, lease)
             if batch:
                 self._launch(si, s, batch, total)
                 launched += 1
+        expired = self.queue.expire(time.perf_counter())
+        self.completed.extend(expired)
+        if self.on_done is not None:
+            for t in expired:
+                self.on_done(t)
         return launched
 
     def _launch(self, si: int, s: _Slot, batch: list, total: int) -> None:
@@ -188,10 +266,9 @@ class Server:
         s.event.record(s.stream)
         s.tickets = batch
         s.busy = True
-        self.in_flight_bytes += total * self.per_ray
 
     def idle(self) -> bool:
-        return not self.queue and not any(s.busy for s in self.slots)
+        return not len(self.queue) and not any(s.busy for s in self.slots)
 
     # --------------------------------------------------------------- drivers
     def run(self, requests, on_done=None) -> list:

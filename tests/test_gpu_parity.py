@@ -508,3 +508,32 @@ def test_octree_dimension_poses(ctx):
     gs.sc.refit()
     again = gs.trace(rays, 7)
     assert np.array_equal(again["part"], got["part"]) and np.array_equal(again["t"], got["t"])
+
+
+def test_animation_never_writes_the_svos(ctx):
+    """Animation moves only poses (Sec. III): after 60 frames of poses, refits
+    and traces with every trace option, each asset's device data is byte for
+    byte what the host build produced."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    fig = synthetic.articulated_figure(depth=7)
+    gs = GpuScene(ctx, fig.scene)
+    before = [ctx.read_asset(h) for h in gs.handles]
+    for a, (nodes, rgb) in zip(fig.scene.assets, before):
+        hn, hrgb = g.build_host(a.depth, a.leaf_ids, a.rgb)
+        assert np.array_equal(nodes, hn) and np.array_equal(rgb, hrgb)
+    rays = torch.from_numpy(fig.rays(320, 180)).cuda()
+    hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device="cuda")
+    opts = [g.TRACE_DEFAULT, g.TRACE_DEFAULT | g.TRACE_REUSE, g.TRACE_FP64_FIX, g.TRACE_DEFAULT | g.trace_image(320),
+            g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN]
+    for f in range(60):
+        gs.sc.set_transforms(fig.pose(f))
+        gs.sc.refit()
+        gs.sc.trace(rays, hits, flags=opts[f % len(opts)])
+    gs.sc.hit_colors(hits)
+    torch.cuda.synchronize()
+    after = [ctx.read_asset(h) for h in gs.handles]
+    for (n0, c0), (n1, c1) in zip(before, after):
+        assert n0.tobytes() == n1.tobytes() and c0.tobytes() == c1.tobytes()

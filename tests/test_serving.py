@@ -88,3 +88,20 @@ def test_admission_by_memory(world_ctx):
     dones = sorted(t.done for t in tickets)
     # never two in flight at once: each launch happens after the previous completion
     assert all(starts[i + 1] >= dones[i] - 1e-9 for i in range(len(starts) - 1))
+
+
+def test_requests_time_out_in_the_queue(world_ctx):
+    """With a maximum queue wait, requests that cannot start in time end with
+    status "timeout" and never reach the GPU; the others complete normally."""
+    from paper_1911_06001_gb300.serving import Server
+
+    ctx, world, scenes = world_ctx
+    srv = Server(ctx, scenes, n_slots=1, max_batch_rays=1 << 16, memory_budget=(1 << 16) * 82, instances_per_scene=1,
+                 max_wait=0.0)
+    reqs = world.requests(40, rate=1e7, seed=11, resolutions=((200, 200),))
+    tickets = srv.run(reqs)
+    status = [t.status for t in tickets]
+    assert set(status) <= {"done", "timeout"}
+    assert "done" in status and "timeout" in status
+    assert all(t.hits is None and t.slot == -1 for t in tickets if t.status == "timeout")
+    assert all(t.done >= t.arrival for t in tickets)
