@@ -193,10 +193,11 @@ struct ExactState {
   unsigned long long vox;
 };
 
-// Exact closed-box entry of one leaf in FP64 (the definition the oracle
-// follows): ray to the part frame with the FP64 inverse, slab test of the leaf
-// cell's box; a zero direction component keeps the slab only if the origin
-// lies in it.  Returns whether the leaf is hit and its candidate t.
+// Closed-box entry of one leaf in FP64 (the definition the oracle follows,
+// each slab quotient taken as a product with the reciprocal of the direction
+// component): ray to the part frame with the FP64 inverse, slab test of the
+// leaf cell's box; a zero direction component keeps the slab only if the
+// origin lies in it.  Returns whether the leaf is hit and its candidate t.
 __device__ __forceinline__ bool leaf_entry64(const double *__restrict__ m, int D, unsigned long long vox, float4 o,
                                              float4 d, double &t) {
   const double ox = o.x, oy = o.y, oz = o.z, dx = d.x, dy = d.y, dz = d.z;
@@ -216,7 +217,11 @@ __device__ __forceinline__ bool leaf_entry64(const double *__restrict__ m, int D
       if (lo3[k] < blo || lo3[k] > bhi) return false;
       continue;
     }
-    double ta = (blo - lo3[k]) / ld3[k], tb = (bhi - lo3[k]) / ld3[k];
+    // one reciprocal per axis instead of two divisions: FP64 issues at a few
+    // lanes per clock, so this pass is bound by its FP64 instruction count
+    // (the result differs from the quotient by at most an ulp or two)
+    const double inv = 1.0 / ld3[k];
+    double ta = (blo - lo3[k]) * inv, tb = (bhi - lo3[k]) * inv;
     if (ta > tb) {
       const double x = ta;
       ta = tb;
@@ -1045,7 +1050,14 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
             if (slot < L.fix_capacity) {
               // contenders still in play (lo <= hi_min); none stored = full FP64 retrace
               unsigned long long nc = 0;
-              if (!con.overflow && slot < L.cand_capacity) {
+              if (ids_ok && slot < L.cand_capacity) {
+                // ids certified, only t needs FP64: the winner alone, whatever
+                // the contender list holds
+                L.fix_cand[slot * kContenders] =
+                    make_uint4(st.part1, (uint32_t)(st.vox1 & 0xFFFFFFFFull), (uint32_t)(st.vox1 >> 32),
+                               __float_as_uint(st.lo1));
+                nc = 1;
+              } else if (!con.overflow && slot < L.cand_capacity) {
                 for (int q = 0; q < con.n; ++q) {
                   if (!(con.lo[q] <= st.hi_min)) continue;
                   L.fix_cand[slot * kContenders + nc] =
@@ -1053,6 +1065,10 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
                                  __float_as_uint(con.lo[q]));
                   ++nc;
                 }
+              } else if (slot < L.cand_capacity) {
+                // the list overflowed: the re-trace may stop at hi_min, an
+                // upper bound (rounded up) of the winner's t
+                L.fix_cand[slot * kContenders] = make_uint4(0u, 0u, 0u, __float_as_uint(st.hi_min));
               }
               const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
               L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
@@ -1145,7 +1161,11 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     // no contender list (it overflowed): the warp re-traces the ray, lane q
     // taking parts q, q + 32, ...; each lane keeps the exact minimum over its
     // parts, the warp's best hit so far prunes whole parts, and a warp
-    // reduction gives the overall minimum
+    // reduction gives the overall minimum.  The segment ends at the FP32
+    // pass's certain upper bound of the winner's t where one was stored: the
+    // winner (and every leaf tied with it) starts no later, so no candidate
+    // is lost and the leaves beyond it are never tested in FP64.
+    const float tcap = i < L.cand_capacity ? __uint_as_float(L.fix_cand[i * kContenders].w) : Num<float>::inf();
     RayW r;
     r.ox = o.x;
     r.oy = o.y;
@@ -1154,7 +1174,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     r.dx = d.x;
     r.dy = d.y;
     r.dz = d.z;
-    r.tmax = d.w;
+    r.tmax = fminf(d.w, tcap);
     r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
     r.inv_len = 0.f;
     r.onorm = 0.f;
@@ -1163,7 +1183,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     hs.ex.part = kMissPart;
     hs.ex.vox = kMissVoxel;
     hs.o = o;
-    hs.d = d;
+    hs.d = make_float4(d.x, d.y, d.z, r.tmax);
     uint2 stk_local[kMaxDepth];
     double best = Num<double>::inf();  // the warp's best hit t after each round
     for (int base = 0; base < I.n_parts; base += 32) {
