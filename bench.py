@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--launch", default="", help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER instead of autotuning")
     ap.add_argument("--many-parts-only", action="store_true",
                     help="run only the 1024-part section (cluster level vs scene grid) and print its JSON")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched section (64 uneven scenes in one launch) and print its JSON")
     return ap.parse_args()
 
 
@@ -432,6 +434,25 @@ def many_parts_inputs(pool) -> tuple:
             synthetic.random_rays(1 << 20, np.random.default_rng(SEED_MANY), (-box / 2,) * 3, (box / 2,) * 3))
 
 
+def run_batched_only() -> None:
+    import synthetic
+    import torch
+
+    pool = synthetic.asset_pool(range(6, 12), 4, seed=synthetic.config_seed(2, 1))
+    bat = synthetic.batched_scenes(pool=pool)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1911_06001_gb300 as g
+
+    dev = torch.device("cuda", 0)
+    ctx = g.Context(0)
+    handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    print(json.dumps({"batched": batched_section(g, ctx, bat, handles, dev, reps=5, flush=flush)}))
+    ctx.close()
+
+
 def run_many_parts_only() -> None:
     import synthetic
     import torch
@@ -528,6 +549,9 @@ def main() -> None:
 
     if args.many_parts_only:
         run_many_parts_only()
+        return
+    if args.batched_only:
+        run_batched_only()
         return
 
     # host-side inputs and the CPU baseline come first: no process forks after CUDA is up
