@@ -1110,18 +1110,90 @@ __device__ __forceinline__ void write_fixed(const TraceItem &I, unsigned long lo
   if (I.ray_flags) I.ray_flags[ray] = why | SVO_RAY_FIXED;
 }
 
+// Lexicographic minimum of (t, part, voxel) across each aligned group of 8
+// lanes (every lane of the group returns it).
+__device__ __forceinline__ void group_min8(ExactState &s) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    ExactState x;
+    x.t = __shfl_xor_sync(0xffffffffu, s.t, o);
+    x.part = __shfl_xor_sync(0xffffffffu, s.part, o);
+    x.vox = __shfl_xor_sync(0xffffffffu, s.vox, o);
+    offer(s, x.t, x.part, x.vox);
+  }
+}
+
+// The FP64 pass for a flagged ray without a contender list (the list
+// overflowed), called by the whole warp (i: its list index, e: its entry).
+// The warp re-traces the ray, lane q taking parts q, q + 32, ...; each lane
+// keeps the exact minimum over its parts, the warp's best hit so far prunes
+// whole parts, and a warp reduction gives the overall minimum.  The segment
+// ends at the FP32 pass's certain upper bound of the winner's t where one was
+// stored: the winner (and every leaf tied with it) starts no later, so no
+// candidate is lost and the leaves beyond it are never tested in FP64.
+template <int NI>
+__device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i, unsigned long long e,
+                                 const Tables *tab, unsigned int &err, Counters &cnt) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t why = ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN;
+  const int it = (int)((e >> kRayBits) & 0x7Fu);
+  const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
+  const TraceItem &I = L.items[it];
+  const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
+  const float tcap = i < L.cand_capacity ? __uint_as_float(L.fix_cand[i * kContenders].w) : Num<float>::inf();
+  RayW r;
+  r.ox = o.x;
+  r.oy = o.y;
+  r.oz = o.z;
+  r.tmin = o.w;
+  r.dx = d.x;
+  r.dy = d.y;
+  r.dz = d.z;
+  r.tmax = fminf(d.w, tcap);
+  r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
+  r.inv_len = 0.f;
+  r.onorm = 0.f;
+  HybridState hs;
+  hs.ex.t = Num<double>::inf();
+  hs.ex.part = kMissPart;
+  hs.ex.vox = kMissVoxel;
+  hs.o = o;
+  hs.d = make_float4(d.x, d.y, d.z, r.tmax);
+  uint2 stk_local[kMaxDepth];
+  double best = Num<double>::inf();  // the warp's best hit t after each round
+  for (int base = 0; base < I.n_parts; base += 32) {
+    const int p = base + lane;
+    if (p < I.n_parts) {
+      float tin, tref;
+      if (part_cull(r, I.hot[p], tin, tref) && !(tin > __double2float_ru(fmin(best, hs.ex.t)))) {
+        hs.inv64 = I.inv64 + 12 * p;
+        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs, nullptr,
+                                              err, cnt);
+      }
+    }
+    double bb = hs.ex.t;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bb = fmin(bb, __shfl_xor_sync(0xffffffffu, bb, off));
+    best = bb;
+  }
+  warp_min(hs.ex);
+  if (lane == 0) write_fixed(I, ray, hs.ex, why);
+}
+
 // Re-intersects the rays the FP32 pass flagged, in FP64 and without
-// certification.  One warp per flagged ray:
+// certification:
 //   * with a contender list (the leaves that may still be the closest hit),
-//     lane q intersects contender q with the exact closed-box rule and a warp
-//     reduction keeps the lexicographic minimum of (t, part, voxel);
+//     lane q of the ray's 8-lane group intersects contender q with the exact
+//     closed-box rule and a group reduction keeps the lexicographic minimum
+//     of (t, part, voxel);
 //   * without one (the list overflowed), the warp re-traces the ray, the
 //     parts dealt over the lanes: the FP32 descent with inflated boxes, every
 //     leaf reached decided in FP64.
 // GB300 issues FP64 at 2 lanes per clock per SM, so spreading a ray's
 // contenders over lanes (instead of one lane looping over them) cuts the
-// pass's latency by the contender count.  List entries are dealt round-robin
-// over the warps so that a short list still spreads over the whole GPU.
+// pass's latency by the contender count.  Groups of four list entries are
+// dealt round-robin over the warps so that a short list still spreads over
+// the whole GPU.
 template <int NI>
 __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLaunchT<NI> L) {
   // the rare re-traces read the order tables from global memory (L1/L2), so
@@ -1133,76 +1205,47 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   const int lane = threadIdx.x & 31;
   const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
   const unsigned long long warp = blockIdx.x + (unsigned long long)gridDim.x * (threadIdx.x >> 5);
-  for (unsigned long long i = warp; i < n; i += n_warps) {
-    const unsigned long long e = L.fix_list[i];
+  // Four list entries per warp, one group of 8 lanes each (at most 8
+  // contenders per entry): FP64 issues at a few lanes per clock and a warp
+  // instruction holds the pipe whatever its active lanes, so packing entries
+  // cuts the pipe time per entry.  Entries without contenders are re-traced
+  // afterwards by the whole warp, one at a time.
+  static_assert(kContenders == 8, "8-lane groups");
+  const int sub = lane >> 3, sl = lane & 7;
+  for (unsigned long long i0 = 4 * warp; i0 < n; i0 += 4 * n_warps) {
+    const unsigned long long i = i0 + (unsigned long long)sub;
+    const bool have = i < n;
+    const unsigned long long e = have ? L.fix_list[i] : 0ull;
     const int nc = (int)(e >> 48);
-    const uint32_t why = ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN;
-    const int it = (int)((e >> kRayBits) & 0x7Fu);
-    const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
-    const TraceItem &I = L.items[it];
-    const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
-    if (nc > 0) {
-      // the FP32 pass narrowed the ray to nc contender leaves: one per lane
+    {
+      // the FP32 pass narrowed the ray to nc contender leaves: one per lane of the group
       ExactState st;
       st.t = Num<double>::inf();
       st.part = kMissPart;
       st.vox = kMissVoxel;
-      if (lane < nc && lane < kContenders) {
-        const uint4 cv = L.fix_cand[i * kContenders + lane];
+      const int it = (int)((e >> kRayBits) & 0x7Fu);
+      const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
+      if (have && sl < nc) {
+        const TraceItem &I = L.items[it];
+        const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
+        const uint4 cv = L.fix_cand[i * kContenders + sl];
         const uint32_t p = cv.x;
         const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
         double tq;
         if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
       }
-      warp_min(st);
-      if (lane == 0) write_fixed(I, ray, st, why);
-      continue;
+      group_min8(st);
+      if (have && nc > 0 && sl == 0)
+        write_fixed(L.items[it], ray, st, ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN);
     }
-    // no contender list (it overflowed): the warp re-traces the ray, lane q
-    // taking parts q, q + 32, ...; each lane keeps the exact minimum over its
-    // parts, the warp's best hit so far prunes whole parts, and a warp
-    // reduction gives the overall minimum.  The segment ends at the FP32
-    // pass's certain upper bound of the winner's t where one was stored: the
-    // winner (and every leaf tied with it) starts no later, so no candidate
-    // is lost and the leaves beyond it are never tested in FP64.
-    const float tcap = i < L.cand_capacity ? __uint_as_float(L.fix_cand[i * kContenders].w) : Num<float>::inf();
-    RayW r;
-    r.ox = o.x;
-    r.oy = o.y;
-    r.oz = o.z;
-    r.tmin = o.w;
-    r.dx = d.x;
-    r.dy = d.y;
-    r.dz = d.z;
-    r.tmax = fminf(d.w, tcap);
-    r.inv_dd = 1.0f / (d.x * d.x + d.y * d.y + d.z * d.z);
-    r.inv_len = 0.f;
-    r.onorm = 0.f;
-    HybridState hs;
-    hs.ex.t = Num<double>::inf();
-    hs.ex.part = kMissPart;
-    hs.ex.vox = kMissVoxel;
-    hs.o = o;
-    hs.d = make_float4(d.x, d.y, d.z, r.tmax);
-    uint2 stk_local[kMaxDepth];
-    double best = Num<double>::inf();  // the warp's best hit t after each round
-    for (int base = 0; base < I.n_parts; base += 32) {
-      const int p = base + lane;
-      if (p < I.n_parts) {
-        float tin, tref;
-        if (part_cull(r, I.hot[p], tin, tref) && !(tin > __double2float_ru(fmin(best, hs.ex.t)))) {
-          hs.inv64 = I.inv64 + 12 * p;
-          trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs,
-                                                nullptr, err, cnt);
-        }
-      }
-      double b = hs.ex.t;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
-      best = b;
+    unsigned int pending = __ballot_sync(0xffffffffu, have && nc == 0 && sl == 0);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1u;
+      const unsigned long long ie = i0 + (unsigned long long)(src >> 3);
+      const unsigned long long ee = __shfl_sync(0xffffffffu, e, src);
+      overflow_retrace(L, ie, ee, tab, err, cnt);
     }
-    warp_min(hs.ex);
-    if (lane == 0) write_fixed(I, ray, hs.ex, why);
   }
   // count fixed rays once per launch
   if (L.stats && blockIdx.x == 0 && threadIdx.x == 0 && (L.flags & SVO_TRACE_STATS)) atomicAdd(&L.stats->fixed, n);
