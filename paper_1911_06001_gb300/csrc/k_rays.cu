@@ -125,7 +125,7 @@ __global__ void k_order_keys(const float4 *__restrict__ rays, unsigned long long
 }
 
 // Exclusive scan of kBins counters by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_order_scan(unsigned int *__restrict__ hist) {
+__device__ __forceinline__ void scan_bins(unsigned int *__restrict__ hist) {
   constexpr int kPer = kBins / 1024;
   __shared__ unsigned int part[1024];
   unsigned int local[kPer];
@@ -147,6 +147,90 @@ __global__ void __launch_bounds__(1024) k_order_scan(unsigned int *__restrict__ 
   const unsigned int prefix = part[threadIdx.x] - sum;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) hist[base + k] = prefix + local[k];
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan(unsigned int *__restrict__ hist) { scan_bins(hist); }
+
+// The same counting sort for every item of a batch in one set of launches:
+// each item keeps its own histogram, keys and permutation; warps run over the
+// concatenation of the items' rays, and the warp-aggregated atomics group
+// lanes by (item, key).
+struct OrderBatch {
+  OrderItem items[kMaxBatchItems];
+  unsigned long long begin[kMaxBatchItems + 1];  // first ray of each item in the concatenation
+  int n_items;
+  int mode;
+};
+
+__device__ __forceinline__ int order_item_of(const OrderBatch &B, unsigned long long g) {
+  int lo = 0, hi = B.n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.begin[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_order_zero_batch(const __grid_constant__ OrderBatch B) {
+  unsigned int *h = B.items[blockIdx.x].hist;
+  for (int k = threadIdx.x; k < kBins; k += blockDim.x) h[k] = 0u;
+}
+
+__global__ void k_order_keys_batch(const __grid_constant__ OrderBatch B) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = B.begin[B.n_items];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w < total;
+       w += stride) {
+    const unsigned long long g = w + lane;
+    const bool valid = g < total;
+    uint32_t tag = 0xFFFFFFFFu, k = 0;  // out of range: never counted
+    int it = 0;
+    if (valid) {
+      it = order_item_of(B, g);
+      const OrderItem &I = B.items[it];
+      const unsigned long long i = g - B.begin[it];
+      const float4 o = __ldcs(&I.rays[2 * i]), d = __ldcs(&I.rays[2 * i + 1]);
+      k = ray_key(o, d, B.mode, *I.bound) & (kBins - 1);
+      I.keys[i] = (uint16_t)k;
+      tag = ((uint32_t)it << 16) | k;
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, tag);
+    if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&B.items[it].hist[k], (unsigned int)__popc(peers));
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan_batch(const __grid_constant__ OrderBatch B) {
+  scan_bins(B.items[blockIdx.x].hist);
+}
+
+__global__ void k_order_scatter_batch(const __grid_constant__ OrderBatch B) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = B.begin[B.n_items];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane; w < total;
+       w += stride) {
+    const unsigned long long g = w + lane;
+    const bool valid = g < total;
+    uint32_t tag = 0xFFFFFFFFu, k = 0;
+    int it = 0;
+    unsigned long long i = 0;
+    if (valid) {
+      it = order_item_of(B, g);
+      i = g - B.begin[it];
+      k = (uint32_t)B.items[it].keys[i];
+      tag = ((uint32_t)it << 16) | k;
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, tag);
+    const int leader = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&B.items[it].hist[k], (unsigned int)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) B.items[it].perm[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
 }
 
 __global__ void k_order_scatter(const uint16_t *__restrict__ keys, unsigned long long n,
@@ -179,6 +263,40 @@ cudaError_t launch_raygen(const RaygenArgs &a, float *rays, int n_sm, cudaStream
 
 size_t order_scratch_bytes(unsigned long long n) {
   return (size_t)kBins * sizeof(unsigned int) + ((n * sizeof(uint16_t) + 255) & ~255ull) + n * sizeof(uint32_t);
+}
+
+OrderItem order_item(const float *rays, unsigned long long n, const float4 *bound, void *scratch) {
+  unsigned char *p = static_cast<unsigned char *>(scratch);
+  OrderItem it;
+  it.rays = reinterpret_cast<const float4 *>(rays);
+  it.n = n;
+  it.bound = bound;
+  it.hist = reinterpret_cast<unsigned int *>(p);
+  it.keys = reinterpret_cast<uint16_t *>(p + kBins * sizeof(unsigned int));
+  it.perm = reinterpret_cast<uint32_t *>(p + kBins * sizeof(unsigned int) + ((n * sizeof(uint16_t) + 255) & ~255ull));
+  return it;
+}
+
+cudaError_t launch_order_batch(const OrderItem *items, int n_items, int mode, int n_sm, cudaStream_t stream) {
+  if (n_items <= 0 || n_items > kMaxBatchItems) return cudaErrorInvalidValue;
+  OrderBatch *B = new OrderBatch();  // large: off the host stack
+  B->n_items = n_items;
+  B->mode = mode;
+  B->begin[0] = 0;
+  for (int i = 0; i < n_items; ++i) {
+    B->items[i] = items[i];
+    B->begin[i + 1] = B->begin[i] + items[i].n;
+  }
+  const unsigned long long total = B->begin[n_items];
+  unsigned long long blocks = (total + 255) / 256;
+  if (blocks > (unsigned long long)n_sm * 8) blocks = (unsigned long long)n_sm * 8;
+  if (blocks == 0) blocks = 1;
+  k_order_zero_batch<<<(unsigned int)n_items, 256, 0, stream>>>(*B);
+  k_order_keys_batch<<<(unsigned int)blocks, 256, 0, stream>>>(*B);
+  k_order_scan_batch<<<(unsigned int)n_items, 1024, 0, stream>>>(*B);
+  k_order_scatter_batch<<<(unsigned int)blocks, 256, 0, stream>>>(*B);
+  delete B;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_order(const float *rays, unsigned long long n, int mode, const float4 *bound, void *scratch,

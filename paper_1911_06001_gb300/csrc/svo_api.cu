@@ -222,12 +222,21 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
       slot->order_cap = need;
     }
     size_t off = 0;
-    for (int i = 0; i < L.n_items; ++i) {
+    if (L.n_items == 1) {
       uint32_t *perm = nullptr;
-      CK(launch_order(reinterpret_cast<const float *>(L.items[i].rays), L.items[i].n, order_mode, bounds[i],
-                      static_cast<char *>(slot->d_order) + off, &perm, ctx->n_sm, st));
-      L.items[i].perm = perm;
-      off += (order_scratch_bytes(L.items[i].n) + 255) & ~size_t(255);
+      CK(launch_order(reinterpret_cast<const float *>(L.items[0].rays), L.items[0].n, order_mode, bounds[0],
+                      slot->d_order, &perm, ctx->n_sm, st));
+      L.items[0].perm = perm;
+    } else {
+      // every item sorted by the same four launches
+      std::vector<OrderItem> oi((size_t)L.n_items);
+      for (int i = 0; i < L.n_items; ++i) {
+        oi[i] = order_item(reinterpret_cast<const float *>(L.items[i].rays), L.items[i].n, bounds[i],
+                           static_cast<char *>(slot->d_order) + off);
+        L.items[i].perm = oi[i].perm;
+        off += (order_scratch_bytes(L.items[i].n) + 255) & ~size_t(255);
+      }
+      CK(launch_order_batch(oi.data(), L.n_items, order_mode, ctx->n_sm, st));
     }
   }
   L.n_tiles = layout_tiles(L.items, L.n_items, ctx->rays_per_lane);

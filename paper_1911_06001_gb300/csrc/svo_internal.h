@@ -177,6 +177,19 @@ size_t order_scratch_bytes(unsigned long long n);
 // mode 1: by direction, 2: by origin cell then direction; *perm_out points into scratch.
 cudaError_t launch_order(const float *rays, unsigned long long n, int mode, const float4 *bound, void *scratch,
                          uint32_t **perm_out, int n_sm, cudaStream_t stream);
+// One item of a batched ordering: its rays, its scene bound and its part of
+// the scratch (order_scratch_bytes(n) bytes, carved by order_item).
+struct OrderItem {
+  const float4 *rays;
+  unsigned long long n;
+  const float4 *bound;
+  unsigned int *hist;
+  uint16_t *keys;
+  uint32_t *perm;  // the item's permutation once the launches have run
+};
+OrderItem order_item(const float *rays, unsigned long long n, const float4 *bound, void *scratch);
+// The orderings of up to kMaxBatchItems items in four launches in all.
+cudaError_t launch_order_batch(const OrderItem *items, int n_items, int mode, int n_sm, cudaStream_t stream);
 
 struct RefitArgs {
   int32_t n_parts;

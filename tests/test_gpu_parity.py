@@ -537,3 +537,35 @@ def test_animation_never_writes_the_svos(ctx):
     after = [ctx.read_asset(h) for h in gs.handles]
     for (n0, c0), (n1, c1) in zip(before, after):
         assert n0.tobytes() == n1.tobytes() and c0.tobytes() == c1.tobytes()
+
+
+def test_batched_ray_ordering_does_not_change_results(ctx, pr1):
+    """Ray ordering across a batch (all items sorted by the same launches)
+    leaves every item's hits and flags at its rays' own indices, equal to the
+    unordered batch."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    scene, gs, so = pr1
+    fig = synthetic.articulated_figure(depth=6)
+    ga = GpuScene(ctx, fig.scene)
+    rng = np.random.default_rng(31)
+    sets = [(gs, synthetic.pr1_rays(scene)), (ga, fig.rays(200, 120)), (gs, synthetic.random_rays(5000, rng, (-3,) * 3,
+                                                                                                   (3,) * 3)),
+            (ga, np.zeros((0, 8), np.float32)), (ga, synthetic.random_rays(777, rng, (-2,) * 3, (2,) * 3))]
+    outs = {}
+    for order in (0, g.TRACE_ORDER_DIR, g.TRACE_ORDER_ORIGIN):
+        items, res = [], []
+        for sc, r in sets:
+            rt = torch.from_numpy(np.ascontiguousarray(r, dtype=np.float32)).cuda()
+            ht = torch.zeros((r.shape[0], 2), dtype=torch.int64, device="cuda")
+            ft = torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")
+            items.append((sc.sc, rt, ht, ft))
+            res.append((ht, ft))
+        ctx.trace_batch(items, flags=7 | order)
+        torch.cuda.synchronize()
+        outs[order] = [(h.cpu().numpy(), f.cpu().numpy()) for h, f in res]
+    for order in (g.TRACE_ORDER_DIR, g.TRACE_ORDER_ORIGIN):
+        for (h0, f0), (h1, f1) in zip(outs[0], outs[order]):
+            assert np.array_equal(h0, h1) and np.array_equal(f0, f1)
