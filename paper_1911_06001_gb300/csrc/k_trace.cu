@@ -1183,7 +1183,7 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
 // Re-intersects the rays the FP32 pass flagged, in FP64 and without
 // certification:
 //   * with a contender list (the leaves that may still be the closest hit),
-//     lane q of the ray's lane group intersects contender q with the exact
+//     lane q of the ray's 8-lane group intersects contender q with the exact
 //     closed-box rule and a group reduction keeps the lexicographic minimum
 //     of (t, part, voxel);
 //   * without one (the list overflowed), the warp re-traces the ray, the
@@ -1191,9 +1191,9 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
 //     leaf reached decided in FP64.
 // GB300 issues FP64 at 2 lanes per clock per SM, so spreading a ray's
 // contenders over lanes (instead of one lane looping over them) cuts the
-// pass's latency by the contender count.  Runs of 32 list entries are dealt
-// round-robin over the warps so that a short list still spreads over the
-// whole GPU.
+// pass's latency by the contender count.  Groups of four list entries are
+// dealt round-robin over the warps so that a short list still spreads over
+// the whole GPU.
 template <int NI>
 __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLaunchT<NI> L) {
   // the rare re-traces read the order tables from global memory (L1/L2), so
@@ -1205,57 +1205,27 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   const int lane = threadIdx.x & 31;
   const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
   const unsigned long long warp = blockIdx.x + (unsigned long long)gridDim.x * (threadIdx.x >> 5);
-  // Each warp loads 32 list entries at a time.  FP64 issues at a few lanes
-  // per clock and a warp instruction holds the pipe whatever its active
-  // lanes, so the entries share warp instructions: those with one contender
-  // leaf (every t refinement among them) one lane each, all at once; those
-  // with 2-8 contenders four at a time, one group of 8 lanes each; those
-  // without a contender list (it overflowed) the whole warp, one at a time.
+  // Four list entries per warp, one group of 8 lanes each (at most 8
+  // contenders per entry): FP64 issues at a few lanes per clock and a warp
+  // instruction holds the pipe whatever its active lanes, so packing entries
+  // cuts the pipe time per entry.  Entries without contenders are re-traced
+  // afterwards by the whole warp, one at a time.
   static_assert(kContenders == 8, "8-lane groups");
   const int sub = lane >> 3, sl = lane & 7;
-  for (unsigned long long i0 = 32 * warp; i0 < n; i0 += 32 * n_warps) {
-    const unsigned long long my_i = i0 + (unsigned long long)lane;
-    const bool have = my_i < n;
-    const unsigned long long my_e = have ? L.fix_list[my_i] : 0ull;
-    const int my_nc = (int)(my_e >> 48);
-    // one contender: this lane alone
-    if (have && my_nc == 1) {
-      ExactState st;
-      st.t = Num<double>::inf();
-      st.part = kMissPart;
-      st.vox = kMissVoxel;
-      const int it = (int)((my_e >> kRayBits) & 0x7Fu);
-      const unsigned long long ray = my_e & ((1ull << kRayBits) - 1ull);
-      const TraceItem &I = L.items[it];
-      const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
-      const uint4 cv = L.fix_cand[my_i * kContenders];
-      const uint32_t p = cv.x;
-      const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
-      double tq;
-      if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
-      write_fixed(I, ray, st, ((my_e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN);
-    }
-    // 2-8 contenders: four entries at a time, one 8-lane group each
-    unsigned int multi = __ballot_sync(0xffffffffu, have && my_nc > 1);
-    while (multi) {
-      int src = -1;  // this group's entry: the sub-th remaining one
-      unsigned int m = multi;
-      for (int q = 0; q < 4 && m; ++q) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1u;
-        if (q == sub) src = b;
-      }
-      multi = m;
-      const unsigned long long e = __shfl_sync(0xffffffffu, my_e, src < 0 ? 0 : src);
-      const unsigned long long i = i0 + (unsigned long long)(src < 0 ? 0 : src);
-      const int nc = src < 0 ? 0 : (int)(e >> 48);
+  for (unsigned long long i0 = 4 * warp; i0 < n; i0 += 4 * n_warps) {
+    const unsigned long long i = i0 + (unsigned long long)sub;
+    const bool have = i < n;
+    const unsigned long long e = have ? L.fix_list[i] : 0ull;
+    const int nc = (int)(e >> 48);
+    {
+      // the FP32 pass narrowed the ray to nc contender leaves: one per lane of the group
       ExactState st;
       st.t = Num<double>::inf();
       st.part = kMissPart;
       st.vox = kMissVoxel;
       const int it = (int)((e >> kRayBits) & 0x7Fu);
       const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
-      if (sl < nc) {
+      if (have && sl < nc) {
         const TraceItem &I = L.items[it];
         const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
         const uint4 cv = L.fix_cand[i * kContenders + sl];
@@ -1265,15 +1235,16 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
         if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
       }
       group_min8(st);
-      if (nc > 0 && sl == 0)
+      if (have && nc > 0 && sl == 0)
         write_fixed(L.items[it], ray, st, ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN);
     }
-    // no contender list: the whole warp re-traces, one entry at a time
-    unsigned int pending = __ballot_sync(0xffffffffu, have && my_nc == 0);
+    unsigned int pending = __ballot_sync(0xffffffffu, have && nc == 0 && sl == 0);
     while (pending) {
       const int src = __ffs(pending) - 1;
       pending &= pending - 1u;
-      overflow_retrace(L, i0 + (unsigned long long)src, __shfl_sync(0xffffffffu, my_e, src), tab, err, cnt);
+      const unsigned long long ie = i0 + (unsigned long long)(src >> 3);
+      const unsigned long long ee = __shfl_sync(0xffffffffu, e, src);
+      overflow_retrace(L, ie, ee, tab, err, cnt);
     }
   }
   // count fixed rays once per launch
