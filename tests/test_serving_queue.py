@@ -81,3 +81,4 @@ def test_expiry_and_cancellation():
     q2 = RequestQueue(slot_rays=10, budget_bytes=100, bytes_per_ray=1)
     q2.submit(_t(5, arrival=-1e9))
     assert q2.expire(now=0.0) == [] and len(q2) == 1
+
