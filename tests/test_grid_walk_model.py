@@ -13,7 +13,7 @@ every case below.  The 2^-10-cell widening matters only for rays within
 rounding distance of a cell edge, which random inputs do not reach (these
 cases pass without it, because the directed rounding of the sphere boxes
 already lists a box that touches a plane on both sides).  Its margin rests
-on the error bound stated with the walk.
+on the error bound stated with the walk."""
 
 from __future__ import annotations
 
