@@ -1,5 +1,6 @@
-"""The autotuner's host-side mapping from a tuned configuration to trace
-flags (no GPU)."""
+"""Host-side logic (no GPU): the autotuner's mapping from a tuned
+configuration to trace flags, and the bench's lookup of measured DRAM
+traffic."""
 
 from __future__ import annotations
 
