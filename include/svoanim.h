@@ -57,6 +57,13 @@ typedef int32_t svo_status;
 #define SVO_ERR_LIMIT (-9)    /* a size exceeds a documented library limit */
 #define SVO_ERR_DEVICE (-10)  /* a kernel reported an internal check failure */
 
+/* Rays (Eq. 1).  A ray must have a direction: the largest magnitude of its
+ * direction's components must lie in [2^-60, 2^60], its origin and direction
+ * must be finite and neither tmin nor tmax may be NaN.  Any other input is
+ * not a ray and is reported as a miss (not an error). */
+#define SVO_RAY_DIR_MIN 0x1p-60
+#define SVO_RAY_DIR_MAX 0x1p60
+
 /* Limits. */
 #define SVO_MAX_DEPTH 16        /* octree depth of an asset (leaf level) */
 #define SVO_MAX_PARTS 1024      /* parts per scene */
@@ -94,7 +101,15 @@ typedef int32_t svo_status;
 /* per-ray flags written when ray_flags != NULL */
 #define SVO_RAY_UNCERTAIN 1u /* FP32 could not certify which leaf is hit first (near tie / grazing) */
 #define SVO_RAY_FIXED 2u     /* the hit was recomputed in FP64 */
-#define SVO_RAY_T_REFINED 4u /* the ids were certified but t was recomputed in FP64 for precision */
+#define SVO_RAY_T_REFINED 4u /* the ids were certified but the FP32 t interval was wider than 2^-17 of
+                                max(t, leaf diagonal / |d|): t is recomputed in FP64 (FP64_FIX), else
+                                bits 8-15 hold a certified error bound (SVO_RAY_T_BOUND_EXP) */
+/* For a ray flagged SVO_RAY_T_REFINED and not SVO_RAY_FIXED: with e = SVO_RAY_T_BOUND_EXP(flags),
+ * |t - t_exact| <= 2^e * max(t_exact, h / |d|) * (1 + 2^-18), h being the world length of the hit
+ * part's leaf diagonal (t_exact: the closed-box entry in exact arithmetic; the bound comes from
+ * the FP32 pass's rounding-error analysis; the last factor covers the FP32 evaluation of h / |d|).
+ * A biased value of 255 means no finite bound. */
+#define SVO_RAY_T_BOUND_EXP(flags) ((int32_t)(((flags) >> 8) & 0xFFu) - 128)
 #define SVO_RAY_REUSED 8u    /* SVO_TRACE_REUSE kept the previous hit (no descent) */
 
 typedef struct svo_ctx svo_ctx;
@@ -310,8 +325,10 @@ svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n,
  * frame loop with a hard deadline, where cudaMalloc may synchronise the
  * device, or a host application whose own allocator owns all device memory.
  * (The paper has no counterpart; this is a deployment variant.)  Same
- * arguments and results as trace_rays without `stats`; SVO_TRACE_STATS and
- * SVO_TRACE_DEFER_FIX are rejected (SVO_ERR_ARG).  It never calls cudaMalloc
+ * arguments and results as trace_rays without `stats`; SVO_TRACE_STATS,
+ * SVO_TRACE_DEFER_FIX and the ray-order flags SVO_TRACE_ORDER_DIR /
+ * SVO_TRACE_ORDER_ORIGIN (which need per-ray scratch) are rejected
+ * (SVO_ERR_ARG).  It never calls cudaMalloc
  * or cudaFree: its scratch (about 6.3 MB) is a static device array inside the
  * library that every GPU loading the library holds until the process exits.
  * n above SVO_NOALLOC_MAX_RAYS returns SVO_ERR_LIMIT.  The first call on a
@@ -319,7 +336,8 @@ svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n,
  * that first call before any stream capture.  All calls share the array: the
  * counters are cleared on `stream` at every call, and two calls whose work
  * overlaps on the GPU (other streams or host threads) race -- serialise
- * them. */
+ * them.  The looked-up address is kept for the life of the process: do not
+ * reset the device (cudaDeviceReset) while the library is loaded. */
 svo_status trace_rays_noalloc(svo_scene *scene, const float *rays, uint64_t n, svo_hit *hits,
                               uint32_t *ray_flags, uint32_t flags, void *stream);
 

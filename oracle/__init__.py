@@ -49,6 +49,8 @@ def lib():
         L.oracle_trace.argtypes = [C.c_int, C.POINTER(C.c_void_p), dp, C.c_int64, dp, dp, up32, up64, dp, C.c_int,
                                    C.c_int]
         L.oracle_trace.restype = C.c_int
+        L.oracle_ray_valid.argtypes = [dp]
+        L.oracle_ray_valid.restype = C.c_int
         _lib = L
     return _lib
 
@@ -158,6 +160,14 @@ def trace(part_assets, inv, rays, mode: int = 1, threads: int | None = None) -> 
     return {"t": out_t, "part": out_p, "voxel": out_v, "second": out_s}
 
 
+def ray_valid(rays) -> np.ndarray:
+    """Per ray, whether it is a ray the method traces (the oracle's rule:
+    finite origin and direction, no NaN bound, largest direction component
+    magnitude in [2^-60, 2^60]); anything else is reported as a miss."""
+    rays = np.ascontiguousarray(np.asarray(rays).astype(np.float64)).reshape(-1, 8)
+    return np.array([bool(lib().oracle_ray_valid(np.ascontiguousarray(r))) for r in rays], dtype=bool)
+
+
 def trs_to_local(rts) -> np.ndarray:
     """Sec. III-B poses (rotation R, translation t, octree dimensions s; rows
     ``R (9, row-major) | t | s``) as local 3x4 affines: x_parent = R (s * x) + t."""
@@ -183,6 +193,7 @@ def trace_octree_dims(part_leaf_ids, part_depth, rts, rays) -> dict:
     best_t = np.full(n, np.inf)
     best_p = np.full(n, MISS_PART, dtype=np.uint32)
     best_v = np.full(n, MISS_VOXEL, dtype=np.uint64)
+    valid = ray_valid(rays)
     for p, row in enumerate(rts):
         R, tv, dims = row[:9].reshape(3, 3), row[9:12], row[12:15]
         ids = np.asarray(part_leaf_ids[p], dtype=np.uint64)
@@ -194,6 +205,8 @@ def trace_octree_dims(part_leaf_ids, part_depth, rts, rays) -> dict:
         lo = cell * dims / 2.0 ** D
         hi = (cell + 1.0) * dims / 2.0 ** D
         for r in range(n):
+            if not valid[r]:
+                continue
             o = R.T @ (rays[r, 0:3] - tv)
             d = R.T @ rays[r, 4:7]
             a = np.full(ids.size, rays[r, 3])

@@ -405,11 +405,30 @@ typedef struct {
   atomic_llong next;
 } trace_job;
 
+/* Which inputs are rays (Eq. 1: an origin, a direction, t in [tmin, tmax]).
+ * The paper's rays always have a direction; this reading makes it a rule:
+ * the largest direction component magnitude must lie in [2^-60, 2^60] (the
+ * zero vector has none, and the bounds keep |d|^2 a normal FP32 number for
+ * every such direction), origin and direction must be finite, and neither
+ * bound may be NaN.  Anything else meets nothing and is reported as a miss.
+ * Every test is an exact comparison, so any implementation applies it alike. */
+static int ray_valid(const double *ray) {
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(ray[i]) || !isfinite(ray[4 + i])) return 0;
+  if (isnan(ray[3]) || isnan(ray[7])) return 0;
+  double m = fabs(ray[4]);
+  if (fabs(ray[5]) > m) m = fabs(ray[5]);
+  if (fabs(ray[6]) > m) m = fabs(ray[6]);
+  return m >= ldexp(1.0, -60) && m <= ldexp(1.0, 60);
+}
+
+int oracle_ray_valid(const double *ray8) { return ray_valid(ray8); }
+
 static void trace_one(const trace_job *j, int64_t r) {
   const double *ray = j->rays + 8 * r;
   best_hit b;
   best_init(&b);
-  for (int p = 0; p < j->n_parts; ++p) {
+  for (int p = 0; p < j->n_parts && ray_valid(ray); ++p) {
     const double *m = j->inv + 12 * p;
     double o[3], d[3];
     for (int i = 0; i < 3; ++i) {

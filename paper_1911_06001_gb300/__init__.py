@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     TRACE_SORT,
     TRACE_STATS,
     SvoError,
+    ray_t_bound_exp,
     trace_image,
 )
 

@@ -37,6 +37,14 @@ def trace_image(width: int) -> int:
 RAY_UNCERTAIN = 1
 RAY_FIXED = 2
 RAY_T_REFINED = 4
+
+
+def ray_t_bound_exp(flags):
+    """Certified error exponent of unfixed T_REFINED rays (SVO_RAY_T_BOUND_EXP):
+    |t - t_exact| <= 2^e max(t_exact, leaf diagonal / |d|); 127 = unbounded."""
+    import numpy as np
+
+    return ((np.asarray(flags).astype(np.uint32) >> np.uint32(8)) & np.uint32(0xFF)).astype(np.int32) - 128
 RAY_REUSED = 8
 
 MAX_DEPTH = 16

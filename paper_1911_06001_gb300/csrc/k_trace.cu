@@ -34,7 +34,10 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "svo_internal.h"
 
@@ -979,8 +982,13 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
         r.dz = d.z;
         r.tmax = d.w;
         const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
+        // a ray needs a direction (Eq. 1): its largest component magnitude
+        // must lie in [2^-60, 2^60] (so |d|^2 is a normal FP32 number), and
+        // origin, direction and bounds must be numbers; anything else is a
+        // miss.  Exact comparisons: the rule does not depend on rounding.
+        const float dm = fmaxf(fmaxf(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
         const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
-                            isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dd > 0.f && isfinite(dd);
+                            isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dm >= 0x1p-60f && dm <= 0x1p60f;
         r.inv_dd = __frcp_rn(dd);  // the correctly rounded 1 / dd
         r.inv_len = rsqrtf(dd);
         r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
@@ -1003,6 +1011,7 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
                                         cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr, sMbox,
                                         L.mbox_words);
       bool flagged = false, ids_ok = true;
+      uint32_t tbound = 0;  // T_REFINED: the certified error exponent, biased (flag bits 8-15)
       if (in_range && reused) {
         if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
         if (STATS) ++cnt.reused;
@@ -1018,6 +1027,14 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
           const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
           ids_ok = w_ok && o_ok;
           flagged = !(ids_ok && t_ok);
+          if (ids_ok && !t_ok && I.ray_flags) {
+            // the written t and the exact one both lie in [lo1, hi1]: their
+            // distance is at most 2^e scale with e = ceil(log2((hi1 - lo1) /
+            // scale)), both operations rounded up
+            const uint32_t bits = __float_as_uint(__fdiv_ru(__fsub_ru(st.hi1, st.lo1), scale));
+            const int e = (int)(bits >> 23) - 127 + ((bits & 0x7FFFFFu) != 0u ? 1 : 0);
+            tbound = (uint32_t)min(max(e + 128, 1), 255);
+          }
           if (STATS) {
             cnt.f_winner += w_ok ? 0u : 1u;
             cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
@@ -1034,7 +1051,8 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
         hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
         hv.w = (uint32_t)(vox >> 32);
         __stcs(&I.hits[ray], hv);
-        if (I.ray_flags) I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? SVO_RAY_T_REFINED : 0u);
+        if (I.ray_flags)
+          I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? (SVO_RAY_T_REFINED | (tbound << 8)) : 0u);
         if (STATS && !ids_ok) ++n_flag;
       }
       // compact flagged rays for the FP64 pass (one atomic per warp)
@@ -1257,6 +1275,54 @@ size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, in
          clusters * sizeof(Cluster) + parts * sizeof(int32_t) + (size_t)mbox_words * block * sizeof(uint32_t);
 }
 
+// Resident blocks per SM of a trace kernel at a dynamic shared-memory size.
+// The attribute that admits the size and the occupancy are host calls of a
+// few microseconds each, so they are made once per (device, kernel, size); the
+// attribute only ever grows, so a size admitted once stays admitted.
+struct OccEntry {
+  const void *fn;
+  int dev;
+  size_t smem;
+  int per_sm;
+};
+struct AttrEntry {
+  const void *fn;
+  int dev;
+  size_t smem_max;
+};
+std::mutex g_occ_mu;
+std::vector<OccEntry> g_occ;
+std::vector<AttrEntry> g_attr;
+
+template <typename K>
+cudaError_t blocks_per_sm(K kern, int block, size_t smem, int &per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const void *fn = reinterpret_cast<const void *>(kern);
+  std::lock_guard<std::mutex> g(g_occ_mu);
+  for (const OccEntry &x : g_occ)
+    if (x.fn == fn && x.dev == dev && x.smem == smem) {
+      per_sm = x.per_sm;
+      return cudaSuccess;
+    }
+  AttrEntry *a = nullptr;
+  for (AttrEntry &x : g_attr)
+    if (x.fn == fn && x.dev == dev) a = &x;
+  if (!a || a->smem_max < smem) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a)
+      a->smem_max = smem;
+    else
+      g_attr.push_back({fn, dev, smem});
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+  if (e != cudaSuccess) return e;
+  g_occ.push_back({fn, dev, smem, per_sm});
+  return cudaSuccess;
+}
+
 template <int NI, int BLOCK>
 cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t stream) {
   const bool stats = (L.flags & SVO_TRACE_STATS) && L.stats;
@@ -1272,10 +1338,8 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
   auto kern = walk ? (stats ? k_trace<NI, true, BLOCK, false, true> : k_trace<NI, false, BLOCK, false, true>)
               : stats ? (reuse ? k_trace<NI, true, BLOCK, true, false> : k_trace<NI, true, BLOCK, false, false>)
                       : (reuse ? k_trace<NI, false, BLOCK, true, false> : k_trace<NI, false, BLOCK, false, false>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
+  const cudaError_t e = blocks_per_sm(kern, BLOCK, smem, per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   // one warp per tile: no more blocks than the tiles can keep busy
@@ -1334,17 +1398,24 @@ cudaError_t init_trace_tables(cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// The kernel parameter block of a batch (about 16 KB): one per host thread,
+// allocated on its first batch, so it stays off the caller's stack and off
+// the heap of later calls.
+TraceLaunchT<kMaxBatchItems> &batch_params() {
+  thread_local std::unique_ptr<TraceLaunchT<kMaxBatchItems>> p;
+  if (!p) p.reset(new TraceLaunchT<kMaxBatchItems>());
+  return *p;
+}
+
 cudaError_t launch_trace(const TraceLaunch &L, int n_sm, cudaStream_t stream) {
   if (L.n_items <= 1) {
     TraceLaunchT<1> l1;
     fill_launch(L, l1);
     return launch_trace_t(l1, n_sm, stream);
   }
-  TraceLaunchT<kMaxBatchItems> *p = new TraceLaunchT<kMaxBatchItems>();  // large: off the host stack
-  fill_launch(L, *p);
-  cudaError_t e = launch_trace_t(*p, n_sm, stream);
-  delete p;
-  return e;
+  TraceLaunchT<kMaxBatchItems> &p = batch_params();
+  fill_launch(L, p);
+  return launch_trace_t(p, n_sm, stream);
 }
 
 cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream) {
@@ -1353,11 +1424,9 @@ cudaError_t launch_fix(const TraceLaunch &L, int n_sm, cudaStream_t stream) {
     fill_launch(L, l1);
     return launch_fix_t(l1, n_sm, stream);
   }
-  TraceLaunchT<kMaxBatchItems> *p = new TraceLaunchT<kMaxBatchItems>();
-  fill_launch(L, *p);
-  cudaError_t e = launch_fix_t(*p, n_sm, stream);
-  delete p;
-  return e;
+  TraceLaunchT<kMaxBatchItems> &p = batch_params();
+  fill_launch(L, p);
+  return launch_fix_t(p, n_sm, stream);
 }
 
 }  // namespace svo

@@ -16,6 +16,16 @@
 // must start at zero are cleared on `stream` at the start of every call.  Two
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads) therefore race on the array and must be serialised by the caller.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process.  A cudaDeviceReset (or anything else that destroys the
+// device's primary context) while the library is loaded would leave that
+// address stale, so it is not supported.
+//
+// Ray ordering (SVO_TRACE_ORDER_DIR / _ORIGIN) needs per-ray scratch of its
+// own and is rejected here, as are STATS and DEFER_FIX.  The launch record
+// lives in static storage under a lock of its own, so the call puts nothing
+// large on the caller's stack.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -40,6 +50,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+std::mutex g_launch_mu;  // guards the static launch record of trace_rays_noalloc
 void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
@@ -82,8 +93,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   }
   if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: rays and hits must be 16-byte aligned");
-  if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX))
-    return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: STATS and DEFER_FIX are not supported");
+  if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX | SVO_TRACE_ORDER_DIR | SVO_TRACE_ORDER_ORIGIN))
+    return set_last_error(SVO_ERR_ARG,
+                          "trace_rays_noalloc: STATS, DEFER_FIX and the ORDER flags are not supported");
   constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
   if ((flags & SVO_TRACE_REUSE) && (flags & kReuseNeeds) != kReuseNeeds)
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
@@ -100,7 +112,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
     return set_last_error(SVO_ERR_CUDA, m.c_str());
   }
   cudaStream_t st = (cudaStream_t)stream;
-  TraceLaunch launch;  // on the stack: no host heap either
+  // static launch record (about 16 KB): neither the host heap nor the caller's stack
+  static TraceLaunch launch;
+  std::lock_guard<std::mutex> guard(g_launch_mu);
   TraceLaunch *L = &launch;
   L->items[0] = scene_item(s, rays, n, hits, ray_flags);
   if (flags & SVO_TRACE_IMAGE_TILES) L->items[0].width = flags >> 16;

@@ -74,6 +74,17 @@ def compare(scene, local, rays, gpu, ora, allow_flagged_mismatch=0):
     unf = ~flagged
     bad_unf_id = np.nonzero(unf & ~id_eq)[0]
     bad_unf_t = np.nonzero(unf & ~t_eq & (~t_refined | fixed))[0]
+    # t-refined rays the FP64 pass did not fix: held to the certified bound
+    # their flag word carries, |t - t_exact| <= 2^e max(t_exact, h) (1 + 2^-18)
+    loose = unf & t_refined & ~fixed
+    e = g.ray_t_bound_exp(gpu["flags"])
+    with np.errstate(invalid="ignore", over="ignore"):
+        lim = np.ldexp(1.0, np.minimum(e, 1000)) * np.maximum(np.abs(t_o), h) * (1.0 + 2.0 ** -18)
+        loose_err = np.where(loose, np.abs(t_g - t_o), 0.0)
+    assert np.all(e[loose] >= -16), "a t-refined ray carries no bound exponent"
+    bad_loose = np.nonzero(loose & (e < 127) & ~(loose_err <= lim))[0]
+    assert bad_loose.size == 0, f"t-refined rays outside their certified bound at {bad_loose[:10]}: " \
+                                f"{t_g[bad_loose[:5]]} vs {t_o[bad_loose[:5]]}, e {e[bad_loose[:5]]}"
     assert bad_unf_id.size == 0, f"unflagged id mismatches at {bad_unf_id[:10]}: gpu part {gpu['part'][bad_unf_id[:5]]} " \
                                  f"vox {gpu['voxel'][bad_unf_id[:5]]} vs ora {ora['part'][bad_unf_id[:5]]} " \
                                  f"{ora['voxel'][bad_unf_id[:5]]}; t {t_g[bad_unf_id[:5]]} vs {t_o[bad_unf_id[:5]]}"
@@ -89,6 +100,10 @@ def compare(scene, local, rays, gpu, ora, allow_flagged_mismatch=0):
         "flagged_id_mismatch": int(flag_id_bad.sum()),
         "flagged_t_mismatch": int(flag_t_bad.sum()),
         "fp64_ties": int(fp64_tie.sum()),
+        "t_refined_unfixed": int(loose.sum()),
+        "t_refined_unfixed_max_rel_err": float(np.max(loose_err[loose] / np.maximum(np.abs(t_o[loose]), h[loose])))
+        if loose.any() else 0.0,
+        "t_refined_unfixed_unbounded": int((loose & (e >= 127)).sum()),
         "max_rel_t_err": float(np.max(np.abs(t_g[hit_o] - t_o[hit_o]) / np.maximum(np.abs(t_o[hit_o]), h[hit_o])))
         if hit_o.any() else 0.0,
     }

@@ -121,7 +121,7 @@ def test_pr1_parity(ctx, pr1, flags):
     ora = so.trace(rays)
     res = gs.trace(rays, flags)
     rep = compare(scene, gs.local, rays, res, ora)
-    assert rep["hits"] > 1000
+    assert rep["hits"] >= 1241  # the oracle hits 1379 of these rays; the floor is 90% of that
     assert rep["flagged"] <= 0.05 * rep["rays"], rep
     print("PR1", flags, rep)
 
@@ -150,7 +150,9 @@ def test_articulated_reduced_parity(ctx):
         ora = so.trace(rays, local=local)
         res = gs.trace(rays, 7)
         rep = compare(fig.scene, local, rays, res, ora)
-        assert rep["hits"] > 2000
+        # the oracle hits 3374 / 3668 / 3834 of these seeded rays at frames 0 / 17 / 45;
+        # the floor (90% of the smallest) keeps a changed workload from thinning the comparison
+        assert rep["hits"] >= 3030
         print("ART-reduced frame", frame, rep)
 
 
@@ -191,8 +193,15 @@ def test_incoherent_affine_many_parts(ctx):
 
 
 def test_edge_rays(ctx, pr1):
+    """Degenerate and extreme rays, every one compared with the oracle.  Both
+    sides apply the same rule to inputs that are not rays (Eq. 1 needs a
+    direction: its largest component magnitude in [2^-60, 2^60], finite origin
+    and direction, no NaN bound): they are misses, even a zero direction whose
+    origin lies inside an occupied leaf."""
     scene, gs, so = pr1
     base = synthetic.pr1_rays(scene)[8000:8064].copy()
+    ora_base = so.trace(base)
+    k = int(np.nonzero(ora_base["part"] != oracle.MISS_PART)[0][0])  # a ray that hits
     rays = base.copy()
     rays[0, 3], rays[0, 7] = 5.0, 1.0          # tmin > tmax: empty segment
     rays[1, 4:7] = 0.0                          # zero direction
@@ -202,14 +211,33 @@ def test_edge_rays(ctx, pr1):
     rays[5, 4:7] = [0.0, -1.0, 0.0]
     rays[6, 4:7] *= 1000.0                      # long direction (t scales)
     rays[7, 4:7] *= 1e-3                        # short direction
-    res = gs.trace(rays, 7)
-    for i in (0, 1, 2, 3):
-        assert res["part"][i] == oracle.MISS_PART and math.isinf(res["t"][i])
-    ok = np.ones(len(rays), bool)
-    ok[[0, 1, 2, 3]] = False
-    ora = so.trace(rays[ok])
-    sub = {k: v[ok] for k, v in res.items()}
-    compare(scene, gs.local, rays[ok], sub, ora)
+    # zero direction from the centre of the leaf ray k hits
+    part, vox = int(ora_base["part"][k]), int(ora_base["voxel"][k])
+    D = scene.assets[int(scene.part_asset[part])].depth
+    cell = np.array([(vox >> (a * D)) & ((1 << D) - 1) for a in range(3)], dtype=np.float64)
+    W = oracle.compose(scene.parent, gs.local)[part].reshape(3, 4)
+    inside = W[:, :3] @ ((cell + 0.5) / 2.0 ** D) + W[:, 3]
+    rays[8, 0:3], rays[8, 3], rays[8, 4:7], rays[8, 7] = inside, 0.0, 0.0, np.inf
+    # ray k with its direction rescaled to the ends of the valid range and just beyond
+    m = np.float32(np.abs(base[k, 4:7]).max())
+    unit = (base[k, 4:7] / m).astype(np.float32)  # largest component exactly 1
+    for row, scale in ((9, 2.0 ** -60), (10, 2.0 ** -61), (11, 2.0 ** 60), (12, 2.0 ** 61)):
+        rays[row] = base[k]
+        rays[row, 4:7] = unit * np.float32(scale)
+    rays[13, 3] = np.nan                        # NaN tmin
+    rays[14, 7] = np.nan                        # NaN tmax
+    rays[15, 4] = np.inf                        # infinite direction component
+    valid = oracle.ray_valid(rays)
+    assert not valid[[1, 2, 8, 10, 12, 13, 14, 15]].any() and valid[[0, 3, 9, 11]].all()
+    ora = so.trace(rays)
+    for flags in (0, 4, 7):
+        res = gs.trace(rays, flags)
+        for i in (0, 1, 2, 3, 8, 10, 12, 13, 14, 15):
+            assert res["part"][i] == oracle.MISS_PART and math.isinf(res["t"][i]), (flags, i)
+            assert ora["part"][i] == oracle.MISS_PART, i
+        for i in (9, 11):  # valid rescaled rays hit the same leaf; t scales with 1 / |d|
+            assert ora["part"][i] == ora_base["part"][k] and ora["voxel"][i] == ora_base["voxel"][k]
+        compare(scene, gs.local, rays, res, ora)
     # scaling d by s divides t by s
     r6 = gs.trace(base[6:7], 7)
     assert abs(res["t"][6] * 1000.0 - r6["t"][0]) <= 1e-5 * r6["t"][0] or not np.isfinite(r6["t"][0])
@@ -236,7 +264,9 @@ def test_empty_and_degenerate_assets(ctx):
     ora = so.trace(rays)
     res = gs.trace(rays, 7)
     rep = compare(scene, local, rays, res, ora)
-    assert rep["hits"] > 50
+    # the oracle hits 155 of these 8192 seeded rays (three of the four assets are
+    # nearly empty); the floor is 90% of that
+    assert rep["hits"] >= 139
     # the deep asset is reachable: rays aimed at its leaf centres hit it
     world = oracle.compose(scene.parent, local)
     W = world[2].reshape(3, 4)
@@ -318,7 +348,9 @@ def test_articulated_full_size_sampled(ctx):
         ora = so.trace(rays[idx], local=local)
         sub = {k: v[idx] for k, v in res.items()}
         rep = compare(fig.scene, local, rays[idx], sub, ora)
-        assert rep["hits"] > 500
+        # about 6% of the frame's rays hit: the oracle hits 1184 / 1336 of the
+        # sampled rays at frames 0 / 31; the floor is 90% of the smaller
+        assert rep["hits"] >= 1065
         print("ART full sampled frame", frame, rep, "flag rate full frame",
               float(((res["flags"] & 1) != 0).mean()))
 

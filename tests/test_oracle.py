@@ -644,3 +644,47 @@ def test_octree_dims_equal_the_affine_pose(seed):
         clear = hit & (ref["second"] - ref["t"] > 1e-9 * np.maximum(np.abs(ref["t"]), 1.0))
     assert np.array_equal(got["part"][clear], ref["part"][clear])
     assert np.array_equal(got["voxel"][clear], ref["voxel"][clear])
+
+
+def test_ray_validity_rule():
+    """Eq. 1 rays have a direction.  The oracle's reading makes that a rule
+    with exact bounds: the largest direction component magnitude lies in
+    [2^-60, 2^60], origin and direction are finite and neither bound is NaN.
+    Anything else is a miss -- even a zero direction whose origin lies inside
+    an occupied leaf, which the slab rule alone would report at tmin.  A valid
+    tiny or huge direction is traced: t scales as 1 / |d| exactly (the
+    entry plane x = 0 is 1 unit away from the origin)."""
+    depth = 2
+    n = 1 << depth
+    g = np.arange(n)
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    asset = synthetic.make_asset(depth, (x.ravel(), y.ravel(), z.ravel()))
+    scene = synthetic.Scene("full", [asset], np.zeros(1, np.int32), np.array([-1], np.int32),
+                            synthetic.affine12(np.eye(3), np.zeros(3))[None, :])
+    inside = [0.3, 0.4, 0.6]
+    outside = [-1.0, 0.4, 0.6]
+    rows = [
+        (inside, [0.0, 0.0, 0.0], 0.0, math.inf, None),                   # zero direction, origin in a leaf
+        (outside, [2.0 ** -61, 0.0, 0.0], 0.0, math.inf, None),           # below the range
+        (outside, [2.0 ** 61, 0.0, 0.0], 0.0, math.inf, None),            # above the range
+        (outside, [math.nan, 1.0, 0.0], 0.0, math.inf, None),             # NaN component
+        ([math.inf, 0.4, 0.6], [1.0, 0.0, 0.0], 0.0, math.inf, None),     # infinite origin
+        (outside, [1.0, 0.0, 0.0], math.nan, math.inf, None),             # NaN tmin
+        (outside, [1.0, 0.0, 0.0], 0.0, math.nan, None),                  # NaN tmax
+        (outside, [2.0 ** -60, 0.0, 0.0], 0.0, math.inf, 2.0 ** 60),      # smallest valid |d|
+        (outside, [2.0 ** 60, 0.0, 0.0], 0.0, math.inf, 2.0 ** -60),      # largest valid |d|
+        (outside, [-(2.0 ** -60), 2.0 ** -70, 0.0], 0.0, math.inf, "miss"),  # valid, pointing away
+        (inside, [0.0, 0.0, 2.0 ** -60], 0.25, math.inf, 0.25),           # valid, starts inside: tmin
+    ]
+    rays = np.zeros((len(rows), 8))
+    for i, (o, d, t0, t1, _) in enumerate(rows):
+        rays[i, 0:3], rays[i, 3], rays[i, 4:7], rays[i, 7] = o, t0, d, t1
+    valid = oracle.ray_valid(rays)
+    assert valid.tolist() == [r[4] is not None for r in rows]
+    for mode in (0, 1):
+        res = oracle.SceneOracle(scene).trace(rays, mode=mode, threads=1)
+        for i, (*_, exp) in enumerate(rows):
+            if exp is None or exp == "miss":
+                assert res["part"][i] == oracle.MISS_PART and math.isinf(res["t"][i]), (mode, i)
+            else:
+                assert res["part"][i] == 0 and res["t"][i] == exp, (mode, i, res["t"][i])
