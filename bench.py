@@ -202,6 +202,8 @@ def cpu_oracle_baseline(fig, poses, budget_s: float = 12.0) -> dict:
 
 
 def run_reference(args, rank: int, world: int) -> None:
+    """The reference arm: the FP64 oracle as it stands on the host cores, one
+    whole frame of the same workload per step (the bench's own config)."""
     if rank != 0:
         return
     import oracle
@@ -211,13 +213,10 @@ def run_reference(args, rank: int, world: int) -> None:
     poses = [fig.pose(f) for f in range(FRAMES)]
     so = oracle.SceneOracle(fig.scene)
     rays = fig.rays(WIDTH, HEIGHT)
-    sample = N_RAYS // 8
-    rng = np.random.default_rng(7)
     threads = oracle.default_threads()
 
     def step(s):
-        idx = rng.choice(N_RAYS, sample, replace=False)
-        so.trace(rays[idx], local=poses[s % FRAMES], threads=threads)
+        so.trace(rays, local=poses[frame_of(s, 1, 0)], threads=threads)
 
     for s in range(args.warmup):
         step(s)
@@ -225,17 +224,124 @@ def run_reference(args, rank: int, world: int) -> None:
     for s in range(args.steps):
         step(args.warmup + s)
     dt = time.perf_counter() - t0
-    value = args.steps * sample / dt / 1e6
-    desc = f"each step: {sample} random rays (1/8) of one {WIDTH}x{HEIGHT} frame, FP64 oracle descent"
+    value = args.steps * N_RAYS / dt / 1e6
+    desc = f"each step: one whole {WIDTH}x{HEIGHT} frame of the workload, FP64 oracle descent (no culling)"
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rays_per_step": sample},
+        "config": config_of(fig, 1),
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+def config_of(fig, world: int) -> dict:
+    """The workload's config block (the same for both arms)."""
+    return {"workload": WORKLOAD, "rays_per_step": N_RAYS, "parts": fig.scene.n_parts, "svo_depth": 9,
+            "leaves": int(sum(a.n_leaves for a in fig.scene.assets)),
+            "flags": "cull+sort+fp64_fix (+ autotuned launch shape and ray order)",
+            "parallelism": f"replicas x{world} (frames sharded)",
+            "l2": "flushed between steps (256 MiB write, outside the per-step events)"}
+
+
+def precision_oracle(threads: int) -> dict:
+    """CPU-baseline leg, precision stress (8 depth-13 parts behind five-level
+    rigid chains, 2^20 rays of which 30% graze leaf faces): the inputs and the
+    FP64 oracle's hits, against which the GPU's are compared."""
+    import oracle
+    import synthetic
+
+    prec = synthetic.precision_scene()
+    sc = prec.scene
+    world = oracle.compose(sc.parent, sc.local)
+    rays, n_prim = synthetic.precision_rays(prec, world, 1 << 20)
+    so = oracle.SceneOracle(sc)
+    t0 = time.perf_counter()
+    ora = so.trace(rays, threads=threads)
+    dt = time.perf_counter() - t0
+    depth = np.array([sc.assets[int(a)].depth for a in sc.part_asset])
+    diag = np.array([np.linalg.norm(world[p].reshape(3, 4)[:, :3] @ np.ones(3)) * 2.0 ** -depth[p]
+                     for p in range(sc.n_parts)])
+    return {"prec": prec, "rays": rays, "n_prim": n_prim, "ora": ora, "diag": diag, "oracle_s": dt,
+            "threads": threads}
+
+
+def precision_section(g, ctx, pin, dev, flush, reps: int = 5) -> dict:
+    """Error of the GPU path against the FP64 oracle on the precision-stress
+    workload, with and without the FP64 re-intersection pass, and its speed."""
+    import torch
+
+    import oracle
+
+    prec, rays_np, ora = pin["prec"], pin["rays"], pin["ora"]
+    sc_spec = prec.scene
+    handles = [ctx.upload(a.depth, a.leaf_ids, a.rgb) for a in sc_spec.assets]
+    sc = ctx.scene([handles[int(a)] for a in sc_spec.part_asset], sc_spec.parent)
+    sc.set_transforms(sc_spec.local)
+    sc.refit()
+    rays = torch.from_numpy(rays_np).to(dev)
+    n = int(rays.shape[0])
+    hits = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    rf = torch.zeros(n, dtype=torch.int32, device=dev)
+    t_o, p_o, v_o = ora["t"], ora["part"], ora["voxel"]
+    hit_o = p_o != oracle.MISS_PART
+    dn = np.linalg.norm(rays_np[:, 4:7].astype(np.float64), axis=1)
+    h = np.ones(n)
+    h[hit_o] = pin["diag"][p_o[hit_o]] / dn[hit_o]
+    scale = np.maximum(np.abs(t_o), h)
+    with np.errstate(invalid="ignore"):
+        tie = hit_o & (ora["second"] - t_o <= 1e-9 * np.maximum(np.abs(t_o), 1.0))
+    out = {"workload": f"precision stress: {len(prec.visible)} depth-13 parts at the ends of 5-level rigid chains "
+                       f"(translations up to 1e4 leaf sizes), {n} rays of which {n - pin['n_prim']} graze leaf "
+                       f"faces at < 1e-3 rad",
+           "rays": n, "oracle_hits": int(hit_o.sum()), "fp64_ties": int(tie.sum()),
+           "oracle": {"s": pin["oracle_s"], "mrays_per_s": n / pin["oracle_s"] / 1e6, "cores": pin["threads"]}}
+    for name, flags in (("fp32_only", g.TRACE_CULL | g.TRACE_SORT), ("with_fp64_pass", g.TRACE_DEFAULT)):
+        evs = []
+        for i in range(reps + 1):
+            flush.fill_(i & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record()
+            sc.trace(rays, hits, flags=flags, ray_flags=rf)
+            e[1].record()
+            evs.append(e)
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in evs[1:]]))
+        res = g.decode_hits(hits)
+        fl = rf.cpu().numpy().astype(np.uint32)
+        unc = (fl & g.RAY_UNCERTAIN) != 0
+        tref = (fl & g.RAY_T_REFINED) != 0
+        fixed = (fl & g.RAY_FIXED) != 0
+        id_eq = (res["part"] == p_o) & (res["voxel"] == v_o)
+        t_g = res["t"].astype(np.float64)
+        with np.errstate(invalid="ignore"):
+            rel = np.where(hit_o, np.abs(t_g - t_o) / scale, np.where(np.isinf(t_g), 0.0, np.inf))
+        # rays whose result is final: FP32-certified ones without the FP64 pass, every ray with it
+        final = (~unc & ~(tref & ~fixed)) if name == "fp32_only" else np.ones(n, bool)
+        row = {"ms": ms, "mrays_per_s": n / (ms / 1e3) / 1e6,
+               "flagged_uncertain": int(unc.sum()), "flagged_pct": float(100.0 * unc.mean()),
+               "t_refined": int(tref.sum()), "fixed": int(fixed.sum()),
+               "id_mismatch_outside_flags": int((~unc & ~id_eq & ~tie).sum()),
+               "id_mismatch_flagged": int((unc & ~id_eq & ~tie).sum()),
+               "id_mismatch_all": int((~id_eq & ~tie).sum()),
+               "grazing_flagged_pct": float(100.0 * unc[pin["n_prim"]:].mean()),
+               "final_rays": int(final.sum()),
+               "t_rel_err_max": float(rel[final & hit_o].max()) if (final & hit_o).any() else 0.0,
+               "t_rel_err_mean": float(rel[final & hit_o].mean()) if (final & hit_o).any() else 0.0}
+        if name == "fp32_only":
+            loose = tref & ~unc
+            e_b = g.ray_t_bound_exp(fl)
+            row["t_refined_unfixed_max_rel_err"] = float(rel[loose & hit_o].max()) if (loose & hit_o).any() else 0.0
+            row["t_refined_unfixed_within_bound"] = bool(np.all(
+                rel[loose & hit_o] <= np.ldexp(1.0, np.minimum(e_b[loose & hit_o], 1000)) * (1 + 2.0 ** -18)))
+        out[name] = row
+    ctx.check_device()
+    sc.close()
+    for hd in handles:
+        ctx.release(hd)
+    return out
 
 
 def hit_buffer_section(g, ctx, sc, fig, poses, rays, flags: int, stream, flush, frames: int = 60) -> dict:
@@ -347,10 +453,30 @@ def paper_experiment_section(g, ctx, fig, poses, dev, stream, flush, frames: int
             **out}
 
 
+def alg_bytes(st: dict) -> float:
+    """Algorithmic bytes of a trace from its STATS counters: 8 per node
+    descriptor fetched, 64 per (ray, part) entered, 48 per ray of I/O."""
+    return BYTES_PER_NODE * st["nodes_visited"] + BYTES_PER_PART * st["parts_entered"] + BYTES_PER_RAY_IO * st["rays"]
+
+
+def roofline_of(bytes_: float, ms: float, what: str) -> dict:
+    peaks = measured_peaks()
+    achieved = bytes_ / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peaks['source']} hbm_gbs (copy)",
+            "bytes": bytes_, "ms": ms, "timed": what}
+
+
 def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
     """The batched configuration: many uneven scenes traced in one persistent
-    launch (trace_batch) against the same scenes traced one call each."""
+    launch (trace_batch), the launch shape autotuned on the batch itself, and
+    the whole batched frame (per-scene pose copies and refits, ordering,
+    trace, FP64 pass) replayed from one CUDA graph; against the same scenes
+    traced one call each."""
     import torch
+
+    from paper_1911_06001_gb300 import autotune
+    from paper_1911_06001_gb300.graphs import BatchGraph
 
     scenes = []
     for sc_spec in bat.scenes:
@@ -363,62 +489,127 @@ def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
     n = sum(int(r.shape[0]) for r in rays)
     items = [(sc, r, h, None) for sc, r, h in zip(scenes, rays, hits)]
     torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
 
-    def timed(fn):
+    def timed(fn, st=None):
+        st = st or stream
         evs = []
         for i in range(reps + 2):
             flush.fill_(i & 0xFF)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            e[0].record()
+            e[0].record(st)
             fn()
-            e[1].record()
+            e[1].record(st)
             evs.append(e)
         torch.cuda.synchronize()
         return float(np.mean([a.elapsed_time(b) for a, b in evs[2:]]))
 
     flags = g.TRACE_DEFAULT
-    t_batch = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_ORDER_ORIGIN))
+    old_cfg = ctx.trace_config()
+    ctx.set_trace_config(128, 1)
     t_given = timed(lambda: ctx.trace_batch(items, flags=flags))
+    t_origin = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_ORDER_ORIGIN))
     t_each = timed(lambda: [sc.trace(r, h, flags=flags) for sc, r, h, _ in items])
+    # roofline of the trace kernel on the batch: algorithmic bytes from a
+    # counting pass, over the launch with the FP64 pass deferred (the call
+    # then issues two counter memsets and the trace kernel only)
+    st = g.new_stats(dev)
+    ctx.trace_batch(items, flags=flags | g.TRACE_STATS, stats=st)
+    torch.cuda.synchronize()
+    counts = g.read_stats(st)
+    t_kernel = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_DEFER_FIX))
+    ctx.fix_pending()
+    # the launch shape tuned on this batch, then the graph-captured frame in that shape
+    tuned = autotune.tune_batch(ctx, items, flags=flags, reps=2, blocks=(64, 128, 256), rays_per_lane=(1, 2, 4))
+    tflags = flags | autotune.order_flag(tuned)
+    t_tuned = timed(lambda: ctx.trace_batch(items, flags=tflags))
+    bg = BatchGraph(ctx, items, [s.local for s in bat.scenes], flags=tflags)
+    t_graph = timed(lambda: bg.replay(), st=bg.stream)
+    ctx.set_trace_config(*old_cfg)
     ctx.check_device()
     for sc in scenes:
         sc.close()
+    mr = lambda ms: n / (ms / 1e3) / 1e6  # noqa: E731
     return {"workload": f"{len(bat.scenes)} scenes of 4-256 parts (depth 6-11 pool, affine with shear), "
                         f"{n} incoherent rays in all", "rays": n,
-            "batched": {"value": n / (t_batch / 1e3) / 1e6, "unit": "Mrays/s", "ms": t_batch,
-                        "launch": "one persistent trace_batch, rays ordered by origin cell and direction per item "
-                                  "(one set of ordering launches for the whole batch)"},
-            "batched_given_order": {"value": n / (t_given / 1e3) / 1e6, "unit": "Mrays/s", "ms": t_given,
-                                    "launch": "the same, rays in their given order"},
-            "per_scene_calls": {"value": n / (t_each / 1e3) / 1e6, "unit": "Mrays/s", "ms": t_each}}
+            "batched": {"value": mr(t_tuned), "unit": "Mrays/s", "ms": t_tuned,
+                        "launch": f"one persistent trace_batch in the shape tuned on this batch (block "
+                                  f"{tuned['block']}, {tuned['rays_per_lane']} rays per lane, order "
+                                  f"{tuned['order']}, culling {tuned['cull']})"},
+            "graph": {"value": mr(t_graph), "unit": "Mrays/s", "ms": t_graph,
+                      "launch": "one CUDA graph replay: pose copy + refit of all 64 scenes (parallel branches), "
+                                "ordering, the persistent trace and the FP64 pass, in the tuned shape"},
+            "batched_given_order": {"value": mr(t_given), "unit": "Mrays/s", "ms": t_given,
+                                    "launch": "block 128, 1 ray per lane, rays in their given order"},
+            "batched_origin_order": {"value": mr(t_origin), "unit": "Mrays/s", "ms": t_origin},
+            "per_scene_calls": {"value": mr(t_each), "unit": "Mrays/s", "ms": t_each},
+            "tuned": {k: tuned[k] for k in ("block", "rays_per_lane", "order", "cull", "ms", "default_ms", "key")},
+            "nodes_per_ray": counts["nodes_visited"] / n, "parts_entered_per_ray": counts["parts_entered"] / n,
+            "roofline": {**roofline_of(alg_bytes(counts), t_kernel,
+                                       "trace_batch with the FP64 pass deferred: two 16-byte memsets and the "
+                                       "trace kernel (block 128, 1 ray per lane, given order)"),
+                         "kernel": "k_trace"}}
 
 
-def serving_section(g, ctx, srv, pool_handles, n_requests: int, warm: int, rate: float) -> dict:
+def serving_section(g, ctx, srv, pool_handles, n_requests: int, warm: int, rate: float,
+                    sweep=(4000.0, 8000.0, 16000.0), sweep_requests: int = 3000) -> dict:
     """Served render requests (continuous batching) against the same stream
-    rendered one request at a time."""
+    rendered one request at a time: at the configuration's arrival rate, over
+    a sweep of higher rates, and for a burst that saturates the server (every
+    request queued at once), with the burst's roofline."""
     from paper_1911_06001_gb300.serving import Server, latency_stats, run_unbatched
 
     scenes = [([pool_handles[int(a)] for a in s.scene.part_asset], s.scene.parent) for s in srv.scenes]
-    reqs = srv.requests(n_requests, rate=rate, seed=int(SEED_SERVE))
     server = Server(ctx, scenes, n_slots=4, max_batch_rays=8 << 20, instances_per_scene=4)
-    tickets = server.run(reqs)
-    meas = {id(r) for r in reqs[warm:]}
-    served = latency_stats([(t.arrival, t.done, t.n_rays) for t in tickets if id(t.request) in meas])
-    batches = {}
-    for t in tickets:
-        batches[t.submitted] = batches.get(t.submitted, 0) + 1
-    served["mean_batch"] = float(np.mean(list(batches.values())))
-    # saturation: every request queued at once -> the server's throughput ceiling
-    burst = srv.requests(max(n_requests // 3, 64), rate=1e9, seed=int(SEED_SERVE) + 1)
-    bt = server.run(burst)
-    sat = latency_stats([(t.arrival, t.done, t.n_rays) for t in bt])
     alone = [ctx.scene(h, p) for h, p in scenes]
-    plain = latency_stats(run_unbatched(ctx, alone, reqs)[warm:])
+
+    def served_stats(tickets, reqs, warm_n):
+        meas = {id(r) for r in reqs[warm_n:]}
+        st = latency_stats([(t.arrival, t.done, t.n_rays, t.device_ms) for t in tickets
+                            if id(t.request) in meas])
+        batches = {}
+        for t in tickets:
+            batches[t.submitted] = batches.get(t.submitted, 0) + 1
+        st["mean_batch"] = float(np.mean(list(batches.values())))
+        return st
+
+    def point(r, n_req, warm_n, seed):
+        reqs = srv.requests(n_req, rate=r, seed=seed)
+        served = served_stats(server.run(reqs), reqs, warm_n)
+        plain = latency_stats(run_unbatched(ctx, alone, reqs)[warm_n:])
+        return {"rate_req_s": r, "offered_mrays_per_s": float(sum(q.width * q.height for q in reqs[warm_n:]) /
+                                                              (reqs[-1].arrival - reqs[warm_n].arrival) / 1e6),
+                "served": served, "unbatched": plain,
+                "served_vs_unbatched_mrays": served["mrays_per_s"] / plain["mrays_per_s"]}
+
+    main = point(rate, n_requests, warm, int(SEED_SERVE))
+    points = [point(r, sweep_requests, sweep_requests // 10, int(SEED_SERVE) + 10 + i) for i, r in enumerate(sweep)]
+    # saturation: every request queued at once -> the server's throughput ceiling, with its latencies;
+    # then the same burst once more with counters on, for the algorithmic bytes of the roofline
+    burst = srv.requests(max(n_requests // 3, 64), rate=1e9, seed=int(SEED_SERVE) + 1)
+    sat = served_stats(server.run(burst), burst, 0)
+    server.stats = g.new_stats(server.dev)
+    server.run(burst)
+    import torch
+
+    torch.cuda.synchronize()
+    counts = g.read_stats(server.stats)
+    server.stats = None
+    span_ms = float(sum(q.width * q.height for q in burst)) / sat["mrays_per_s"] / 1e3
     ctx.check_device()
-    return {"workload": f"{len(srv.scenes)} resident scenes (16-128 parts, depth 8-11), Poisson {rate:g} req/s, "
+    for sc in alone:
+        sc.close()
+    return {"workload": f"{len(srv.scenes)} resident scenes (16-128 parts, depth 8-11), Poisson arrivals, "
                         f"resolutions 256^2/512^2/1280x720/1920x1080, fresh pose per request",
-            "served": served, "unbatched": plain,
-            "saturated": {"requests": sat["requests"], "mrays_per_s": sat["mrays_per_s"]}}
+            "rate_req_s": rate, "served": main["served"], "unbatched": main["unbatched"],
+            "served_vs_unbatched_mrays": main["served_vs_unbatched_mrays"],
+            "sweep": points,
+            "saturated": sat,
+            "saturated_roofline": {**roofline_of(alg_bytes(counts), span_ms,
+                                                 "the saturated burst, first arrival to last completion (host "
+                                                 "scheduling, pose uploads, refits, raygen, trace, FP64 pass)"),
+                                   "kernel": "served pipeline (k_trace dominant)",
+                                   "nodes_per_ray": counts["nodes_visited"] / max(counts["rays"], 1)}}
 
 
 SEED_SERVE = 1911_06001 + 4 * 1000 + 7
@@ -565,9 +756,13 @@ def main() -> None:
         bat = synthetic.batched_scenes(pool=pool)
         srv = synthetic.serving_world(pool=pool, pool_indices=list(range(2 * 4, 6 * 4)))
         many = many_parts_inputs(pool)
-    cpu = None
+    cpu = pin = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_baseline(fig, poses)
+        if extra:
+            import oracle
+
+            pin = precision_oracle(oracle.default_threads())
 
     import torch
     import torch.distributed as dist
@@ -748,17 +943,19 @@ def main() -> None:
     nodes = np.mean([stats_by_frame[f]["nodes_visited"] for f in timed_frames])
     parts = np.mean([stats_by_frame[f]["parts_entered"] for f in timed_frames])
     flagged = np.mean([stats_by_frame[f]["flagged"] for f in timed_frames])
-    alg_bytes = BYTES_PER_NODE * nodes + BYTES_PER_PART * parts + BYTES_PER_RAY_IO * N_RAYS
+    frame_bytes = BYTES_PER_NODE * nodes + BYTES_PER_PART * parts + BYTES_PER_RAY_IO * N_RAYS
     peaks = measured_peaks()
-    achieved = alg_bytes / (trace_ms.mean() / 1e3) / 1e9
+    achieved = frame_bytes / (trace_ms.mean() / 1e3) / 1e9
     traffic, traffic_src = measured_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "k_trace",
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
-                "bytes_per_launch": alg_bytes, "launch_ms": float(trace_ms.mean())}
+                "bytes_per_launch": frame_bytes, "launch_ms": float(trace_ms.mean())}
 
-    batched = serving = hit_buffer = paper_experiment = many_parts = None
+    batched = serving = hit_buffer = paper_experiment = many_parts = precision = None
+    if pin is not None:
+        precision = precision_section(g, ctx, pin, dev, flush)
     if extra:
         pool_handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
         hit_buffer = hit_buffer_section(g, ctx, sc, fig, poses, rays, g.TRACE_DEFAULT | order, stream, flush)
@@ -774,10 +971,7 @@ def main() -> None:
             "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rays_per_step": N_RAYS, "parts": fig.scene.n_parts, "svo_depth": 9,
-                       "leaves": int(sum(a.n_leaves for a in fig.scene.assets)),
-                       "flags": "cull+sort+fp64_fix (+ autotuned launch shape and ray order)", "parallelism": f"replicas x{world} (frames sharded)",
-                       "l2": "flushed between steps (256 MiB write, outside the per-step events)"},
+            "config": config_of(fig, world),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "per": "frame (pose upload + refit + trace + FP64 fix)"},
             "breakdown_ms": {"refit": float(refit_ms.mean()), "trace": float(trace_ms.mean()),
@@ -793,6 +987,7 @@ def main() -> None:
             "batched": batched,
             "many_parts": many_parts,
             "serving": serving,
+            "precision": precision,
             "flagged_frac": float(flagged / N_RAYS),
             "nodes_per_ray": float(nodes / N_RAYS),
             "parts_entered_per_ray": float(parts / N_RAYS),

@@ -8,7 +8,9 @@ of 8 x 4 pixels) and, for scenes of 64 parts or more, the culling structure
 (the cluster level or the scene grid).  ``tune`` times every combination on the caller's rays with
 CUDA events (L2 flushed between repetitions), keeps the fastest, and can
 remember it in a JSON cache under a caller-chosen key (for example the scene
-and ray-batch shape).
+and ray-batch shape).  ``tune_batch`` does the same for a batch of uneven
+scenes traced in one persistent launch (``Context.trace_batch``), keyed by the
+batch's shape (``batch_key``).
 """
 
 from __future__ import annotations
@@ -116,3 +118,73 @@ def load(cache_path: str) -> dict:
         with open(cache_path) as f:
             return json.load(f)
     return {}
+
+
+def batch_key(items) -> str:
+    """Cache key of a batch's shape: item count, ray count and part count of
+    every item (the workload the tuned launch applies to)."""
+    shape = ",".join(f"{int(it[1].shape[0])}x{int(it[0].n_parts)}" for it in items)
+    import hashlib
+
+    return f"batch:{len(items)}:{hashlib.sha256(shape.encode()).hexdigest()[:16]}"
+
+
+def tune_batch(ctx: Context, items, flags: int = TRACE_DEFAULT, reps: int = 3, blocks=BLOCKS,
+               rays_per_lane=RAYS_PER_LANE, orders=("none", "dir", "origin"), culls=None,
+               cache_path: str | None = None, key: str | None = None, stream=None) -> dict:
+    """Time every (block, rays_per_lane, order, cull) on a whole batch traced by
+    one ``trace_batch`` launch (``items`` as for ``Context.trace_batch``);
+    apply and return the fastest.  The grid is tried when some scene of the
+    batch has GRID_MIN_PARTS parts or more.  ``key`` defaults to
+    ``batch_key(items)``."""
+    import torch
+
+    key = key or batch_key(items)
+    if cache_path:
+        cached = load(cache_path).get(key)
+        if cached:
+            apply(ctx, cached)
+            return cached
+    if culls is None:
+        cs = TRACE_CULL | TRACE_SORT
+        big = any(getattr(it[0], "n_parts", 0) >= GRID_MIN_PARTS for it in items)
+        culls = ("clusters", "grid") if big and (flags & cs) == cs and not (flags & TRACE_REUSE) else ("clusters",)
+    dev = items[0][1].device
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    old = ctx.trace_config()
+    table = []
+    for b, r, o, c in itertools.product(blocks, rays_per_lane, orders, culls):
+        ctx.set_trace_config(b, r)
+        f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | ORDERS[o] | CULLS[c]
+        evs = []
+        with torch.cuda.stream(st):
+            for i in range(reps + 1):
+                flush.fill_(i & 0xFF)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                e[0].record(st)
+                ctx.trace_batch(items, flags=f, stream=st)
+                e[1].record(st)
+                evs.append(e)
+        torch.cuda.synchronize()
+        table.append({"block": b, "rays_per_lane": r, "order": o, "cull": c,
+                      "ms": float(np.median([a.elapsed_time(z) for a, z in evs[1:]]))})
+    ctx.set_trace_config(*old)
+    best = min(table, key=lambda x: x["ms"])
+    default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"
+                    and x["cull"] == "clusters"), None)
+    result = dict(best)
+    result["default_ms"] = default["ms"] if default else None
+    result["n_rays"] = int(sum(int(it[1].shape[0]) for it in items))
+    result["image_width"] = 0
+    result["key"] = key
+    result["table"] = table
+    apply(ctx, result)
+    if cache_path:
+        data = load(cache_path)
+        data[key] = result
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1)
+        os.replace(tmp, cache_path)
+    return result

@@ -53,3 +53,82 @@ class FrameGraph:
             host = torch.from_numpy(np.ascontiguousarray(local, dtype=np.float64).reshape(-1, 12))
             self.poses.copy_(host, non_blocking=False)
         self.graph.replay()
+
+
+class BatchGraph:
+    """A batched frame of many scenes captured as one CUDA graph.
+
+    One replay copies every scene's local poses from a pinned host buffer to
+    the device, composes / inverts / refits every scene, and runs
+    ``trace_batch`` over all items (its ray-ordering launches, the persistent
+    trace kernel and the FP64 pass included).  The per-scene refits are
+    one-block kernels, so the graph fans them out over ``branches`` parallel
+    branches (side streams joined by events at capture) and they run side by
+    side on the device instead of one after another.
+
+    ``items``: (scene, rays, hits, ray_flags-or-None[, image_width]) as for
+    ``Context.trace_batch``; ``local``: one [P, 12] FP64 pose array per
+    distinct scene, in order of first appearance in ``items``.  Capture
+    happens once, after an eager warm-up on the same streams has grown the
+    library's per-stream scratch."""
+
+    def __init__(self, ctx: Context, items, local, flags: int = TRACE_DEFAULT, branches: int = 8):
+        import torch
+
+        self.ctx = ctx
+        self.items = list(items)
+        self.flags = int(flags)
+        dev = self.items[0][1].device
+        self.scenes = []
+        for it in self.items:
+            if all(it[0] is not s for s in self.scenes):
+                self.scenes.append(it[0])
+        sizes = [12 * s.n_parts for s in self.scenes]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = int(self.offsets[-1])
+        self.host = torch.empty(n, dtype=torch.float64).pin_memory()
+        self.dev = torch.empty(n, dtype=torch.float64, device=dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.side = [torch.cuda.Stream(device=dev) for _ in range(max(1, min(branches, len(self.scenes))))]
+        self.fork = torch.cuda.Event()
+        self.joins = [torch.cuda.Event() for _ in self.side]
+        self.done = torch.cuda.Event()
+        self.set_poses(local)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.stream):
+            self._frame()  # eager warm-up on the capture streams: grows their scratch
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self._frame()
+
+    def set_poses(self, local) -> None:
+        """Write the next replay's poses (waits until the previous replay has read them)."""
+        self.done.synchronize()
+        h = self.host.numpy()
+        for k, sc in enumerate(self.scenes):
+            h[self.offsets[k]:self.offsets[k + 1]] = np.ascontiguousarray(local[k], dtype=np.float64).ravel()
+
+    def _frame(self) -> None:
+        s = self.stream
+        self.dev.copy_(self.host, non_blocking=True)
+        self.fork.record(s)
+        nb = len(self.side)
+        for b, side in enumerate(self.side):
+            side.wait_event(self.fork)
+            for k in range(b, len(self.scenes), nb):
+                sc = self.scenes[k]
+                sc.set_transforms_device(self.dev[self.offsets[k]:self.offsets[k + 1]], stream=side)
+                sc.refit(stream=side)
+            self.joins[b].record(side)
+        for e in self.joins:
+            s.wait_event(e)
+        self.ctx.trace_batch(self.items, flags=self.flags, stream=s)
+
+    def replay(self, local=None) -> None:
+        """Run one batched frame on ``self.stream``; ``local`` (per scene [P, 12]
+        poses) replaces the poses first."""
+        if local is not None:
+            self.set_poses(local)
+        self.graph.replay()
+        self.done.record(self.stream)

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import TRACE_DEFAULT, Context, trace_image
+from . import TRACE_DEFAULT, TRACE_STATS, Context, trace_image
 
 RAY_BYTES = 32
 HIT_BYTES = 16
@@ -51,6 +51,7 @@ class Ticket:
     instance: object = None
     hits: object = None     # CUDA int64 view [n, 2] into the slot's hit buffer (valid until the slot is reused)
     status: str = "queued"  # queued -> running -> done, or queued -> timeout / cancelled
+    device_ms: float = 0.0  # device time of its batch (first kernel of the batch to completion)
 
     @property
     def latency(self) -> float:
@@ -142,6 +143,7 @@ class _Slot:
     hits: object
     capacity: int
     event: object = None
+    start: object = None    # timing event recorded before the batch's first kernel
     tickets: list = field(default_factory=list)
     busy: bool = False
 
@@ -173,6 +175,7 @@ class Server:
         self.completed = []
         self.max_batch_rays = max_batch_rays
         self.on_done = None  # called for every completed ticket before its slot is reused
+        self.stats = None    # a stats tensor (new_stats): every batch accumulates its counters into it
         self._warm()
 
     def _warm(self) -> None:
@@ -205,9 +208,11 @@ class Server:
         now = time.perf_counter()
         for s in self.slots:
             if s.busy and s.event.query():
+                dev_ms = s.start.elapsed_time(s.event)
                 for t in s.tickets:
                     t.done = now
                     t.status = "done"
+                    t.device_ms = dev_ms
                     self.instances[t.request.scene].append(t.instance)
                     out.append(t)
                 self.queue.release(s.tickets)
@@ -248,6 +253,8 @@ class Server:
 
         items = []
         now = time.perf_counter()
+        s.start = torch.cuda.Event(enable_timing=True)
+        s.start.record(s.stream)
         for t in batch:
             r = t.request
             inst = t.instance
@@ -261,8 +268,11 @@ class Server:
             t.hits = hits
             t.slot = si
             t.submitted = now
-        self.ctx.trace_batch(items, flags=self.flags, stream=s.stream)
-        s.event = torch.cuda.Event()
+        if self.stats is not None:
+            self.ctx.trace_batch(items, flags=self.flags | TRACE_STATS, stats=self.stats, stream=s.stream)
+        else:
+            self.ctx.trace_batch(items, flags=self.flags, stream=s.stream)
+        s.event = torch.cuda.Event(enable_timing=True)
         s.event.record(s.stream)
         s.tickets = batch
         s.busy = True
@@ -306,28 +316,39 @@ def render_alone(ctx: Context, scene_handle, request, flags: int = TRACE_DEFAULT
 def run_unbatched(ctx: Context, scene_handles, requests, flags: int = TRACE_DEFAULT) -> list:
     """The baseline: the same request stream served one request at a time, each
     traced alone as soon as it has arrived and the previous one has finished.
-    Returns (arrival, done, n_rays) per request."""
+    Returns (arrival, done, n_rays, device ms) per request."""
     import torch
 
     t0 = time.perf_counter()
     out = []
     stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for r in sorted(requests, key=lambda q: q.arrival):
         while time.perf_counter() < t0 + r.arrival:
             pass
+        ev[0].record(stream)
         render_alone(ctx, scene_handles[r.scene], r, flags=flags, stream=stream)
+        ev[1].record(stream)
         stream.synchronize()
-        out.append((t0 + r.arrival, time.perf_counter(), int(r.width) * int(r.height)))
+        out.append((t0 + r.arrival, time.perf_counter(), int(r.width) * int(r.height), ev[0].elapsed_time(ev[1])))
     return out
 
 
 def latency_stats(pairs) -> dict:
-    """pairs: iterable of (arrival, done, n_rays).  p50/p99 latency in ms and Mrays/s over the window."""
+    """pairs: iterable of (arrival, done, n_rays[, device_ms]).  p50/p99 latency
+    in ms and Mrays/s over the window; with device times also their p50/p99
+    and those of the rest of the latency (waiting, host work, polling)."""
     a = np.array(list(pairs), dtype=np.float64)
     if a.size == 0:
         return {"requests": 0}
     lat = (a[:, 1] - a[:, 0]) * 1e3
     span = a[:, 1].max() - a[:, 0].min()
-    return {"requests": int(a.shape[0]), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "mrays_per_s": float(a[:, 2].sum() / span / 1e6)}
+    out = {"requests": int(a.shape[0]), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+           "mrays_per_s": float(a[:, 2].sum() / span / 1e6)}
+    if a.shape[1] > 3:
+        dev = a[:, 3]
+        out.update({"device_p50_ms": float(np.percentile(dev, 50)), "device_p99_ms": float(np.percentile(dev, 99)),
+                    "host_and_wait_p50_ms": float(np.percentile(lat - dev, 50)),
+                    "host_and_wait_p99_ms": float(np.percentile(lat - dev, 99))})
+    return out

@@ -39,4 +39,5 @@ from .scenes import (  # noqa: F401
     PrecisionScene,
     precision_scene,
     grazing_rays,
+    precision_rays,
 )

@@ -783,3 +783,38 @@ def grazing_rays(world12, depth: int, leaf_ids, n: int, rng: np.random.Generator
         out[k, 4:7] = wd
         out[k, 7] = np.inf
     return out
+
+
+def precision_rays(prec: PrecisionScene, world, n_total: int = 1 << 20, graze_frac: float = 0.3,
+                   seed: int = 13) -> tuple:
+    """The precision-stress ray set: ``n_total`` rays of which ``graze_frac``
+    graze leaf faces (``grazing_rays``, dealt over the visible parts) and the
+    rest are pinhole rays, one square camera per visible part framing its
+    shell from three shell radii away.  ``world``: the parts' world poses
+    ([P, 12], as the caller composes them), used only to aim the rays.
+    Returns (rays [n, 8] float32, number of pinhole rays first)."""
+    rng = np.random.default_rng(seed)
+    scene = prec.scene
+    n_graze = int(graze_frac * n_total)
+    per_cam = (n_total - n_graze) // len(prec.visible)
+    side = int(np.sqrt(per_cam))
+    prim = []
+    for v in prec.visible:
+        a = scene.assets[int(scene.part_asset[v])]
+        x, y, z = unpack_ids(a.leaf_ids, a.depth)
+        cells = (np.stack([x, y, z], 1) + 0.5) / (1 << a.depth)
+        mid = cells.mean(0)
+        r_l = float(np.linalg.norm(cells - mid, axis=1).max())
+        W = np.asarray(world[v]).reshape(3, 4)
+        c = W[:, :3] @ mid + W[:, 3]  # rigid chain: the shell keeps its size
+        view = rng.standard_normal(3)
+        view /= np.linalg.norm(view)
+        prim.append(pinhole_rays(c + 3.0 * r_l * view, c, side, side, 44.0))
+    prim = np.concatenate(prim)
+    graze = []
+    for k in range(n_graze // 4096 + 1):
+        v = int(prec.visible[k % len(prec.visible)])
+        a = scene.assets[int(scene.part_asset[v])]
+        graze.append(grazing_rays(world[v], a.depth, a.leaf_ids, 4096, rng))
+    graze = np.concatenate(graze)[:n_graze]
+    return np.ascontiguousarray(np.concatenate([prim, graze]), dtype=np.float32), prim.shape[0]

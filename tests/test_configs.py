@@ -113,32 +113,9 @@ def test_precision_stress(ctx):
     world = oracle.compose(scene.parent, scene.local)
     got = gs.sc.read_poses()
     assert np.allclose(got["world"], world, rtol=0, atol=1e-12 * max(1.0, np.abs(world).max()))
-    rng = np.random.default_rng(13)
     n_total = 1 << 20
-    n_graze = int(0.3 * n_total)
-    per_cam = (n_total - n_graze) // len(prec.visible)
-    side = int(np.sqrt(per_cam))
-    prim = []
-    for v in prec.visible:
-        a = scene.assets[int(scene.part_asset[v])]
-        x, y, z = synthetic.unpack_ids(a.leaf_ids, a.depth)
-        cells = (np.stack([x, y, z], 1) + 0.5) / (1 << a.depth)
-        mid = cells.mean(0)
-        r_l = float(np.linalg.norm(cells - mid, axis=1).max())
-        W = world[v].reshape(3, 4)
-        c = W[:, :3] @ mid + W[:, 3]  # rigid chain: the shell keeps its size
-        view = rng.standard_normal(3)
-        view /= np.linalg.norm(view)
-        # frame the shell from three shell radii away
-        prim.append(synthetic.pinhole_rays(c + 3.0 * r_l * view, c, side, side, 44.0))
-    prim = np.concatenate(prim)
-    graze = []
-    for k in range(n_graze // 4096 + 1):
-        v = int(prec.visible[k % len(prec.visible)])
-        a = scene.assets[int(scene.part_asset[v])]
-        graze.append(synthetic.grazing_rays(world[v], a.depth, a.leaf_ids, 4096, rng))
-    graze = np.concatenate(graze)[:n_graze]
-    rays = np.concatenate([prim, graze])
+    rays, n_prim = synthetic.precision_rays(prec, world, n_total)
+    prim = rays[:n_prim]
     ora = oracle.SceneOracle(scene).trace(rays)
     res = gs.trace(rays, g.TRACE_DEFAULT)
     rep = compare(scene, scene.local, rays, res, ora)

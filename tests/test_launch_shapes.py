@@ -214,3 +214,71 @@ def test_host_frame_loop_overlaps_calls(ctx):
         got = g.decode_hits(hh)
         for key in ("t", "part", "voxel"):
             assert np.array_equal(got[key], ref[key]), (f, key)
+
+
+def _small_batch(ctx):
+    import torch
+
+    bat = synthetic.batched_scenes(seed=5, n_scenes=6, parts=(4, 80), depths=range(6, 9), side=(48, 128),
+                                   per_depth=2)
+    handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in bat.pool]
+    items = []
+    for s, r in zip(bat.scenes, bat.rays):
+        sc = ctx.scene([handles[int(a)] for a in s.part_asset], s.parent)
+        sc.set_transforms(s.local)
+        sc.refit()
+        items.append((sc, torch.from_numpy(r).cuda(), torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda"),
+                      torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")))
+    return bat, items
+
+
+def test_batch_graph_replays_match_eager_batches(ctx):
+    """A batched frame (per-scene pose copies, refits fanned out over graph
+    branches, ordering, the persistent trace and the FP64 pass) replayed from
+    one CUDA graph gives bit-identical hits and flags to the eager
+    trace_batch of the same poses, over several pose sets."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300.graphs import BatchGraph
+
+    bat, items = _small_batch(ctx)
+    rng = np.random.default_rng(3)
+    flags = g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN
+    graph_items = [(sc, r, torch.empty_like(h), torch.zeros_like(f)) for sc, r, h, f in items]
+    bg = BatchGraph(ctx, graph_items, [s.local for s in bat.scenes], flags=flags, branches=4)
+    for rep in range(3):
+        local = []
+        for s in bat.scenes:  # every root re-posed: a small rigid motion of each scene
+            L = s.local.copy()
+            for i in np.nonzero(s.parent < 0)[0]:
+                A = synthetic.euler_xyz(*rng.uniform(-0.2, 0.2, 3))
+                M = L[i].reshape(3, 4)
+                L[i] = np.hstack([A @ M[:, :3], (A @ M[:, 3] + rng.uniform(-0.3, 0.3, 3))[:, None]]).ravel()
+            local.append(L)
+        bg.replay(local)
+        for (sc, _, _, _), L in zip(items, local):
+            sc.set_transforms(L)
+            sc.refit()
+        ctx.trace_batch(items, flags=flags)
+        torch.cuda.synchronize()
+        hits = 0
+        for (_, _, h_ref, f_ref), (_, _, h_g, f_g) in zip(items, graph_items):
+            assert torch.equal(h_ref, h_g) and torch.equal(f_ref, f_g), rep
+            hits += int((g.decode_hits(h_ref)["part"] != 0xFFFFFFFF).sum())
+        assert hits > 2000
+
+
+def test_tune_batch_picks_and_caches(ctx, tmp_path):
+    import paper_1911_06001_gb300 as g
+    from paper_1911_06001_gb300 import autotune
+
+    _, items = _small_batch(ctx)
+    cache = str(tmp_path / "tune.json")
+    cfg = autotune.tune_batch(ctx, items, reps=1, blocks=(128,), rays_per_lane=(1, 2), orders=("none", "origin"),
+                              cache_path=cache)
+    assert cfg["key"] == autotune.batch_key(items) and len(cfg["table"]) == 2 * 2 * 2  # grid tried: 80 parts
+    assert ctx.trace_config() == (cfg["block"], cfg["rays_per_lane"])
+    assert autotune.tune_batch(ctx, items, cache_path=cache)["ms"] == cfg["ms"]
+    ctx.set_trace_config(128, 4)
+    assert g.TRACE_GRID == autotune.CULLS["grid"]
