@@ -266,7 +266,9 @@ def test_batch_graph_replays_match_eager_batches(ctx):
         for (_, _, h_ref, f_ref), (_, _, h_g, f_g) in zip(items, graph_items):
             assert torch.equal(h_ref, h_g) and torch.equal(f_ref, f_g), rep
             hits += int((g.decode_hits(h_ref)["part"] != 0xFFFFFFFF).sum())
-        assert hits > 2000
+        # the oracle hits 1660 / 1612 / 1569 of these 33838 seeded rays over the
+        # three pose sets; the floor is 90% of the smallest
+        assert hits >= 1412
 
 
 def test_tune_batch_picks_and_caches(ctx, tmp_path):
