@@ -185,6 +185,15 @@ const char *svo_status_string(svo_status s);
  * Results do not depend on it; the autotuner picks it.  Default 128 / 1. */
 svo_status svo_set_trace_config(svo_ctx *ctx, int32_t block, int32_t rays_per_lane);
 svo_status svo_get_trace_config(svo_ctx *ctx, int32_t *block, int32_t *rays_per_lane);
+/* Top octree levels (0..4) that each thread block of a one-scene trace
+ * (trace_rays, or trace_batch whose items all trace one scene of at most
+ * 256 parts) copies into shared memory at start, so that the first node
+ * fetches of every descent are served on chip (the paper's traversal starts
+ * every ray at the root, Sec. IV-B).  Fewer levels are staged when a scene's
+ * top nodes would exceed 16 KB.  Results do not depend on it; the autotuner
+ * picks it.  Default 0. */
+svo_status svo_set_smem_levels(svo_ctx *ctx, int32_t levels);
+svo_status svo_get_smem_levels(svo_ctx *ctx, int32_t *levels);
 /* Read and clear the context's device error word (synchronises the device).
  * Returns SVO_OK, or SVO_ERR_DEVICE with the failing check in the message. */
 svo_status svo_check_device(svo_ctx *ctx);

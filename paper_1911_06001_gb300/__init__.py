@@ -116,6 +116,15 @@ class Context:
         _lib.check(self.lib.svo_get_trace_config(self.h, C.byref(b), C.byref(r)))
         return b.value, r.value
 
+    def set_smem_levels(self, levels: int) -> None:
+        """Top octree levels (0-4) one-scene traces stage in shared memory (speed only)."""
+        _lib.check(self.lib.svo_set_smem_levels(self.h, int(levels)))
+
+    def smem_levels(self) -> int:
+        v = C.c_int32(0)
+        _lib.check(self.lib.svo_get_smem_levels(self.h, C.byref(v)))
+        return v.value
+
     def check_device(self) -> None:
         _lib.check(self.lib.svo_check_device(self.h))
 

@@ -2,7 +2,8 @@
 
 Knobs that change only speed, never results: the trace kernel's block size
 (64 / 128 / 256 threads), the rays each lane takes per warp tile (1 / 2 / 4 /
-8), the ray order (as given, grouped by direction, grouped by origin cell
+8), the number of top octree levels each block stages in shared memory (0-4,
+for traces of one scene), the ray order (as given, grouped by direction, grouped by origin cell
 then direction, or -- for rays that are the pixels of an image -- warp tiles
 of 8 x 4 pixels) and, for scenes of 64 parts or more, the culling structure
 (the cluster level or the scene grid).  ``tune`` times every combination on the caller's rays with
@@ -49,12 +50,12 @@ def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> floa
 
 def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, blocks=BLOCKS,
          rays_per_lane=RAYS_PER_LANE, orders=None, cache_path: str | None = None,
-         key: str | None = None, image_width: int = 0, culls=None) -> dict:
-    """Time every (block, rays_per_lane, order, cull) on ``rays`` (CUDA [n, 8])
-    traced against ``scene``; apply and return the fastest.  The "image" order
-    is tried only when ``image_width`` (row-major pixels) is given, the "grid"
-    culling only for scenes of GRID_MIN_PARTS parts or more traced with
-    CULL | SORT and without REUSE."""
+         key: str | None = None, image_width: int = 0, culls=None, levels=(0,)) -> dict:
+    """Time every (block, rays_per_lane, smem levels, order, cull) on ``rays``
+    (CUDA [n, 8]) traced against ``scene``; apply and return the fastest.  The
+    "image" order is tried only when ``image_width`` (row-major pixels) is
+    given, the "grid" culling only for scenes of GRID_MIN_PARTS parts or more
+    traced with CULL | SORT and without REUSE."""
     import torch
 
     if cache_path and key:
@@ -71,16 +72,19 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
     hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
     old = ctx.trace_config()
+    old_levels = ctx.smem_levels()
     table = []
-    for b, r, o, c in itertools.product(blocks, rays_per_lane, orders, culls):
+    for b, r, lv, o, c in itertools.product(blocks, rays_per_lane, levels, orders, culls):
         ctx.set_trace_config(b, r)
+        ctx.set_smem_levels(lv)
         f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | _flag(o, image_width) | CULLS[c]
-        table.append({"block": b, "rays_per_lane": r, "order": o, "cull": c,
+        table.append({"block": b, "rays_per_lane": r, "smem_levels": lv, "order": o, "cull": c,
                       "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
+    ctx.set_smem_levels(old_levels)
     best = min(table, key=lambda x: x["ms"])
     default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"
-                    and x["cull"] == "clusters"), None)
+                    and x["cull"] == "clusters" and x["smem_levels"] == 0), None)
     result = dict(best)
     result["default_ms"] = default["ms"] if default else None
     result["n_rays"] = int(rays.shape[0])
@@ -104,6 +108,7 @@ def _flag(order: str, image_width: int) -> int:
 def apply(ctx: Context, cfg: dict) -> int:
     """Set the tuned launch shape on ``ctx``; returns the flags (order, culling) to OR into trace flags."""
     ctx.set_trace_config(int(cfg["block"]), int(cfg["rays_per_lane"]))
+    ctx.set_smem_levels(int(cfg.get("smem_levels", 0)))
     return order_flag(cfg)
 
 
@@ -167,7 +172,7 @@ def tune_batch(ctx: Context, items, flags: int = TRACE_DEFAULT, reps: int = 3, b
                 e[1].record(st)
                 evs.append(e)
         torch.cuda.synchronize()
-        table.append({"block": b, "rays_per_lane": r, "order": o, "cull": c,
+        table.append({"block": b, "rays_per_lane": r, "smem_levels": 0, "order": o, "cull": c,
                       "ms": float(np.median([a.elapsed_time(z) for a, z in evs[1:]]))})
     ctx.set_trace_config(*old)
     best = min(table, key=lambda x: x["ms"])

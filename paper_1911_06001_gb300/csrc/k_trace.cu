@@ -62,6 +62,9 @@ struct TraceLaunchT {
   int32_t mbox_words;    // grid walk: words of each thread's tested-part bitset (max parts / 32)
   int32_t block;         // threads per block of the trace kernel: 64, 128 or 256
   int32_t rays_per_lane; // rays per lane in a warp's tile (tile = 32 * rays_per_lane rays)
+  const int2 *top;       // one_scene: per part (first, count) of its top-level nodes staged in shared memory
+  int32_t top_nodes;     // staged nodes per block (0: none)
+  int32_t top_levels;    // levels staged of every part
 };
 
 namespace {
@@ -328,9 +331,26 @@ struct Counters {
 // tmin/tmax are in that shifted parameter.  State S is CertState (the
 // certified search: leaves give entry bounds) or HybridState (the FP64 pass's
 // re-trace: every leaf reached is decided by leaf_entry64).
+// Node descriptor idx of a part: the first ntop come from the block's
+// shared-memory copy of the part's top levels, the rest from global memory.
+// Descriptor idx, a node of level `lev`, of a part.  The node array is
+// breadth first, so the nodes of the top `top_levels` levels are its first
+// ones; those come from the block's shared-memory copy at address `top`
+// (32-bit shared address of the part's first staged node), the rest from
+// global memory.
+__device__ __forceinline__ uint2 node_at(const uint2 *__restrict__ nodes, uint32_t top, int top_levels, int lev,
+                                         uint32_t idx) {
+  if (top_levels > 0 && lev < top_levels) {  // folds away where top_levels is the constant 0
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(top + 8u * idx));
+    return v;
+  }
+  return __ldg(&nodes[idx]);
+}
+
 template <typename R, typename S, bool STATS, int STRIDE>
 __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
-                                             int D, R ox, R oy,
+                                             uint32_t top, int top_levels, int D, R ox, R oy,
                                              R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, R tshift, uint32_t part,
                                              const Tables *__restrict__ tab, S &st, Contenders *con,
                                              unsigned int &err, Counters &cnt) {
@@ -370,7 +390,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
 
   int level = 0;
   uint32_t px = 0, py = 0, pz = 0;
-  uint2 desc = __ldg(&nodes[0]);
+  uint2 desc = node_at(nodes, top, top_levels, 0, 0u);
   if (STATS) ++cnt.nodes;
   // While-while loop: lanes of a warp descend together, then pop together
   // (a lane that has to pop waits for the others to finish descending).
@@ -456,7 +476,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
         err |= kErrNodeIndex;
         return;
       }
-      desc = __ldg(&nodes[idx]);
+      desc = node_at(nodes, top, top_levels, level + 1, idx);
       if (STATS) ++cnt.nodes;
       const uint32_t m = k ^ mir;
       px = 2u * px + (m & 1u);
@@ -493,7 +513,7 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
         err |= kErrNodeIndex;
         return;
       }
-      desc = __ldg(&nodes[idx]);
+      desc = node_at(nodes, top, top_levels, level + 1, idx);
       if (STATS) ++cnt.nodes;
       const uint32_t m = k ^ mir;
       px = 2u * px + (m & 1u);
@@ -566,10 +586,14 @@ __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
 //   q - c and Ainv (q-c)   5u ||Ainv||_inf ||q - c||_inf, c' rounding u |c'|
 //   mirroring, slabs      u (4 |o'| + 3)
 //   FP32 direction        4u ||Ainv||_inf (|c - q|_1 + r)
+// stop: shared-memory address of the block's staged top-level nodes, of
+// which each part has its top `top_levels` levels (pa.spare0 carries, as
+// bits, the part's first staged node; 0 levels when nothing is staged).
 template <bool STATS, typename S = CertState, int STRIDE = kBlock>
 __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
-                                               uint32_t part, const Tables *tab, uint2 *stk, S &st,
-                                               Contenders *con, unsigned int &err, Counters &cnt) {
+                                               uint32_t part, const Tables *tab, uint32_t stop, int top_levels,
+                                               uint2 *stk, S &st, Contenders *con, unsigned int &err,
+                                               Counters &cnt) {
   const float4 a = ph.r0, b = ph.r1, c = ph.r2;
   const float4 s = ph.sphere;
   const float qx = fmaf(tref, r.dx, r.ox), qy = fmaf(tref, r.dy, r.oy), qz = fmaf(tref, r.dz, r.oz);
@@ -589,8 +613,9 @@ __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph,
       kU * (2.0f * pa.n_ainv * (qn + 5.0f * vn + 4.0f * (v1 + fabsf(s.w))) + 2.0f * cn + 8.0f * on + 6.0f) * 1.001f;
   const float tmin_rel = __fsub_rd(r.tmin, tref), tmax_rel = __fsub_ru(r.tmax, tref);
   if (STATS) ++cnt.parts_entered;
-  descend_part<float, S, STATS, STRIDE>(stk, pa.nodes, pa.n_nodes, pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel,
-                                        tmax_rel, eta, tref, part, tab, st, con, err, cnt);
+  descend_part<float, S, STATS, STRIDE>(stk, pa.nodes, pa.n_nodes, stop + 8u * __float_as_uint(pa.spare0), top_levels,
+                                        pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel, eta, tref, part, tab,
+                                        st, con, err, cnt);
 }
 
 // Insert (t, p) into the sorted register list (ct, cp); the displaced largest
@@ -632,8 +657,9 @@ template <bool STATS, int BLOCK>
 __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGrid &g,
                                           const int32_t *__restrict__ cstart, const int32_t *__restrict__ cparts,
                                           const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
-                                          const Tables *tab, uint2 *stk, uint32_t *mbox, int mwords, CertState &st,
-                                          Contenders &con, unsigned int &err, Counters &cnt) {
+                                          const Tables *tab, uint32_t stop, int top_levels, uint2 *stk, uint32_t *mbox,
+                                          int mwords, CertState &st, Contenders &con, unsigned int &err,
+                                          Counters &cnt) {
   const int G = g.G;
   const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
   bool ok = true, walking = go;
@@ -713,8 +739,8 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGri
 #pragma unroll 1
     for (int i = 0; i < kCap && __any_sync(0xffffffffu, ct[0] != Num<float>::inf()); ++i) {
       if (ct[0] != Num<float>::inf() && ct[0] <= prune_bound(st, r.tmax))
-        trace_part_f32<STATS, CertState, BLOCK>(r, hot[cp[0]], aux[cp[0]], ce[0], (uint32_t)cp[0], tab, stk, st,
-                                                &con, err, cnt);
+        trace_part_f32<STATS, CertState, BLOCK>(r, hot[cp[0]], aux[cp[0]], ce[0], (uint32_t)cp[0], tab, stop,
+                                                top_levels, stk, st, &con, err, cnt);
 #pragma unroll
       for (int j = 0; j < kCap - 1; ++j) {
         ct[j] = ct[j + 1];
@@ -755,7 +781,9 @@ template <bool STATS, int BLOCK, bool GRID>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
-                              uint2 *stk, CertState &st, Contenders &con, unsigned int &err, Counters &cnt,
+                              uint32_t stop, int top_levels, uint2 *stk, CertState &st, Contenders &con,
+                              unsigned int &err,
+                              Counters &cnt,
                               bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused,
                               const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords) {
   reused = false;
@@ -777,8 +805,8 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
     if (GRID && grid != nullptr && grid->valid != 0) {  // warp-uniform: one item per warp
       // a ray the walk cannot take safely goes on to the cluster level below
       const SceneGrid &g = *grid;
-      const bool walked = grid_walk<STATS, BLOCK>(r, need, g, g.cell_start, g.cell_parts, hot, aux, tab, stk, mbox,
-                                                  mwords, st, con, err, cnt);
+      const bool walked = grid_walk<STATS, BLOCK>(r, need, g, g.cell_start, g.cell_parts, hot, aux, tab, stop,
+                                                  top_levels, stk, mbox, mwords, st, con, err, cnt);
       if (STATS && need && walked) ++cnt.passes;
       need = need && !walked;
     }
@@ -848,7 +876,8 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
             stopped = true;
             break;
           }
-          trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], eta, (uint32_t)p, tab, stk, st, &con, err, cnt);
+          trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], eta, (uint32_t)p, tab, stop, top_levels, stk,
+                                                  st, &con, err, cnt);
           last_t = tin;
           last_p = p;
         }
@@ -864,7 +893,8 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       const bool h = part_cull(r, hot[p], tin, tref);
       if (cull && !h) continue;
       // the plain trace descends every part, even one whose sphere is missed
-      trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stk, st, &con, err, cnt);
+      trace_part_f32<STATS, CertState, BLOCK>(r, hot[p], aux[p], tref, (uint32_t)p, tab, stop, top_levels, stk, st,
+                                              &con, err, cnt);
     }
   }
 }
@@ -910,7 +940,10 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
 // REUSE: hit buffer reuse compiled in (a separate instantiation, so that the
 // common kernel carries none of its registers or tests).
 // GRID: the scene-level grid walk compiled in (likewise).
-template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID>
+// TOP: the top levels of every part staged in shared memory (a separate
+// instantiation: the staged-node base is one more live register, which the
+// common kernel does not carry).
+template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID, bool TOP = false>
 __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
@@ -922,16 +955,31 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
-  uint32_t *sMbox = reinterpret_cast<uint32_t *>(sOrd + sp) + threadIdx.x;  // word-major, stride BLOCK
+  uint2 *sTop = reinterpret_cast<uint2 *>(sOrd + sp + (sp & 1));  // 8-byte aligned: sOrd starts so
+  const int ntop_all = (TOP && L.one_scene) ? L.top_nodes : 0;
+  uint32_t *sMbox = reinterpret_cast<uint32_t *>(sTop + ntop_all) + threadIdx.x;  // word-major, stride BLOCK
+  const uint32_t sTopAddr = (uint32_t)__cvta_generic_to_shared(sTop);
   load_tables(tab);
   if (L.one_scene) {
     const TraceItem &I0 = L.items[0];
     for (int i = threadIdx.x; i < I0.n_parts; i += BLOCK) {
       sHot[i] = I0.hot[i];
-      sAux[i] = I0.aux[i];
+      PartAux a = I0.aux[i];
+      if (ntop_all > 0) {
+        const int2 t = L.top[i];
+        a.spare0 = __uint_as_float((uint32_t)t.x);
+        a.spare1 = __uint_as_float((uint32_t)t.y);  // count (the kernel needs only the first)
+      }
+      sAux[i] = a;
       sOrd[i] = I0.order[i];
     }
     for (int i = threadIdx.x; i < I0.n_clusters; i += BLOCK) sCl[i] = I0.clusters[i];
+    // every part's top levels: breadth first, they are the first nodes of its array
+    for (int p = 0; p < I0.n_parts && ntop_all > 0; ++p) {
+      const int2 t = L.top[p];
+      const uint2 *src = I0.aux[p].nodes;
+      for (int k = threadIdx.x; k < t.y; k += BLOCK) sTop[t.x + k] = __ldg(&src[k]);
+    }
   }
   __syncthreads();  // the only block barrier: warps then take tiles independently
   unsigned int err = 0;
@@ -1007,8 +1055,9 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
       const bool reuse = REUSE && active;
       const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
-      trace_ray_f32<STATS, BLOCK, GRID>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sStack, st, con, err,
-                                        cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr, sMbox,
+      trace_ray_f32<STATS, BLOCK, GRID>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sTopAddr,
+                                        (TOP && ntop_all > 0) ? L.top_levels : 0, sStack, st, con,
+                                        err, cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr, sMbox,
                                         L.mbox_words);
       bool flagged = false, ids_ok = true;
       uint32_t tbound = 0;  // T_REFINED: the certified error exponent, biased (flag bits 8-15)
@@ -1185,8 +1234,8 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
       float tin, tref;
       if (part_cull(r, I.hot[p], tin, tref) && !(tin > __double2float_ru(fmin(best, hs.ex.t)))) {
         hs.inv64 = I.inv64 + 12 * p;
-        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, stk_local, hs, nullptr,
-                                              err, cnt);
+        trace_part_f32<false, HybridState, 1>(r, I.hot[p], I.aux[p], tref, (uint32_t)p, tab, 0u, 0, stk_local, hs,
+                                              nullptr, err, cnt);
       }
     }
     double bb = hs.ex.t;
@@ -1270,9 +1319,10 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   if (err) atomicOr(L.err, err);
 }
 
-size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, int mbox_words) {
+size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, int mbox_words, int top_nodes) {
   return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
-         clusters * sizeof(Cluster) + parts * sizeof(int32_t) + (size_t)mbox_words * block * sizeof(uint32_t);
+         clusters * sizeof(Cluster) + (parts + (parts & 1)) * sizeof(int32_t) + (size_t)top_nodes * sizeof(uint2) +
+         (size_t)mbox_words * block * sizeof(uint32_t);
 }
 
 // Resident blocks per SM of a trace kernel at a dynamic shared-memory size.
@@ -1333,11 +1383,17 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
     for (int i = 0; i < L.n_items; ++i) any = any || L.items[i].grid != nullptr;
     walk = any;
   }
+  // the staged top levels only in the common kernel (counting, reuse and grid traces give the same
+  // results without them)
+  const bool top = L.one_scene && L.top_nodes > 0 && !stats && !reuse && !walk;
   const size_t smem = trace_smem_bytes(L.stack_levels, L.one_scene ? L.items[0].n_parts : 0,
-                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK, walk ? L.mbox_words : 0);
+                                       L.one_scene ? L.items[0].n_clusters : 0, BLOCK, walk ? L.mbox_words : 0,
+                                       top ? L.top_nodes : 0);
   auto kern = walk ? (stats ? k_trace<NI, true, BLOCK, false, true> : k_trace<NI, false, BLOCK, false, true>)
               : stats ? (reuse ? k_trace<NI, true, BLOCK, true, false> : k_trace<NI, true, BLOCK, false, false>)
-                      : (reuse ? k_trace<NI, false, BLOCK, true, false> : k_trace<NI, false, BLOCK, false, false>);
+              : reuse ? k_trace<NI, false, BLOCK, true, false>
+              : top   ? k_trace<NI, false, BLOCK, false, false, true>
+                      : k_trace<NI, false, BLOCK, false, false>;
   int per_sm = 0;
   const cudaError_t e = blocks_per_sm(kern, BLOCK, smem, per_sm);
   if (e != cudaSuccess) return e;
@@ -1389,6 +1445,9 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   dst.err = src.err;
   dst.block = src.block;
   dst.rays_per_lane = src.rays_per_lane < 1 ? 1 : src.rays_per_lane;
+  dst.top = src.top;
+  dst.top_nodes = (dst.one_scene && src.top) ? src.top_nodes : 0;
+  dst.top_levels = dst.top_nodes > 0 ? src.top_levels : 0;
 }
 
 }  // namespace

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -55,6 +56,7 @@ struct AssetRec {
   uint2 *d_nodes = nullptr;
   uint32_t *d_rgb = nullptr;
   float box_lo[3] = {0.f, 0.f, 0.f}, box_hi[3] = {0.f, 0.f, 0.f};  // occupied leaves, local units
+  uint32_t top_nodes[kMaxSmemLevels + 1] = {};  // interior nodes in its top 0..kMaxSmemLevels levels
   int refs = 0;
 };
 
@@ -91,6 +93,7 @@ struct svo_ctx {
   int n_sm = 1;
   int block = 128;         // trace kernel block size
   int rays_per_lane = 1;   // warp tile = 32 * rays_per_lane rays (1: finest load balance)
+  int smem_levels = 0;     // top octree levels staged in shared memory by one-scene traces
   std::mutex mu;
   std::vector<AssetRec> assets;
   std::unordered_set<svo_scene *> scenes;
@@ -117,6 +120,8 @@ struct svo_scene {
   uint8_t *d_dirty = nullptr;  // per part: world pose changed since the scene's previous trace
   SceneGrid *d_grid = nullptr;  // scene-level grid header, cell starts and part lists
   int32_t *d_cell_start = nullptr, *d_cell_parts = nullptr;
+  int2 *d_top = nullptr;  // [kMaxSmemLevels][P] (first, count) of each part's top-level nodes
+  size_t top_total[kMaxSmemLevels + 1] = {};  // staged nodes of all parts, per level count
   double *h_stage = nullptr;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
@@ -168,6 +173,14 @@ svo_status get_slot(svo_ctx *ctx, void *stream, unsigned long long need, Slot **
   return SVO_OK;
 }
 
+// The launch record of trace_rays / trace_batch (about 16 KB): one per host
+// thread, allocated on its first trace, so no call allocates it afresh.
+TraceLaunch &launch_record() {
+  thread_local std::unique_ptr<TraceLaunch> p;
+  if (!p) p.reset(new TraceLaunch());
+  return *p;
+}
+
 TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, uint32_t *flags) {
   TraceItem it;
   it.hot = s->d_hot;
@@ -192,9 +205,27 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   return it;
 }
 
+// Top levels of a one-scene launch staged in shared memory: the most levels
+// up to the context's setting whose nodes fit kTopCapBytes.
+void set_top_levels(svo_ctx *ctx, const svo_scene *only, TraceLaunch &L) {
+  L.top = nullptr;
+  L.top_nodes = 0;
+  L.top_levels = 0;
+  if (!only || only->P > 256) return;  // the trace kernel stages part tables up to 256 parts
+  for (int l = ctx->smem_levels; l >= 1; --l) {
+    if (only->top_total[l] * sizeof(uint2) <= kTopCapBytes && only->top_total[l] > 0) {
+      L.top = only->d_top + (size_t)(l - 1) * only->P;
+      L.top_nodes = (int32_t)only->top_total[l];
+      L.top_levels = l;
+      return;
+    }
+  }
+}
+
 // bounds[i]: scene bound of item i (frame of origin-based ray ordering).
+// only: the scene every item traces, or nullptr (items of several scenes).
 svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays, const float4 *const *bounds,
-                     void *stream) {
+                     const svo_scene *only, void *stream) {
   constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
   if ((L.flags & SVO_TRACE_REUSE) && (L.flags & kReuseNeeds) != kReuseNeeds)
     return fail(SVO_ERR_ARG, "SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
@@ -249,6 +280,7 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.err = ctx->d_err;
   L.block = ctx->block;
   L.rays_per_lane = ctx->rays_per_lane;
+  set_top_levels(ctx, only, L);
   CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
   if (L.flags & SVO_TRACE_GRID) {
     GridLaunch gl;
@@ -375,6 +407,20 @@ svo_status svo_set_trace_config(svo_ctx *ctx, int32_t block, int32_t rays_per_la
   return ok();
 }
 
+svo_status svo_set_smem_levels(svo_ctx *ctx, int32_t levels) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_set_smem_levels: ctx is NULL");
+  if (levels < 0 || levels > kMaxSmemLevels)
+    return fail(SVO_ERR_ARG, "svo_set_smem_levels: %d levels (0..%d)", levels, kMaxSmemLevels);
+  ctx->smem_levels = levels;
+  return ok();
+}
+
+svo_status svo_get_smem_levels(svo_ctx *ctx, int32_t *levels) {
+  if (!ctx || !levels) return fail(SVO_ERR_ARG, "svo_get_smem_levels: NULL argument");
+  *levels = ctx->smem_levels;
+  return ok();
+}
+
 svo_status svo_get_trace_config(svo_ctx *ctx, int32_t *block, int32_t *rays_per_lane) {
   if (!ctx) return fail(SVO_ERR_ARG, "svo_get_trace_config: ctx is NULL");
   if (block) *block = ctx->block;
@@ -418,6 +464,8 @@ svo_status svo_upload(svo_ctx *ctx, const svo_desc *d, svo_handle *out) {
   a.depth = b.depth;
   a.n_nodes = b.n_nodes;
   a.n_leaves = b.n_leaves;
+  for (int l = 0; l <= kMaxSmemLevels; ++l)  // breadth first: the top l levels are the first nodes
+    a.top_nodes[l] = (uint32_t)(b.n_nodes ? b.level_start[l < b.depth ? l : b.depth] : 0);
   for (int k = 0; k < 3; ++k) {
     a.box_lo[k] = (float)std::ldexp((double)b.box_lo[k], -b.depth);
     a.box_hi[k] = (float)std::ldexp((double)b.box_hi[k], -b.depth);
@@ -499,11 +547,13 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
     level[i] = parent[i] < 0 ? 0 : level[parent[i]] + 1;
   }
   std::vector<PartStatic> stat(n_parts);
+  std::vector<uint32_t> top_cnt((size_t)(kMaxSmemLevels + 1) * n_parts, 0u);
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     for (int i = 0; i < n_parts; ++i) {
       AssetRec *a = find_asset(ctx, asset[i]);
       if (!a) return fail(SVO_ERR_HANDLE, "scene_create: part %d: unknown asset %u", i, asset[i]);
+      for (int l = 0; l <= kMaxSmemLevels; ++l) top_cnt[(size_t)l * n_parts + i] = a->top_nodes[l];
       stat[i].nodes = a->d_nodes;
       stat[i].n_nodes = (uint32_t)a->n_nodes;
       stat[i].depth = a->depth;
@@ -545,7 +595,8 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   // for about 32 cells per part
   const int grid_G = grid_cells_per_axis(P);
   const int grid_cap = grid_G > 0 ? 32 * P + grid_G * grid_G * grid_G : 0;
-  size_t off_grid = al(off_dirty + P);
+  size_t off_top = al(off_dirty + P);
+  size_t off_grid = al(off_top + (size_t)kMaxSmemLevels * P * sizeof(int2));
   size_t off_cstart = al(off_grid + sizeof(SceneGrid));
   size_t off_cparts = al(off_cstart + (grid_G > 0 ? (size_t)(grid_G * grid_G * grid_G + 1) * sizeof(int32_t) : 0));
   size_t total = al(off_cparts + (size_t)grid_cap * sizeof(int32_t));
@@ -578,6 +629,17 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   s->d_grid = reinterpret_cast<SceneGrid *>(s->d_mem + off_grid);
   s->d_cell_start = reinterpret_cast<int32_t *>(s->d_mem + off_cstart);
   s->d_cell_parts = reinterpret_cast<int32_t *>(s->d_mem + off_cparts);
+  s->d_top = reinterpret_cast<int2 *>(s->d_mem + off_top);
+  std::vector<int2> top((size_t)kMaxSmemLevels * P);
+  for (int l = 1; l <= kMaxSmemLevels; ++l) {
+    size_t first = 0;
+    for (int i = 0; i < P; ++i) {
+      const uint32_t c = top_cnt[(size_t)l * P + i];
+      top[(size_t)(l - 1) * P + i] = make_int2((int)first, (int)c);
+      first += c;
+    }
+    s->top_total[l] = first;
+  }
   s->grid_G = grid_G;
   s->grid_cap = grid_cap;
   std::vector<double> ident(P * 12, 0.0);
@@ -598,6 +660,7 @@ svo_status scene_create(svo_ctx *ctx, int32_t n_parts, const svo_handle *asset, 
   if (e == cudaSuccess) e = cudaMemset(s->d_world, 0xFF, P * 12 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s->d_dirty, 1, P);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_stat, stat.data(), P * sizeof(PartStatic), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_top, top.data(), top.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_level_order, lorder.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_level_start, lstart.data(), (L + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -791,16 +854,14 @@ svo_status trace_rays(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits
   if (n >= (1ull << 40)) return fail(SVO_ERR_LIMIT, "trace_rays: %llu rays", (unsigned long long)n);
   if ((flags & SVO_TRACE_STATS) && !stats) return fail(SVO_ERR_ARG, "trace_rays: STATS without stats buffer");
   CK(cudaSetDevice(s->ctx->device));
-  TraceLaunch *L = new TraceLaunch();
+  TraceLaunch *L = &launch_record();
   L->items[0] = make_item(s, rays, n, hits, ray_flags);
   if (flags & SVO_TRACE_IMAGE_TILES) L->items[0].width = flags >> 16;
   L->n_items = 1;
   L->flags = flags;
   L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
   const float4 *bounds[1] = {s->d_bound};
-  svo_status rc = run_trace(s->ctx, *L, n, bounds, stream);
-  delete L;
-  return rc;
+  return run_trace(s->ctx, *L, n, bounds, s, stream);
 }
 
 svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_items, uint32_t flags,
@@ -811,42 +872,34 @@ svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_item
   CK(cudaSetDevice(ctx->device));
   for (int b = 0; b < n_items; b += kMaxBatchItems) {
     const int cnt = (n_items - b) < kMaxBatchItems ? (n_items - b) : kMaxBatchItems;
-    TraceLaunch *L = new TraceLaunch();
+    TraceLaunch *L = &launch_record();
     L->n_items = 0;
     unsigned long long total = 0;
     const float4 *bounds[kMaxBatchItems];
+    svo_scene *only = nullptr;
+    bool one = true;
     for (int i = 0; i < cnt; ++i) {
       const svo_batch_item &it = items[b + i];
-      if (!it.scene) {
-        delete L;
-        return fail(SVO_ERR_ARG, "trace_batch: item %d has no scene", b + i);
-      }
-      if (it.scene->ctx != ctx) {
-        delete L;
-        return fail(SVO_ERR_ARG, "trace_batch: item %d belongs to another context", b + i);
-      }
+      if (!it.scene) return fail(SVO_ERR_ARG, "trace_batch: item %d has no scene", b + i);
+      if (it.scene->ctx != ctx) return fail(SVO_ERR_ARG, "trace_batch: item %d belongs to another context", b + i);
       if (it.n == 0) continue;
       if (!it.rays || !it.hits || (reinterpret_cast<uintptr_t>(it.rays) & 15) ||
-          (reinterpret_cast<uintptr_t>(it.hits) & 15)) {
-        delete L;
+          (reinterpret_cast<uintptr_t>(it.hits) & 15))
         return fail(SVO_ERR_ARG, "trace_batch: item %d rays/hits NULL or not 16-byte aligned", b + i);
-      }
       TraceItem ti = make_item(it.scene, it.rays, it.n, it.hits, it.ray_flags);
       ti.width = it.image_width;
       total += it.n;
       bounds[L->n_items] = it.scene->d_bound;
       L->items[L->n_items++] = ti;
+      one = one && (only == nullptr || only == it.scene);
+      only = it.scene;
     }
     if (L->n_items > 0) {
       L->flags = flags;
       L->stats = (flags & SVO_TRACE_STATS) ? stats : nullptr;
-      svo_status rc = run_trace(ctx, *L, total, bounds, stream);
-      if (rc != SVO_OK) {
-        delete L;
-        return rc;
-      }
+      svo_status rc = run_trace(ctx, *L, total, bounds, one ? only : nullptr, stream);
+      if (rc != SVO_OK) return rc;
     }
-    delete L;
   }
   return ok();
 }

@@ -124,6 +124,7 @@ int build_octree(int depth, uint64_t n_in, const uint64_t *ids, const uint32_t *
     }
   }
   out->n_nodes = n_nodes;
+  out->level_start = offset;
   return SVO_OK;
 }
 

@@ -17,6 +17,8 @@ constexpr int kMaxClusters = kMaxParts / kClusterSize;
 constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
 constexpr int kContenders = 8;                  // contender leaves kept per flagged ray
 constexpr int kInlinePoseParts = 256;           // poses up to this many parts go by kernel parameter
+constexpr int kMaxSmemLevels = 4;               // top octree levels a trace block may stage in shared memory
+constexpr size_t kTopCapBytes = 16384;          // at most this many bytes of staged top-level nodes per block
 
 // Device error word bits (svo_check_device reports them).
 constexpr unsigned int kErrNodeIndex = 1u;      // a child index fell outside the node array
@@ -47,7 +49,9 @@ struct PartHot {
   float4 sphere;
 };
 
-// Per-frame scalars of a part (32 B).
+// Per-frame scalars of a part (32 B).  In a trace block's shared-memory
+// copy, spare0 / spare1 carry (as bits) the first and the count of the part's
+// nodes staged in shared memory; in global memory both are 0.
 struct PartAux {
   const uint2 *nodes;
   uint32_t n_nodes;
@@ -147,6 +151,9 @@ struct TraceLaunch {
   unsigned int *err;
   int32_t block;          // trace kernel block size: 64, 128 or 256
   int32_t rays_per_lane;  // warp tile = 32 * rays_per_lane rays
+  const int2 *top;        // per part (first, count) of its staged top-level nodes, or nullptr
+  int32_t top_nodes;      // nodes staged in shared memory per block (0: none)
+  int32_t top_levels;     // the top levels of every part that are staged
 };
 
 // Kernel launchers (k_trace.cu, k_refit.cu).

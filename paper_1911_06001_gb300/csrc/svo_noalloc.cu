@@ -133,6 +133,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->fix_cand = reinterpret_cast<uint4 *>(base + kCounterBytes + kFixBytes);
   L->cand_capacity = kCandRays;
   L->err = scene_err_word(s);
+  L->top = nullptr;  // no shared-memory top levels on this path
+  L->top_nodes = 0;
+  L->top_levels = 0;
   // clear what the kernels expect at zero: the tile counter and the list count
   e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess && (flags & SVO_TRACE_GRID)) {

@@ -53,6 +53,43 @@ def test_every_launch_shape_gives_identical_hits(ctx):
         ctx.set_trace_config(128, 3)
 
 
+def test_shared_memory_top_levels_give_identical_hits(ctx):
+    """Staging the top octree levels of every part in shared memory (0-4
+    levels; a depth-9 scene of 16 parts and PR1's four depth-6 parts; a batch
+    of one scene too) changes only where node descriptors are read from."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    fig = synthetic.articulated_figure(depth=9)
+    art = GpuScene(ctx, fig.scene)
+    art.set_pose(fig.pose(12))
+    pr1 = GpuScene(ctx, synthetic.pr1_scene())
+    cases = [(art, fig.rays(400, 225), g.trace_image(400)), (pr1, synthetic.pr1_rays(pr1.scene), 0)]
+    ctx.set_trace_config(128, 1)
+    assert ctx.smem_levels() == 0
+    for gs, rays, img in cases:
+        ref = gs.trace(rays, g.TRACE_DEFAULT | img)
+        assert (ref["part"] != 0xFFFFFFFF).sum() > 1000
+        for levels in (1, 2, 3, 4):
+            ctx.set_smem_levels(levels)
+            _same(gs.trace(rays, g.TRACE_DEFAULT | img), ref)
+            # a batch whose items all trace this scene stages the same levels
+            r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
+            h = torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda")
+            f = torch.zeros(r.shape[0], dtype=torch.int32, device="cuda")
+            ctx.trace_batch([(gs.sc, r[:5000], h[:5000], f[:5000]), (gs.sc, r[5000:], h[5000:], f[5000:])],
+                            flags=g.TRACE_DEFAULT)
+            torch.cuda.synchronize()
+            got = g.decode_hits(h)
+            got["flags"] = f.cpu().numpy().astype(np.uint32)
+            _same(got, ref)
+        ctx.set_smem_levels(0)
+    with pytest.raises(g.SvoError):
+        ctx.set_smem_levels(5)
+    ctx.set_trace_config(128, 4)
+
+
 def test_image_tiles_give_identical_hits(ctx):
     """Warp tiles of 8 x 4*rays_per_lane pixels (rays given as a row-major
     image) on ragged widths and a ragged last row, alone and per batch item:
