@@ -28,7 +28,9 @@
 // the entry of child m is max(T0, max over axes in m of the mid-plane t), so
 // the order follows from sorting the three mid-plane t values; a per-block
 // table maps a child mask to that order.  A stack holds, per level, the
-// parent's descriptor and the children still to visit.
+// parent's descriptor, the children still to visit, the parent's entry T0 and
+// the entry of the next child to visit, so that popping past a child that
+// starts beyond the best hit is one load and one compare.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -349,11 +351,12 @@ __device__ __forceinline__ uint2 node_at(const uint2 *__restrict__ nodes, uint32
 }
 
 template <typename R, typename S, bool STATS, int STRIDE>
-__device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
+__device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
                                              uint32_t top, int top_levels, int D, R ox, R oy,
                                              R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, R tshift, uint32_t part,
                                              const Tables *__restrict__ tab, S &st, Contenders *con,
                                              unsigned int &err, Counters &cnt) {
+  static_assert(std::is_same<R, float>::value, "the stack stores FP32 entry parameters");
   if (n_nodes == 0) return;
   constexpr bool CERT = std::is_same<S, CertState>::value;
   constexpr bool HYBRID = std::is_same<S, HybridState>::value;
@@ -469,7 +472,15 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       }
       const int q = __ffs(hq) - 1;
       const uint32_t rest = hq & (hq - 1u);
-      stk[level * STRIDE] = make_uint2(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16));
+      // the entry of the child visited after this one (if any), kept with the
+      // node so that a pop past it needs no plane arithmetic
+      R en = Num<R>::inf();
+      if (rest) {
+        const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
+        en = fmax(T0, ax == 0 ? Bx : (ax == 1 ? By : Bz));
+      }
+      stk[level * STRIDE] = make_uint4(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16), __float_as_uint(en),
+                                       __float_as_uint(T0));
       const uint32_t k = kt[p * 8 + q];
       const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
       if (idx >= n_nodes) {
@@ -490,22 +501,25 @@ __device__ __forceinline__ void descend_part(uint2 *__restrict__ stk, const uint
       px >>= 1;
       py >>= 1;
       pz >>= 1;
-      const uint2 e = stk[level * STRIDE];
+      const uint4 e = stk[level * STRIDE];
       uint32_t rest = (e.y >> 8) & 0xFFu;
       if (rest == 0u) continue;
+      // the next child's entry, max(T0, mid-plane t of its highest-ranked
+      // axis), was stored when the node was pushed
+      if (__uint_as_float(e.z) > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
       const int q = __ffs(rest) - 1;
       rest &= rest - 1u;
       const int p = (int)(e.y >> 16);
-      // entry of the next child: max(T0, mid-plane t of its highest-ranked axis)
-      const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
-      const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
-      const R T0 = fmax(fmax(Slab<R>::t(lx - eta, ix, ox, bx), Slab<R>::t(ly - eta, iy, oy, by)), fmax(Slab<R>::t(lz - eta, iz, oz, bz), tmin));
-      const int rank = 31 - __clz(q);
-      const int ax = (int)((kAxisOrder >> (6 * p + 2 * rank)) & 3ull);
-      const R Bsel = ax == 0 ? Slab<R>::t((lx + h) - eta, ix, ox, bx) : (ax == 1 ? Slab<R>::t((ly + h) - eta, iy, oy, by) : Slab<R>::t((lz + h) - eta, iz, oz, bz));
-      const R en = fmax(T0, Bsel);
-      if (en > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
-      stk[level * STRIDE].y = (e.y & ~0xFF00u) | (rest << 8);
+      R en = Num<R>::inf();
+      if (rest) {  // the entry of the child after it
+        const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
+        const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
+        const R Bsel = ax == 0   ? Slab<R>::t((R(px) * sz + h) - eta, ix, ox, bx)
+                       : ax == 1 ? Slab<R>::t((R(py) * sz + h) - eta, iy, oy, by)
+                                 : Slab<R>::t((R(pz) * sz + h) - eta, iz, oz, bz);
+        en = fmax(__uint_as_float(e.w), Bsel);
+      }
+      stk[level * STRIDE] = make_uint4(e.x, (e.y & ~0xFF00u) | (rest << 8), __float_as_uint(en), e.w);
       const uint32_t k = kt[p * 8 + q];
       const uint32_t cmask = e.y & 0xFFu;
       const uint32_t idx = e.x + __popc(cmask & ((1u << k) - 1u));
@@ -592,7 +606,7 @@ __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
 template <bool STATS, typename S = CertState, int STRIDE = kBlock>
 __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
                                                uint32_t part, const Tables *tab, uint32_t stop, int top_levels,
-                                               uint2 *stk, S &st, Contenders *con, unsigned int &err,
+                                               uint4 *stk, S &st, Contenders *con, unsigned int &err,
                                                Counters &cnt) {
   const float4 a = ph.r0, b = ph.r1, c = ph.r2;
   const float4 s = ph.sphere;
@@ -657,7 +671,7 @@ template <bool STATS, int BLOCK>
 __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGrid &g,
                                           const int32_t *__restrict__ cstart, const int32_t *__restrict__ cparts,
                                           const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
-                                          const Tables *tab, uint32_t stop, int top_levels, uint2 *stk, uint32_t *mbox,
+                                          const Tables *tab, uint32_t stop, int top_levels, uint4 *stk, uint32_t *mbox,
                                           int mwords, CertState &st, Contenders &con, unsigned int &err,
                                           Counters &cnt) {
   const int G = g.G;
@@ -781,7 +795,7 @@ template <bool STATS, int BLOCK, bool GRID>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
-                              uint32_t stop, int top_levels, uint2 *stk, CertState &st, Contenders &con,
+                              uint32_t stop, int top_levels, uint4 *stk, CertState &st, Contenders &con,
                               unsigned int &err,
                               Counters &cnt,
                               bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused,
@@ -948,10 +962,10 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
   extern __shared__ __align__(16) unsigned char smem[];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
-  uint2 *sStack = reinterpret_cast<uint2 *>(smem + kTablesBytes) + threadIdx.x;
+  uint4 *sStack = reinterpret_cast<uint4 *>(smem + kTablesBytes) + threadIdx.x;
   const int sp = L.one_scene ? L.items[0].n_parts : 0;
   const int sc = L.one_scene ? L.items[0].n_clusters : 0;
-  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * BLOCK * sizeof(uint2));
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * BLOCK * sizeof(uint4));
   PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
   Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
@@ -1226,7 +1240,7 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
   hs.ex.vox = kMissVoxel;
   hs.o = o;
   hs.d = make_float4(d.x, d.y, d.z, r.tmax);
-  uint2 stk_local[kMaxDepth];
+  uint4 stk_local[kMaxDepth];
   double best = Num<double>::inf();  // the warp's best hit t after each round
   for (int base = 0; base < I.n_parts; base += 32) {
     const int p = base + lane;
@@ -1320,7 +1334,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
 }
 
 size_t trace_smem_bytes(int stack_levels, int parts, int clusters, int block, int mbox_words, int top_nodes) {
-  return kTablesBytes + (size_t)stack_levels * block * sizeof(uint2) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
+  return kTablesBytes + (size_t)stack_levels * block * sizeof(uint4) + parts * (sizeof(PartHot) + sizeof(PartAux)) +
          clusters * sizeof(Cluster) + (parts + (parts & 1)) * sizeof(int32_t) + (size_t)top_nodes * sizeof(uint2) +
          (size_t)mbox_words * block * sizeof(uint32_t);
 }
