@@ -389,14 +389,16 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
   const uint32_t HZ = (mir & 4u) ? 0x0Fu : 0xF0u;
   const uint8_t *__restrict__ qt = &tab->q[mir][0][0];
   const uint8_t *__restrict__ kt = &tab->k[mir][0][0];
-  const uint32_t side = 1u << D;
 
   int level = 0;
   uint32_t px = 0, py = 0, pz = 0;
+  uint32_t live = 0;  // bit l: the stack entry of level l still has a child that may hold the closest hit
   uint2 desc = node_at(nodes, top, top_levels, 0, 0u);
   if (STATS) ++cnt.nodes;
   // While-while loop: lanes of a warp descend together, then pop together
-  // (a lane that has to pop waits for the others to finish descending).
+  // (a lane that has to pop waits for the others to finish descending).  A
+  // pop goes straight to the deepest level that still has a child to visit,
+  // so levels with nothing left cost no iteration.
   for (;;) {
     for (;;) {  // descend while the current node has children to visit
       const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
@@ -447,9 +449,9 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
           if (lo > rel_bound(st, tmax, tshift)) break;  // later leaves start even later
           if (STATS) ++cnt.leaves;
           const uint32_t vx = 2u * px + (m & 1u), vy = 2u * py + ((m >> 1) & 1u), vz = 2u * pz + ((m >> 2) & 1u);
-          const unsigned long long gx = (mir & 1u) ? (side - 1u - vx) : vx;
-          const unsigned long long gy = (mir & 2u) ? (side - 1u - vy) : vy;
-          const unsigned long long gz = (mir & 4u) ? (side - 1u - vz) : vz;
+          const unsigned long long gx = (mir & 1u) ? (((1u << D) - 1u) ^ vx) : vx;
+          const unsigned long long gy = (mir & 2u) ? (((1u << D) - 1u) ^ vy) : vy;
+          const unsigned long long gz = (mir & 4u) ? (((1u << D) - 1u) ^ vz) : vz;
           const unsigned long long vox = gx | (gy << D) | (gz << (2 * D));
           if constexpr (CERT) {
             const R clx = (m & 1u) ? lx + h : lx, cly = (m & 2u) ? ly + h : ly, clz = (m & 4u) ? lz + h : lz;
@@ -481,6 +483,7 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
       }
       stk[level * STRIDE] = make_uint4(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16), __float_as_uint(en),
                                        __float_as_uint(T0));
+      live = rest ? (live | (1u << level)) : (live & ~(1u << level));
       const uint32_t k = kt[p * 8 + q];
       const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
       if (idx >= n_nodes) {
@@ -495,20 +498,26 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
       pz = 2u * pz + ((m >> 2) & 1u);
       ++level;
     }
-    for (;;) {  // pop to the next sibling that may still hold the closest hit
-      if (level == 0) return;
-      --level;
-      px >>= 1;
-      py >>= 1;
-      pz >>= 1;
+    for (;;) {  // pop to the deepest level above that still has a child to visit
+      const uint32_t cand = live & ((1u << level) - 1u);
+      if (cand == 0u) return;
+      const int up = level - (31 - __clz(cand));
+      level -= up;
+      px >>= up;
+      py >>= up;
+      pz >>= up;
       const uint4 e = stk[level * STRIDE];
       uint32_t rest = (e.y >> 8) & 0xFFu;
-      if (rest == 0u) continue;
       // the next child's entry, max(T0, mid-plane t of its highest-ranked
-      // axis), was stored when the node was pushed
-      if (__uint_as_float(e.z) > rel_bound(st, tmax, tshift)) continue;  // this and all later siblings are too far
+      // axis), was stored when the node was pushed; past the bound, this and
+      // all later siblings are too far for good (the bound only shrinks)
+      if (__uint_as_float(e.z) > rel_bound(st, tmax, tshift)) {
+        live &= ~(1u << level);
+        continue;
+      }
       const int q = __ffs(rest) - 1;
       rest &= rest - 1u;
+      if (!rest) live &= ~(1u << level);
       const int p = (int)(e.y >> 16);
       R en = Num<R>::inf();
       if (rest) {  // the entry of the child after it
