@@ -50,8 +50,11 @@ typedef int32_t svo_status;
 #define SVO_ERR_OOM (-2)      /* device or host allocation failed */
 #define SVO_ERR_HANDLE (-3)   /* unknown or released asset handle / scene */
 #define SVO_ERR_CUDA (-4)     /* a CUDA runtime call failed (message has the CUDA error) */
-#define SVO_ERR_TIMEOUT (-5)  /* a bounded device wait gave up */
-#define SVO_ERR_ADMIT (-6)    /* request does not fit the memory budget */
+#define SVO_ERR_TIMEOUT (-5)  /* reserved: a request waited past its limit.  No call of this library
+                                 returns it today (no kernel waits on another); request queues built
+                                 on the library (the Python server) report timeouts themselves */
+#define SVO_ERR_ADMIT (-6)    /* reserved: a request does not fit the memory budget.  No call of this
+                                 library returns it today; admission is the server's host policy */
 #define SVO_ERR_NAN (-7)      /* NaN or infinity in a pose */
 #define SVO_ERR_SINGULAR (-8) /* a composed pose is not invertible */
 #define SVO_ERR_LIMIT (-9)    /* a size exceeds a documented library limit */
@@ -175,7 +178,10 @@ typedef struct {
 svo_status svo_ctx_create(int32_t device, svo_ctx **out);
 /* Release every asset, scene and buffer of the context.  NULL is allowed. */
 svo_status svo_ctx_destroy(svo_ctx *ctx);
-/* Thread-local message of the last failing call of this thread ("" if none). */
+/* Thread-local message of the last failing call of this thread ("" if none).
+ * It takes no context: a call can fail before any context exists (a NULL or
+ * bad context, svo_ctx_create itself), and one thread's message must not be
+ * overwritten by another thread's call on the same context. */
 const char *svo_last_error(void);
 /* Static name of a status code. */
 const char *svo_status_string(svo_status s);
