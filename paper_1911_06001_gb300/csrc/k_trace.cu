@@ -395,40 +395,41 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
   uint32_t live = 0;  // bit l: the stack entry of level l still has a child that may hold the closest hit
   uint2 desc = node_at(nodes, top, top_levels, 0, 0u);
   if (STATS) ++cnt.nodes;
-  // While-while loop: lanes of a warp descend together, then pop together
-  // (a lane that has to pop waits for the others to finish descending).  A
-  // pop goes straight to the deepest level that still has a child to visit,
-  // so levels with nothing left cost no iteration.
-  for (;;) {
-    for (;;) {  // descend while the current node has children to visit
-      const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
-      const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
-      const R tl = rel_bound(st, tmax, tshift);
-      const R Ax = Slab<R>::t(lx - eta, ix, ox, bx), Ay = Slab<R>::t(ly - eta, iy, oy, by), Az = Slab<R>::t(lz - eta, iz, oz, bz);
-      const R Bx = Slab<R>::t((lx + h) - eta, ix, ox, bx), By = Slab<R>::t((ly + h) - eta, iy, oy, by), Bz = Slab<R>::t((lz + h) - eta, iz, oz, bz);
-      const R Cx = INFLATE ? Slab<R>::t((lx + h) + eta, ix, ox, bx) : Bx;
-      const R Cy = INFLATE ? Slab<R>::t((ly + h) + eta, iy, oy, by) : By;
-      const R Cz = INFLATE ? Slab<R>::t((lz + h) + eta, iz, oz, bz) : Bz;
-      const R Ex = Slab<R>::t((lx + sz) + eta, ix, ox, bx), Ey = Slab<R>::t((ly + sz) + eta, iy, oy, by), Ez = Slab<R>::t((lz + sz) + eta, iz, oz, bz);
-      const R T0 = fmax(fmax(Ax, Ay), fmax(Az, tmin));
-      const R T1 = fmin(fmin(Ex, Ey), fmin(Ez, tl));
-      // child m (mirrored) is hit iff max(T0, B_i : i in m) <= min(T1, C_j : j not in m)
-      uint32_t hit = (T0 <= T1) ? 0xFFu : 0u;
-      hit &= (Bx <= T1) ? 0xFFu : ~HX;
-      hit &= (By <= T1) ? 0xFFu : ~HY;
-      hit &= (Bz <= T1) ? 0xFFu : ~HZ;
-      hit &= (Cx >= T0) ? 0xFFu : HX;
-      hit &= (Cy >= T0) ? 0xFFu : HY;
-      hit &= (Cz >= T0) ? 0xFFu : HZ;
-      hit &= (Bx <= Cy) ? 0xFFu : ~(HX & ~HY);
-      hit &= (Bx <= Cz) ? 0xFFu : ~(HX & ~HZ);
-      hit &= (By <= Cx) ? 0xFFu : ~(HY & ~HX);
-      hit &= (By <= Cz) ? 0xFFu : ~(HY & ~HZ);
-      hit &= (Bz <= Cx) ? 0xFFu : ~(HZ & ~HX);
-      hit &= (Bz <= Cy) ? 0xFFu : ~(HZ & ~HY);
-      const uint32_t cmask = desc.y & 0xFFu;
-      hit &= cmask;
-      if (hit == 0u) break;
+  // One loop, one node per iteration: every lane of the warp computes the
+  // child mask of its current node, then pushes and goes down, tests the
+  // leaves, or pops.  A pop goes straight to the deepest level that still has
+  // a child to visit, so levels with nothing left cost no iteration, and a
+  // lane that pops is at its next node in the same iteration as the lanes
+  // that descend (no lane waits for the others to finish a run of descents).
+  for (;;) {  // one node per iteration: its child mask, then a push, its leaves or a pop
+    const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
+    const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
+    const R tl = rel_bound(st, tmax, tshift);
+    const R Ax = Slab<R>::t(lx - eta, ix, ox, bx), Ay = Slab<R>::t(ly - eta, iy, oy, by), Az = Slab<R>::t(lz - eta, iz, oz, bz);
+    const R Bx = Slab<R>::t((lx + h) - eta, ix, ox, bx), By = Slab<R>::t((ly + h) - eta, iy, oy, by), Bz = Slab<R>::t((lz + h) - eta, iz, oz, bz);
+    const R Cx = INFLATE ? Slab<R>::t((lx + h) + eta, ix, ox, bx) : Bx;
+    const R Cy = INFLATE ? Slab<R>::t((ly + h) + eta, iy, oy, by) : By;
+    const R Cz = INFLATE ? Slab<R>::t((lz + h) + eta, iz, oz, bz) : Bz;
+    const R Ex = Slab<R>::t((lx + sz) + eta, ix, ox, bx), Ey = Slab<R>::t((ly + sz) + eta, iy, oy, by), Ez = Slab<R>::t((lz + sz) + eta, iz, oz, bz);
+    const R T0 = fmax(fmax(Ax, Ay), fmax(Az, tmin));
+    const R T1 = fmin(fmin(Ex, Ey), fmin(Ez, tl));
+    // child m (mirrored) is hit iff max(T0, B_i : i in m) <= min(T1, C_j : j not in m)
+    uint32_t hit = (T0 <= T1) ? 0xFFu : 0u;
+    hit &= (Bx <= T1) ? 0xFFu : ~HX;
+    hit &= (By <= T1) ? 0xFFu : ~HY;
+    hit &= (Bz <= T1) ? 0xFFu : ~HZ;
+    hit &= (Cx >= T0) ? 0xFFu : HX;
+    hit &= (Cy >= T0) ? 0xFFu : HY;
+    hit &= (Cz >= T0) ? 0xFFu : HZ;
+    hit &= (Bx <= Cy) ? 0xFFu : ~(HX & ~HY);
+    hit &= (Bx <= Cz) ? 0xFFu : ~(HX & ~HZ);
+    hit &= (By <= Cx) ? 0xFFu : ~(HY & ~HX);
+    hit &= (By <= Cz) ? 0xFFu : ~(HY & ~HZ);
+    hit &= (Bz <= Cx) ? 0xFFu : ~(HZ & ~HX);
+    hit &= (Bz <= Cy) ? 0xFFu : ~(HZ & ~HY);
+    const uint32_t cmask = desc.y & 0xFFu;
+    hit &= cmask;
+    if (hit != 0u) {
       const bool cxy = Bx <= By, cxz = Bx <= Bz, cyz = By <= Bz;
       const int rx = (cxy ? 0 : 1) + (cxz ? 0 : 1);
       const int ry = (cxy ? 1 : 0) + (cyz ? 0 : 1);
@@ -470,81 +471,82 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
             static_assert(CERT || HYBRID, "descend_part: CertState or HybridState");
           }
         }
-        break;
-      }
-      const int q = __ffs(hq) - 1;
-      const uint32_t rest = hq & (hq - 1u);
-      // the entry of the child visited after this one (if any), kept with the
-      // node so that a pop past it needs no plane arithmetic
-      R en = Num<R>::inf();
-      if (rest) {
-        const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
-        en = fmax(T0, ax == 0 ? Bx : (ax == 1 ? By : Bz));
-      }
-      stk[level * STRIDE] = make_uint4(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16), __float_as_uint(en),
-                                       __float_as_uint(T0));
-      live = rest ? (live | (1u << level)) : (live & ~(1u << level));
-      const uint32_t k = kt[p * 8 + q];
-      const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
-      if (idx >= n_nodes) {
-        err |= kErrNodeIndex;
-        return;
-      }
-      desc = node_at(nodes, top, top_levels, level + 1, idx);
-      if (STATS) ++cnt.nodes;
-      const uint32_t m = k ^ mir;
-      px = 2u * px + (m & 1u);
-      py = 2u * py + ((m >> 1) & 1u);
-      pz = 2u * pz + ((m >> 2) & 1u);
-      ++level;
-    }
-    for (;;) {  // pop to the deepest level above that still has a child to visit
-      const uint32_t cand = live & ((1u << level) - 1u);
-      if (cand == 0u) return;
-      const int up = level - (31 - __clz(cand));
-      level -= up;
-      px >>= up;
-      py >>= up;
-      pz >>= up;
-      const uint4 e = stk[level * STRIDE];
-      uint32_t rest = (e.y >> 8) & 0xFFu;
-      // the next child's entry, max(T0, mid-plane t of its highest-ranked
-      // axis), was stored when the node was pushed; past the bound, this and
-      // all later siblings are too far for good (the bound only shrinks)
-      if (__uint_as_float(e.z) > rel_bound(st, tmax, tshift)) {
-        live &= ~(1u << level);
+      } else {
+        const int q = __ffs(hq) - 1;
+        const uint32_t rest = hq & (hq - 1u);
+        // the entry of the child visited after this one (if any), kept with the
+        // node so that a pop past it needs no plane arithmetic
+        R en = Num<R>::inf();
+        if (rest) {
+          const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
+          en = fmax(T0, ax == 0 ? Bx : (ax == 1 ? By : Bz));
+        }
+        stk[level * STRIDE] = make_uint4(desc.x, cmask | (rest << 8) | ((uint32_t)p << 16), __float_as_uint(en),
+                                         __float_as_uint(T0));
+        live = rest ? (live | (1u << level)) : (live & ~(1u << level));
+        const uint32_t k = kt[p * 8 + q];
+        const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
+        if (idx >= n_nodes) {
+          err |= kErrNodeIndex;
+          return;
+        }
+        desc = node_at(nodes, top, top_levels, level + 1, idx);
+        if (STATS) ++cnt.nodes;
+        const uint32_t m = k ^ mir;
+        px = 2u * px + (m & 1u);
+        py = 2u * py + ((m >> 1) & 1u);
+        pz = 2u * pz + ((m >> 2) & 1u);
+        ++level;
         continue;
       }
-      const int q = __ffs(rest) - 1;
-      rest &= rest - 1u;
-      if (!rest) live &= ~(1u << level);
-      const int p = (int)(e.y >> 16);
-      R en = Num<R>::inf();
-      if (rest) {  // the entry of the child after it
-        const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
-        const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
-        const R Bsel = ax == 0   ? Slab<R>::t((R(px) * sz + h) - eta, ix, ox, bx)
-                       : ax == 1 ? Slab<R>::t((R(py) * sz + h) - eta, iy, oy, by)
-                                 : Slab<R>::t((R(pz) * sz + h) - eta, iz, oz, bz);
-        en = fmax(__uint_as_float(e.w), Bsel);
-      }
-      stk[level * STRIDE] = make_uint4(e.x, (e.y & ~0xFF00u) | (rest << 8), __float_as_uint(en), e.w);
-      const uint32_t k = kt[p * 8 + q];
-      const uint32_t cmask = e.y & 0xFFu;
-      const uint32_t idx = e.x + __popc(cmask & ((1u << k) - 1u));
-      if (idx >= n_nodes) {
-        err |= kErrNodeIndex;
-        return;
-      }
-      desc = node_at(nodes, top, top_levels, level + 1, idx);
-      if (STATS) ++cnt.nodes;
-      const uint32_t m = k ^ mir;
-      px = 2u * px + (m & 1u);
-      py = 2u * py + ((m >> 1) & 1u);
-      pz = 2u * pz + ((m >> 2) & 1u);
-      ++level;
-      break;
     }
+  for (;;) {  // pop to the deepest level above that still has a child to visit
+    const uint32_t cand = live & ((1u << level) - 1u);
+    if (cand == 0u) return;
+    const int up = level - (31 - __clz(cand));
+    level -= up;
+    px >>= up;
+    py >>= up;
+    pz >>= up;
+    const uint4 e = stk[level * STRIDE];
+    uint32_t rest = (e.y >> 8) & 0xFFu;
+    // the next child's entry, max(T0, mid-plane t of its highest-ranked
+    // axis), was stored when the node was pushed; past the bound, this and
+    // all later siblings are too far for good (the bound only shrinks)
+    if (__uint_as_float(e.z) > rel_bound(st, tmax, tshift)) {
+      live &= ~(1u << level);
+      continue;
+    }
+    const int q = __ffs(rest) - 1;
+    rest &= rest - 1u;
+    if (!rest) live &= ~(1u << level);
+    const int p = (int)(e.y >> 16);
+    R en = Num<R>::inf();
+    if (rest) {  // the entry of the child after it
+      const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
+      const int ax = (int)((kAxisOrder >> (6 * p + 2 * (31 - __clz(__ffs(rest) - 1)))) & 3ull);
+      const R Bsel = ax == 0   ? Slab<R>::t((R(px) * sz + h) - eta, ix, ox, bx)
+                     : ax == 1 ? Slab<R>::t((R(py) * sz + h) - eta, iy, oy, by)
+                               : Slab<R>::t((R(pz) * sz + h) - eta, iz, oz, bz);
+      en = fmax(__uint_as_float(e.w), Bsel);
+    }
+    stk[level * STRIDE] = make_uint4(e.x, (e.y & ~0xFF00u) | (rest << 8), __float_as_uint(en), e.w);
+    const uint32_t k = kt[p * 8 + q];
+    const uint32_t cmask = e.y & 0xFFu;
+    const uint32_t idx = e.x + __popc(cmask & ((1u << k) - 1u));
+    if (idx >= n_nodes) {
+      err |= kErrNodeIndex;
+      return;
+    }
+    desc = node_at(nodes, top, top_levels, level + 1, idx);
+    if (STATS) ++cnt.nodes;
+    const uint32_t m = k ^ mir;
+    px = 2u * px + (m & 1u);
+    py = 2u * py + ((m >> 1) & 1u);
+    pz = 2u * pz + ((m >> 2) & 1u);
+    ++level;
+    break;
+  }
   }
 }
 
