@@ -199,6 +199,19 @@ svo_status svo_get_trace_config(svo_ctx *ctx, int32_t *block, int32_t *rays_per_
  * top nodes would exceed 16 KB.  Results do not depend on it; the autotuner
  * picks it.  Default 0. */
 svo_status svo_set_smem_levels(svo_ctx *ctx, int32_t levels);
+/* The order in which the persistent trace kernel's warps claim the 8 x 4
+ * pixel tiles of image rays (SVO_TRACE_IMAGE, or a batch item's
+ * image_width): row by row, or centre-out (tiles sorted by the distance of
+ * their centres from the image centre).  A tile's cost is set by its slowest
+ * ray, and the kernel ends when its last tile does; claiming the tiles where
+ * the scene usually is (a camera aimed at it) first leaves cheap tiles to fill
+ * the end of the launch.  Results do not depend on it; the autotuner picks
+ * it.  The centre-out table of each image shape is built once per context
+ * (cudaMalloc on the first trace of that shape).  Default centre-out. */
+#define SVO_TILE_ORDER_ROWS 0
+#define SVO_TILE_ORDER_CENTER 1
+svo_status svo_set_tile_order(svo_ctx *ctx, int32_t order);
+svo_status svo_get_tile_order(svo_ctx *ctx, int32_t *order);
 svo_status svo_get_smem_levels(svo_ctx *ctx, int32_t *levels);
 /* Read and clear the context's device error word (synchronises the device).
  * Returns SVO_OK, or SVO_ERR_DEVICE with the failing check in the message. */

@@ -21,6 +21,8 @@ from ._lib import (  # noqa: F401
     RAY_FIXED,
     RAY_REUSED,
     RAY_T_REFINED,
+    TILE_ORDER_CENTER,
+    TILE_ORDER_ROWS,
     RAY_UNCERTAIN,
     TRACE_CULL,
     TRACE_DEFAULT,
@@ -123,6 +125,15 @@ class Context:
     def smem_levels(self) -> int:
         v = C.c_int32(0)
         _lib.check(self.lib.svo_get_smem_levels(self.h, C.byref(v)))
+        return v.value
+
+    def set_tile_order(self, order: int) -> None:
+        """Claim order of image tiles: TILE_ORDER_ROWS or TILE_ORDER_CENTER (speed only)."""
+        _lib.check(self.lib.svo_set_tile_order(self.h, int(order)))
+
+    def tile_order(self) -> int:
+        v = C.c_int32(0)
+        _lib.check(self.lib.svo_get_tile_order(self.h, C.byref(v)))
         return v.value
 
     def check_device(self) -> None:

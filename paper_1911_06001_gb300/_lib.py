@@ -37,6 +37,8 @@ def trace_image(width: int) -> int:
 RAY_UNCERTAIN = 1
 RAY_FIXED = 2
 RAY_T_REFINED = 4
+TILE_ORDER_ROWS = 0
+TILE_ORDER_CENTER = 1
 
 
 def ray_t_bound_exp(flags):
@@ -56,6 +58,7 @@ COLOR_INVALID = 0xFFFFFFFF
 EXPORTS = [
     "svo_ctx_create", "svo_ctx_destroy", "svo_last_error", "svo_status_string", "svo_check_device",
     "svo_set_trace_config", "svo_get_trace_config", "svo_set_smem_levels", "svo_get_smem_levels",
+    "svo_set_tile_order", "svo_get_tile_order",
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info", "svo_read_asset",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device",
     "scene_set_transforms_trs", "scene_refit",
@@ -115,6 +118,8 @@ def load(path: str | None = None):
         "svo_get_trace_config": ([vp, C.POINTER(i32), C.POINTER(i32)], i32),
         "svo_set_smem_levels": ([vp, i32], i32),
         "svo_get_smem_levels": ([vp, C.POINTER(i32)], i32),
+        "svo_set_tile_order": ([vp, i32], i32),
+        "svo_get_tile_order": ([vp, C.POINTER(i32)], i32),
         "svo_build_host": ([C.POINTER(SvoDesc), C.POINTER(u64), C.POINTER(u64), vp, vp], i32),
         "svo_upload": ([vp, C.POINTER(SvoDesc), C.POINTER(u32)], i32),
         "svo_release": ([vp, u32], i32),

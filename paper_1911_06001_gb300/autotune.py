@@ -3,7 +3,8 @@
 Knobs that change only speed, never results: the trace kernel's block size
 (64 / 128 / 256 threads), the rays each lane takes per warp tile (1 / 2 / 4 /
 8), the number of top octree levels each block stages in shared memory (0-4,
-for traces of one scene), the ray order (as given, grouped by direction, grouped by origin cell
+for traces of one scene), the claim order of image tiles (row by row or
+centre-out), the ray order (as given, grouped by direction, grouped by origin cell
 then direction, or -- for rays that are the pixels of an image -- warp tiles
 of 8 x 4 pixels) and, for scenes of 64 parts or more, the culling structure
 (the cluster level or the scene grid).  ``tune`` times every combination on the caller's rays with
@@ -50,7 +51,7 @@ def _time(ctx: Context, scene, rays, hits, flags: int, reps: int, flush) -> floa
 
 def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, blocks=BLOCKS,
          rays_per_lane=RAYS_PER_LANE, orders=None, cache_path: str | None = None,
-         key: str | None = None, image_width: int = 0, culls=None, levels=(0,)) -> dict:
+         key: str | None = None, image_width: int = 0, culls=None, levels=(0,), tile_orders=(1,)) -> dict:
     """Time every (block, rays_per_lane, smem levels, order, cull) on ``rays``
     (CUDA [n, 8]) traced against ``scene``; apply and return the fastest.  The
     "image" order is tried only when ``image_width`` (row-major pixels) is
@@ -73,18 +74,24 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
     old = ctx.trace_config()
     old_levels = ctx.smem_levels()
+    old_tiles = ctx.tile_order()
     table = []
-    for b, r, lv, o, c in itertools.product(blocks, rays_per_lane, levels, orders, culls):
+    for b, r, lv, o, c, to in itertools.product(blocks, rays_per_lane, levels, orders, culls, tile_orders):
+        if o != "image" and to != tile_orders[0]:
+            continue  # the tile order only matters for image tiles
         ctx.set_trace_config(b, r)
         ctx.set_smem_levels(lv)
+        ctx.set_tile_order(to)
         f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | _flag(o, image_width) | CULLS[c]
-        table.append({"block": b, "rays_per_lane": r, "smem_levels": lv, "order": o, "cull": c,
+        table.append({"block": b, "rays_per_lane": r, "smem_levels": lv, "order": o, "cull": c, "tile_order": to,
                       "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
     ctx.set_smem_levels(old_levels)
+    ctx.set_tile_order(old_tiles)
     best = min(table, key=lambda x: x["ms"])
     default = next((x for x in table if x["block"] == 128 and x["rays_per_lane"] == 1 and x["order"] == "none"
-                    and x["cull"] == "clusters" and x["smem_levels"] == 0), None)
+                    and x["cull"] == "clusters" and x["smem_levels"] == 0 and x["tile_order"] == tile_orders[0]),
+                   None)
     result = dict(best)
     result["default_ms"] = default["ms"] if default else None
     result["n_rays"] = int(rays.shape[0])
@@ -109,6 +116,7 @@ def apply(ctx: Context, cfg: dict) -> int:
     """Set the tuned launch shape on ``ctx``; returns the flags (order, culling) to OR into trace flags."""
     ctx.set_trace_config(int(cfg["block"]), int(cfg["rays_per_lane"]))
     ctx.set_smem_levels(int(cfg.get("smem_levels", 0)))
+    ctx.set_tile_order(int(cfg.get("tile_order", 1)))
     return order_flag(cfg)
 
 

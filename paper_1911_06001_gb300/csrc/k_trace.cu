@@ -1031,9 +1031,18 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
       unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
       bool in_range = slot_i < I.n;
       if (I.tiles_x) {
-        // image layout: the tile is a block of 8 x 4*rpl pixels
+        // image layout: the tile is a block of 8 x 4*rpl pixels, claimed in
+        // the item's tile order (row by row without one)
         const uint32_t T = (uint32_t)(tile - I.tile_begin);
-        const uint32_t ty = T / I.tiles_x, tx = T - ty * I.tiles_x;
+        uint32_t ty, tx;
+        if (I.tile_order) {
+          const uint32_t v = __ldg(&I.tile_order[T]);
+          tx = v & 0xFFFFu;
+          ty = v >> 16;
+        } else {
+          ty = T / I.tiles_x;
+          tx = T - ty * I.tiles_x;
+        }
         const uint32_t k = (uint32_t)(j * 32 + lane);
         const uint32_t x = tx * 8u + (k & 7u);
         const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);

@@ -6,6 +6,7 @@
 // pipeline runs in k_refit.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -94,6 +95,8 @@ struct svo_ctx {
   int block = 128;         // trace kernel block size
   int rays_per_lane = 1;   // warp tile = 32 * rays_per_lane rays (1: finest load balance)
   int smem_levels = 0;     // top octree levels staged in shared memory by one-scene traces
+  int tile_order = SVO_TILE_ORDER_CENTER;  // claim order of image tiles
+  std::unordered_map<unsigned long long, uint32_t *> tile_orders;  // (tiles_x, tiles_y) -> device table
   std::mutex mu;
   std::vector<AssetRec> assets;
   std::unordered_set<svo_scene *> scenes;
@@ -202,6 +205,7 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.width = 0;
   it.tiles_x = 0;
   it.pad = 0;
+  it.tile_order = nullptr;
   return it;
 }
 
@@ -220,6 +224,46 @@ void set_top_levels(svo_ctx *ctx, const svo_scene *only, TraceLaunch &L) {
       return;
     }
   }
+}
+
+// The centre-out claim order of a tiles_x x tiles_y grid of image tiles,
+// each tile tw x th pixels: tiles sorted by the distance of their centres from
+// the image centre (ties by row-major index), as tx | ty << 16.  Built on the
+// host once per shape and kept on the device for the context's life.
+svo_status tile_order_table(svo_ctx *ctx, uint32_t tiles_x, uint32_t tiles_y, uint32_t tw, uint32_t th,
+                            uint32_t width, uint32_t height, const uint32_t **out) {
+  *out = nullptr;
+  if (tiles_x == 0 || tiles_y == 0 || tiles_x > 65535u || tiles_y > 65535u) return SVO_OK;  // row by row
+  const unsigned long long key = ((unsigned long long)tiles_x << 32) | tiles_y;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto f = ctx->tile_orders.find(key);
+  if (f != ctx->tile_orders.end()) {
+    *out = f->second;
+    return SVO_OK;
+  }
+  const size_t n = (size_t)tiles_x * tiles_y;
+  std::vector<std::pair<double, uint32_t>> d(n);
+  const double cx = 0.5 * width, cy = 0.5 * height;
+  for (uint32_t ty = 0; ty < tiles_y; ++ty)
+    for (uint32_t tx = 0; tx < tiles_x; ++tx) {
+      const double x = (tx + 0.5) * tw - cx, y = (ty + 0.5) * th - cy;
+      d[(size_t)ty * tiles_x + tx] = {x * x + y * y, tx | (ty << 16)};
+    }
+  std::stable_sort(d.begin(), d.end(), [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &b) {
+    return a.first < b.first;
+  });
+  std::vector<uint32_t> h(n);
+  for (size_t i = 0; i < n; ++i) h[i] = d[i].second;
+  uint32_t *dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, n * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(dev, h.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (dev) cudaFree(dev);
+    return fail(SVO_ERR_CUDA, "tile order table: %s", cudaGetErrorString(e));
+  }
+  ctx->tile_orders[key] = dev;
+  *out = dev;
+  return SVO_OK;
 }
 
 // bounds[i]: scene bound of item i (frame of origin-based ray ordering).
@@ -271,6 +315,17 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
     }
   }
   L.n_tiles = layout_tiles(L.items, L.n_items, ctx->rays_per_lane);
+  for (int i = 0; i < L.n_items; ++i) {  // image items: the claim order of their tiles
+    TraceItem &it = L.items[i];
+    it.tile_order = nullptr;
+    if (!it.tiles_x || ctx->tile_order != SVO_TILE_ORDER_CENTER) continue;
+    const unsigned long long next = i + 1 < L.n_items ? L.items[i + 1].tile_begin : L.n_tiles;
+    const unsigned long long band = 4ull * (unsigned long long)ctx->rays_per_lane;
+    const uint32_t rows = (uint32_t)((it.n + it.width - 1) / it.width);
+    svo_status rc = tile_order_table(ctx, it.tiles_x, (uint32_t)((next - it.tile_begin) / it.tiles_x), 8u,
+                                     (uint32_t)band, it.width, rows, &it.tile_order);
+    if (rc != SVO_OK) return rc;
+  }
   L.tile_counter = slot->d_counters;
   L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
   L.fix_list = slot->d_fix;
@@ -391,6 +446,7 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
       if (e) cudaEventDestroy(e);
     delete kv.second.pending;
   }
+  for (auto &kv : ctx->tile_orders) cudaFree(kv.second);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
   return ok();
@@ -412,6 +468,20 @@ svo_status svo_set_smem_levels(svo_ctx *ctx, int32_t levels) {
   if (levels < 0 || levels > kMaxSmemLevels)
     return fail(SVO_ERR_ARG, "svo_set_smem_levels: %d levels (0..%d)", levels, kMaxSmemLevels);
   ctx->smem_levels = levels;
+  return ok();
+}
+
+svo_status svo_set_tile_order(svo_ctx *ctx, int32_t order) {
+  if (!ctx) return fail(SVO_ERR_ARG, "svo_set_tile_order: ctx is NULL");
+  if (order != SVO_TILE_ORDER_ROWS && order != SVO_TILE_ORDER_CENTER)
+    return fail(SVO_ERR_ARG, "svo_set_tile_order: %d (SVO_TILE_ORDER_ROWS or SVO_TILE_ORDER_CENTER)", order);
+  ctx->tile_order = order;
+  return ok();
+}
+
+svo_status svo_get_tile_order(svo_ctx *ctx, int32_t *order) {
+  if (!ctx || !order) return fail(SVO_ERR_ARG, "svo_get_tile_order: NULL argument");
+  *order = ctx->tile_order;
   return ok();
 }
 

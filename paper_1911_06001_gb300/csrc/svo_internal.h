@@ -107,6 +107,7 @@ struct TraceItem {
   uint32_t width;     // rays are a row-major image of this width (tiles of 8 x 4*rays_per_lane pixels), or 0
   uint32_t tiles_x;   // tiles per image row band (width > 0)
   int32_t pad;
+  const uint32_t *tile_order;  // image tiles: claim order, entry tx | ty << 16 (nullptr: row by row)
 };
 
 // Warp tiles of every item, laid out one item after another: sets each

@@ -53,6 +53,49 @@ def test_every_launch_shape_gives_identical_hits(ctx):
         ctx.set_trace_config(128, 3)
 
 
+def test_tile_claim_order_gives_identical_hits(ctx):
+    """Image tiles claimed row by row or centre-out (per image shape, ragged
+    widths, 1-4 rays per lane, alone and as batch items of two shapes):
+    every ray is traced exactly once with the same result."""
+    import torch
+
+    import paper_1911_06001_gb300 as g
+
+    fig = synthetic.articulated_figure(depth=7)
+    gs = GpuScene(ctx, fig.scene)
+    gs.set_pose(fig.pose(9))
+    assert ctx.tile_order() == g.TILE_ORDER_CENTER
+    for w, h in ((333, 201), (640, 360), (7, 50)):
+        rays = fig.rays(w, h)
+        ctx.set_tile_order(g.TILE_ORDER_ROWS)
+        ref = gs.trace(rays, g.TRACE_DEFAULT)
+        for rpl in (1, 2, 4):
+            ctx.set_trace_config(128, rpl)
+            for order in (g.TILE_ORDER_ROWS, g.TILE_ORDER_CENTER):
+                ctx.set_tile_order(order)
+                _same(gs.trace(rays, g.TRACE_DEFAULT | g.trace_image(w)), ref)
+    # batch items of two image shapes, each with its own table
+    r1, r2 = fig.rays(320, 180), fig.rays(200, 150)
+    ctx.set_tile_order(g.TILE_ORDER_ROWS)
+    ctx.set_trace_config(128, 1)
+    refs = [gs.trace(r, g.TRACE_DEFAULT) for r in (r1, r2)]
+    ctx.set_tile_order(g.TILE_ORDER_CENTER)
+    items = []
+    for r, w in ((r1, 320), (r2, 200)):
+        rt = torch.from_numpy(np.ascontiguousarray(r)).cuda()
+        items.append((gs.sc, rt, torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda"),
+                      torch.zeros(r.shape[0], dtype=torch.int32, device="cuda"), w))
+    ctx.trace_batch(items, flags=g.TRACE_DEFAULT)
+    torch.cuda.synchronize()
+    for (_, _, h, f, _), ref in zip(items, refs):
+        got = g.decode_hits(h)
+        got["flags"] = f.cpu().numpy().astype(np.uint32)
+        _same(got, ref)
+    with pytest.raises(g.SvoError):
+        ctx.set_tile_order(2)
+    ctx.set_trace_config(128, 4)
+
+
 def test_shared_memory_top_levels_give_identical_hits(ctx):
     """Staging the top octree levels of every part in shared memory (0-4
     levels; a depth-9 scene of 16 parts and PR1's four depth-6 parts; a batch
