@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=11000,
                     help="served requests, the first min(1000, n/5) of them warm-up")
     ap.add_argument("--launch", default="",
-                    help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER[,SMEM_LEVELS] instead of autotuning")
+                    help="fixed launch shape BLOCK,RAYS_PER_LANE,ORDER[,SMEM_LEVELS[,TILE_ORDER]] instead of autotuning")
     ap.add_argument("--many-parts-only", action="store_true",
                     help="run only the 1024-part section (cluster level vs scene grid) and print its JSON")
     ap.add_argument("--batched-only", action="store_true",
@@ -798,11 +798,13 @@ def main() -> None:
     if args.launch:
         parts = args.launch.split(",")
         tuned = {"block": int(parts[0]), "rays_per_lane": int(parts[1]), "order": parts[2],
-                 "smem_levels": int(parts[3]) if len(parts) > 3 else 0, "ms": None, "default_ms": None,
-                 "image_width": WIDTH}
+                 "smem_levels": int(parts[3]) if len(parts) > 3 else 0,
+                 "tile_order": int(parts[4]) if len(parts) > 4 else g.TILE_ORDER_CENTER, "ms": None,
+                 "default_ms": None, "image_width": WIDTH}
         autotune.apply(ctx, tuned)
     else:
-        tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3, image_width=WIDTH, levels=(0, 2, 3, 4))
+        tuned = autotune.tune(ctx, sc, rays, flags=g.TRACE_DEFAULT, reps=3, image_width=WIDTH, levels=(0, 2, 3, 4),
+                              tile_orders=(g.TILE_ORDER_CENTER, g.TILE_ORDER_ROWS))
     order = autotune.order_flag(tuned)
     flags = g.TRACE_DEFAULT | g.TRACE_DEFER_FIX | order
 
@@ -983,7 +985,7 @@ def main() -> None:
             "graph": {"value": N_RAYS / (graph_ms.mean() / 1e3) / 1e6, "unit": "Mrays/s",
                       "ms_per_step": float(graph_ms.mean()), "p99_ms": float(np.percentile(graph_ms, 99))},
             "launch": {"block": tuned["block"], "rays_per_lane": tuned["rays_per_lane"], "order": tuned["order"],
-                       "smem_levels": tuned.get("smem_levels", 0),
+                       "smem_levels": tuned.get("smem_levels", 0), "tile_order": tuned.get("tile_order", 1),
                        "autotuned_ms": tuned["ms"], "default_ms": tuned["default_ms"]},
             "hit_buffer": hit_buffer,
             "paper_experiment": paper_experiment,

@@ -268,6 +268,11 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       x.hdiag = sqrtf(s[5]) * __int_as_float((127 - ps.depth) << 23);
       x.spare0 = 0.f;
       x.spare1 = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        x.box_lo[k] = ps.box_lo[k];
+        x.box_hi[k] = ps.box_hi[k];
+      }
+      x.pad[0] = x.pad[1] = 0.f;
       a.aux[p] = x;
       sm.na[p] = rs;
       mn[0] = fminf(mn[0], cfx);

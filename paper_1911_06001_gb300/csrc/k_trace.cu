@@ -636,7 +636,36 @@ __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph,
   const float cn = fmaxf(fmaxf(fabsf(a.w), fabsf(b.w)), fabsf(c.w));
   const float eta =
       kU * (2.0f * pa.n_ainv * (qn + 5.0f * vn + 4.0f * (v1 + fabsf(s.w))) + 2.0f * cn + 8.0f * on + 6.0f) * 1.001f;
-  const float tmin_rel = __fsub_rd(r.tmin, tref), tmax_rel = __fsub_ru(r.tmax, tref);
+  float tmin_rel = __fsub_rd(r.tmin, tref), tmax_rel = __fsub_ru(r.tmax, tref);
+  // Clip the segment to the part's occupied box, inflated by 2 eta: one eta
+  // for the local ray's error, one for this slab arithmetic.  Every leaf lies
+  // in the box, so a leaf's entry is never before the clipped start nor its
+  // exit after the clipped end: no candidate and no entry value changes, the
+  // nodes outside the box along the ray are never visited, and a part whose
+  // box the ray misses is not descended at all.
+  {
+    const float o3[3] = {ox, oy, oz}, d3[3] = {dx, dy, dz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float lo = pa.box_lo[k] - 2.0f * eta, hi = pa.box_hi[k] + 2.0f * eta;
+      if (d3[k] == 0.f) {
+        if (o3[k] < lo || o3[k] > hi) tmax_rel = -Num<float>::inf();
+        continue;
+      }
+      const float inv = 1.0f / d3[k];
+      float ta = (lo - o3[k]) * inv, tb = (hi - o3[k]) * inv;
+      if (ta > tb) {
+        const float x = ta;
+        ta = tb;
+        tb = x;
+      }
+      tmin_rel = fmaxf(tmin_rel, ta);
+      tmax_rel = fminf(tmax_rel, tb);
+    }
+  }
+  // nothing to do either when the box starts beyond the best certain hit so
+  // far (the descent's own bound)
+  if (!(tmin_rel <= tmax_rel) || tmin_rel > rel_bound(st, tmax_rel, tref)) return;
   if (STATS) ++cnt.parts_entered;
   descend_part<float, S, STATS, STRIDE>(stk, pa.nodes, pa.n_nodes, stop + 8u * __float_as_uint(pa.spare0), top_levels,
                                         pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel, eta, tref, part, tab,

@@ -49,7 +49,7 @@ struct PartHot {
   float4 sphere;
 };
 
-// Per-frame scalars of a part (32 B).  In a trace block's shared-memory
+// Per-frame scalars of a part (64 B).  In a trace block's shared-memory
 // copy, spare0 / spare1 carry (as bits) the first and the count of the part's
 // nodes staged in shared memory; in global memory both are 0.
 struct PartAux {
@@ -59,7 +59,11 @@ struct PartAux {
   float n_ainv;      // upper bound of ||Ainv||_inf (max abs row sum of the FP32 rows)
   float hdiag;       // world length of a leaf's diagonal, |A (1,1,1)| 2^-depth
   float spare0, spare1;
+  float box_lo[3];   // local box of the occupied leaves (PartStatic), where the descent starts
+  float box_hi[3];
+  float pad[2];
 };
+static_assert(sizeof(PartAux) == 64, "PartAux is 64 bytes");
 
 // Cluster of up to kClusterSize parts (consecutive in `order`).
 struct Cluster {
