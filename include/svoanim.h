@@ -357,7 +357,7 @@ svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n,
  * SVO_TRACE_DEFER_FIX and the ray-order flags SVO_TRACE_ORDER_DIR /
  * SVO_TRACE_ORDER_ORIGIN (which need per-ray scratch) are rejected
  * (SVO_ERR_ARG).  It never calls cudaMalloc
- * or cudaFree: its scratch (about 6.3 MB) is a static device array inside the
+ * or cudaFree: its scratch (about 15.7 MB) is a static device array inside the
  * library that every GPU loading the library holds until the process exits.
  * n above SVO_NOALLOC_MAX_RAYS returns SVO_ERR_LIMIT.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress); make

@@ -55,8 +55,10 @@ struct TraceLaunchT {
   unsigned long long *fix_list;
   unsigned int *fix_count;
   unsigned long long fix_capacity;
-  uint4 *fix_cand;
-  unsigned long long cand_capacity;
+  uint4 *fix_cand;                  // pool of stored leaves (winner, contenders or re-trace cap)
+  unsigned long long cand_capacity; // pool entries
+  unsigned int *cand_count;         // pool entries taken (zeroed before the launch)
+  uint32_t *fix_off;                // per list slot: its first pool entry, or kNoCand
   svo_trace_stats *stats;
   unsigned int *err;
   int32_t one_scene;     // every item traces the same scene: stage its tables in shared memory
@@ -88,6 +90,7 @@ constexpr int kBlock = 128;  // block size of the FP64 pass; the trace kernel ta
 constexpr int kTraceThreadsPerSM = 768;
 
 constexpr unsigned long long kRayBits = 40;
+constexpr uint32_t kNoCand = 0xFFFFFFFFu;  // a list slot without stored leaves
 
 struct Tables {
   uint8_t q[8][6][256];  // [mirror][perm][true child mask] -> mask in visiting order
@@ -1167,39 +1170,59 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
           I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? (SVO_RAY_T_REFINED | (tbound << 8)) : 0u);
         if (STATS && !ids_ok) ++n_flag;
       }
-      // compact flagged rays for the FP64 pass (one atomic per warp)
+      // compact flagged rays for the FP64 pass: one list slot each and, from
+      // a pool, exactly the leaves the pass needs (one atomic per warp for
+      // each): the winner alone when only t needs FP64, the contenders still
+      // in play (lo <= hi_min) otherwise, or -- when the contender list
+      // overflowed -- one entry carrying hi_min, where the full re-trace may
+      // stop.  A ray the pool cannot hold is re-traced without that bound.
       if (L.flags & SVO_TRACE_FP64_FIX) {
         const unsigned int m = __ballot_sync(0xffffffffu, flagged);
         if (m) {
           const int leader = __ffs(m) - 1;
-          unsigned int basei = 0;
-          if (lane == leader) basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
+          unsigned int ncon = 0;  // contenders in play
+          if (flagged && !ids_ok && !con.overflow)
+            for (int q = 0; q < con.n; ++q) ncon += (con.lo[q] <= st.hi_min) ? 1u : 0u;
+          const unsigned int need = !flagged ? 0u : (ids_ok || con.overflow || ncon == 0u) ? 1u : ncon;
+          unsigned int incl = need;  // inclusive scan of the lanes' pool entries
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+          unsigned int basei = 0, basep = 0;
+          if (lane == leader) {
+            basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
+            basep = atomicAdd(L.cand_count, total);
+          }
           basei = __shfl_sync(0xffffffffu, basei, leader);
+          basep = __shfl_sync(0xffffffffu, basep, leader);
           if (flagged) {
             const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
             if (slot < L.fix_capacity) {
-              // contenders still in play (lo <= hi_min); none stored = full FP64 retrace
-              unsigned long long nc = 0;
-              if (ids_ok && slot < L.cand_capacity) {
-                // ids certified, only t needs FP64: the winner alone, whatever
-                // the contender list holds
-                L.fix_cand[slot * kContenders] =
-                    make_uint4(st.part1, (uint32_t)(st.vox1 & 0xFFFFFFFFull), (uint32_t)(st.vox1 >> 32),
-                               __float_as_uint(st.lo1));
-                nc = 1;
-              } else if (!con.overflow && slot < L.cand_capacity) {
-                for (int q = 0; q < con.n; ++q) {
-                  if (!(con.lo[q] <= st.hi_min)) continue;
-                  L.fix_cand[slot * kContenders + nc] =
-                      make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull), (uint32_t)(con.vox[q] >> 32),
-                                 __float_as_uint(con.lo[q]));
-                  ++nc;
+              const unsigned long long off = (unsigned long long)basep + (incl - need);
+              const bool stored = off + need <= L.cand_capacity;
+              unsigned long long nc = 0;  // leaves listed; 0 = full FP64 re-trace
+              if (stored) {
+                if (ids_ok) {
+                  // ids certified, only t needs FP64: the winner alone
+                  L.fix_cand[off] = make_uint4(st.part1, (uint32_t)(st.vox1 & 0xFFFFFFFFull),
+                                               (uint32_t)(st.vox1 >> 32), __float_as_uint(st.lo1));
+                  nc = 1;
+                } else if (!con.overflow && ncon > 0u) {
+                  for (int q = 0; q < con.n; ++q) {
+                    if (!(con.lo[q] <= st.hi_min)) continue;
+                    L.fix_cand[off + nc] = make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull),
+                                                      (uint32_t)(con.vox[q] >> 32), __float_as_uint(con.lo[q]));
+                    ++nc;
+                  }
+                } else {
+                  // the re-trace may stop at hi_min, an upper bound (rounded up) of the winner's t
+                  L.fix_cand[off] = make_uint4(0u, 0u, 0u, __float_as_uint(st.hi_min));
                 }
-              } else if (slot < L.cand_capacity) {
-                // the list overflowed: the re-trace may stop at hi_min, an
-                // upper bound (rounded up) of the winner's t
-                L.fix_cand[slot * kContenders] = make_uint4(0u, 0u, 0u, __float_as_uint(st.hi_min));
               }
+              L.fix_off[slot] = stored ? (uint32_t)off : kNoCand;
               const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
               L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
             } else {
@@ -1270,7 +1293,8 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
   const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
   const TraceItem &I = L.items[it];
   const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
-  const float tcap = i < L.cand_capacity ? __uint_as_float(L.fix_cand[i * kContenders].w) : Num<float>::inf();
+  const uint32_t off = L.fix_off[i];
+  const float tcap = off != kNoCand ? __uint_as_float(L.fix_cand[off].w) : Num<float>::inf();
   RayW r;
   r.ox = o.x;
   r.oy = o.y;
@@ -1316,9 +1340,9 @@ __device__ void overflow_retrace(const TraceLaunchT<NI> &L, unsigned long long i
 //     lane q of the ray's 8-lane group intersects contender q with the exact
 //     closed-box rule and a group reduction keeps the lexicographic minimum
 //     of (t, part, voxel);
-//   * without one (the list overflowed), the warp re-traces the ray, the
-//     parts dealt over the lanes: the FP32 descent with inflated boxes, every
-//     leaf reached decided in FP64.
+//   * without one (the contender list overflowed, or the leaf pool was
+//     full), the warp re-traces the ray, the parts dealt over the lanes: the
+//     FP32 descent with inflated boxes, every leaf reached decided in FP64.
 // GB300 issues FP64 at 2 lanes per clock per SM, so spreading a ray's
 // contenders over lanes (instead of one lane looping over them) cuts the
 // pass's latency by the contender count.  Groups of four list entries are
@@ -1358,7 +1382,7 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
       if (have && sl < nc) {
         const TraceItem &I = L.items[it];
         const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
-        const uint4 cv = L.fix_cand[i * kContenders + sl];
+        const uint4 cv = L.fix_cand[L.fix_off[i] + sl];
         const uint32_t p = cv.x;
         const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
         double tq;
@@ -1495,6 +1519,8 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   dst.fix_capacity = src.fix_capacity;
   dst.fix_cand = src.fix_cand;
   dst.cand_capacity = src.cand_capacity;
+  dst.cand_count = src.cand_count;
+  dst.fix_off = src.fix_off;
   bool one = true;
   for (int i = 1; i < src.n_items && i < NI; ++i) one = one && src.items[i].hot == src.items[0].hot;
   dst.one_scene = one && src.items[0].n_parts <= kSmemParts ? 1 : 0;

@@ -74,8 +74,9 @@ struct Slot {
   unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
   unsigned long long *d_fix = nullptr;
   unsigned long long cap = 0;
-  uint4 *d_cand = nullptr;                   // contender leaves of the first cand_cap flagged rays
-  unsigned long long cand_cap = 0;
+  uint4 *d_cand = nullptr;                   // pool of leaves stored for the FP64 pass
+  unsigned long long cand_cap = 0;           // pool entries (kPoolPerRay per ray of capacity)
+  uint32_t *d_off = nullptr;                 // per list slot: its first pool entry
   TraceLaunch *pending = nullptr;            // launch whose FP64 pass is deferred
   char *d_stage = nullptr;                   // trace_rays_host: two halves of rays | hits | flags
   cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};  // trace_rays_host: copy in, trace, copy out
@@ -152,25 +153,32 @@ svo_status get_slot(svo_ctx *ctx, void *stream, unsigned long long need, Slot **
       CK(cudaStreamSynchronize((cudaStream_t)stream));
       CK(cudaFree(s.d_fix));
       CK(cudaFree(s.d_cand));
+      CK(cudaFree(s.d_off));
       s.d_fix = nullptr;
       s.d_cand = nullptr;
+      s.d_off = nullptr;
       s.cap = 0;
       s.cand_cap = 0;
     }
-    // contenders are stored for up to 1/8 of the rays (flagged rays are far
-    // fewer); later list entries fall back to a full FP64 retrace
-    const unsigned long long ccap = cap / 8 > 65536 ? cap / 8 : (cap < 65536 ? cap : 65536);
+    // a flagged ray takes 1 pool entry (the winner, or the re-trace bound) or
+    // its contenders (at most kContenders); the pool holds kPoolPerRay per ray
+    // of capacity, and a ray it cannot hold falls back to a full FP64 re-trace
+    const unsigned long long ccap = cap * kPoolPerRay;
     uint4 *c = nullptr;
+    uint32_t *o = nullptr;
     cudaError_t e = cudaMalloc(&p, cap * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c, ccap * kContenders * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&c, ccap * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&o, cap * sizeof(uint32_t));
     if (e != cudaSuccess) {
       if (p) cudaFree(p);
+      if (c) cudaFree(c);
       return fail(SVO_ERR_OOM, "scratch for %llu rays: %s", cap, cudaGetErrorString(e));
     }
     s.d_fix = p;
     s.cap = cap;
     s.d_cand = c;
     s.cand_cap = ccap;
+    s.d_off = o;
   }
   *out = &s;
   return SVO_OK;
@@ -332,11 +340,13 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.fix_capacity = slot->cap;
   L.fix_cand = slot->d_cand;
   L.cand_capacity = slot->cand_cap;
+  L.cand_count = reinterpret_cast<unsigned int *>(slot->d_counters + 2);
+  L.fix_off = slot->d_off;
   L.err = ctx->d_err;
   L.block = ctx->block;
   L.rays_per_lane = ctx->rays_per_lane;
   set_top_levels(ctx, only, L);
-  CK(cudaMemsetAsync(slot->d_counters, 0, 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(slot->d_counters, 0, 3 * sizeof(unsigned long long), st));
   if (L.flags & SVO_TRACE_GRID) {
     GridLaunch gl;
     if (grid_jobs(L.items, L.n_items, gl) > 0) CK(launch_grid(gl, st));
@@ -437,6 +447,7 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
     if (kv.second.d_counters) cudaFree(kv.second.d_counters);
     if (kv.second.d_fix) cudaFree(kv.second.d_fix);
     if (kv.second.d_cand) cudaFree(kv.second.d_cand);
+    if (kv.second.d_off) cudaFree(kv.second.d_off);
     if (kv.second.d_stage) cudaFree(kv.second.d_stage);
     if (kv.second.d_order) cudaFree(kv.second.d_order);
     for (cudaStream_t ps : kv.second.pipe)

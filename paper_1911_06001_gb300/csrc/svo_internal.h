@@ -16,6 +16,7 @@ constexpr int kClusterSize = 8;                 // parts per sphere-hierarchy cl
 constexpr int kMaxClusters = kMaxParts / kClusterSize;
 constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
 constexpr int kContenders = 8;                  // contender leaves kept per flagged ray
+constexpr unsigned long long kPoolPerRay = 3;   // FP64-pass leaf pool entries per ray of scratch capacity
 constexpr int kInlinePoseParts = 256;           // poses up to this many parts go by kernel parameter
 constexpr int kMaxSmemLevels = 4;               // top octree levels a trace block may stage in shared memory
 constexpr size_t kTopCapBytes = 16384;          // at most this many bytes of staged top-level nodes per block
@@ -150,8 +151,10 @@ struct TraceLaunch {
   unsigned long long *fix_list;       // (count << 48) | (item << 40) | ray, capacity fix_capacity
   unsigned int *fix_count;            // zeroed before the launch
   unsigned long long fix_capacity;
-  uint4 *fix_cand;                    // kContenders entries per list slot < cand_capacity
-  unsigned long long cand_capacity;
+  uint4 *fix_cand;                    // pool of the leaves stored per list slot (fix_off)
+  unsigned long long cand_capacity;   // pool entries
+  unsigned int *cand_count;           // pool entries taken; zeroed before the launch
+  uint32_t *fix_off;                  // per list slot: first pool entry, or 0xFFFFFFFF
   svo_trace_stats *stats;
   unsigned int *err;
   int32_t block;          // trace kernel block size: 64, 128 or 256

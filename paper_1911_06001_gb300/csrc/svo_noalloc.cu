@@ -11,7 +11,7 @@
 // allocating library routine on this path.
 //
 // The array is part of the loaded module, so every GPU that loads the library
-// holds it (kNoallocScratchBytes, about 6.3 MB) until the process exits.  All
+// holds it (kNoallocScratchBytes, about 15.7 MB) until the process exits.  All
 // calls share it and it keeps the previous call's contents; the counters that
 // must start at zero are cleared on `stream` at the start of every call.  Two
 // calls whose work overlaps on the GPU (different streams, or different host
@@ -41,11 +41,12 @@ namespace {
 constexpr unsigned long long kNoallocMaxRays = SVO_NOALLOC_MAX_RAYS;
 constexpr unsigned long long kCounterBytes = 256;
 constexpr unsigned long long kFixBytes = kNoallocMaxRays * sizeof(unsigned long long);
-constexpr unsigned long long kCandRays = kNoallocMaxRays / 8;
-constexpr unsigned long long kCandBytes = kCandRays * kContenders * sizeof(uint4);
-constexpr unsigned long long kNoallocScratchBytes = kCounterBytes + kFixBytes + kCandBytes;
+constexpr unsigned long long kOffBytes = kNoallocMaxRays * sizeof(uint32_t);
+constexpr unsigned long long kCandEntries = kNoallocMaxRays * kPoolPerRay;
+constexpr unsigned long long kCandBytes = kCandEntries * sizeof(uint4);
+constexpr unsigned long long kNoallocScratchBytes = kCounterBytes + kFixBytes + kOffBytes + kCandBytes;
 
-// The shared scratch: [counters | flagged-ray list | contender leaves].
+// The shared scratch: [counters | flagged-ray list | pool offsets | leaf pool].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -130,14 +131,16 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->fix_count = reinterpret_cast<unsigned int *>(base + sizeof(unsigned long long));
   L->fix_list = reinterpret_cast<unsigned long long *>(base + kCounterBytes);
   L->fix_capacity = kNoallocMaxRays;
-  L->fix_cand = reinterpret_cast<uint4 *>(base + kCounterBytes + kFixBytes);
-  L->cand_capacity = kCandRays;
+  L->fix_off = reinterpret_cast<uint32_t *>(base + kCounterBytes + kFixBytes);
+  L->fix_cand = reinterpret_cast<uint4 *>(base + kCounterBytes + kFixBytes + kOffBytes);
+  L->cand_capacity = kCandEntries;
+  L->cand_count = reinterpret_cast<unsigned int *>(base + 2 * sizeof(unsigned long long));
   L->err = scene_err_word(s);
   L->top = nullptr;  // no shared-memory top levels on this path
   L->top_nodes = 0;
   L->top_levels = 0;
-  // clear what the kernels expect at zero: the tile counter and the list count
-  e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), st);
+  // clear what the kernels expect at zero: the tile counter, the list count and the pool count
+  e = cudaMemsetAsync(base, 0, 3 * sizeof(unsigned long long), st);
   if (e == cudaSuccess && (flags & SVO_TRACE_GRID)) {
     GridLaunch gl;
     if (grid_jobs(L->items, 1, gl) > 0) e = launch_grid(gl, st);

@@ -31,8 +31,9 @@ from . import TRACE_DEFAULT, TRACE_STATS, Context, trace_image
 
 RAY_BYTES = 32
 HIT_BYTES = 16
-# per-ray scratch the library keeps per stream (FP64 list + contenders / 8 + ordering)
-SCRATCH_BYTES_PER_RAY = 8 + 16 + 10
+# per-ray scratch the library keeps per stream (FP64 list and pool offsets, the FP64 pass's
+# leaf pool of 3 entries of 16 B per ray, ray ordering)
+SCRATCH_BYTES_PER_RAY = 8 + 4 + 48 + 10
 
 
 class AdmissionError(RuntimeError):

@@ -72,10 +72,12 @@ def test_served_results_equal_rendered_alone(world_ctx):
 
 
 def test_admission_by_memory(world_ctx):
-    from paper_1911_06001_gb300.serving import AdmissionError, Server
+    from paper_1911_06001_gb300.serving import HIT_BYTES, RAY_BYTES, SCRATCH_BYTES_PER_RAY, AdmissionError, Server
 
     ctx, world, scenes = world_ctx
-    small = Server(ctx, scenes, n_slots=2, max_batch_rays=1 << 16, memory_budget=(1 << 15) * 82,
+    per_ray = RAY_BYTES + HIT_BYTES + SCRATCH_BYTES_PER_RAY
+    # a budget of 32768 rays: one 160x160 request (25600 rays) at a time
+    small = Server(ctx, scenes, n_slots=2, max_batch_rays=1 << 16, memory_budget=(1 << 15) * per_ray,
                    instances_per_scene=1)
     big = world.requests(1, 100.0, seed=9, resolutions=((512, 512),))[0]
     with pytest.raises(AdmissionError):
@@ -93,11 +95,12 @@ def test_admission_by_memory(world_ctx):
 def test_requests_time_out_in_the_queue(world_ctx):
     """With a maximum queue wait, requests that cannot start in time end with
     status "timeout" and never reach the GPU; the others complete normally."""
-    from paper_1911_06001_gb300.serving import Server
+    from paper_1911_06001_gb300.serving import HIT_BYTES, RAY_BYTES, SCRATCH_BYTES_PER_RAY, Server
 
     ctx, world, scenes = world_ctx
-    srv = Server(ctx, scenes, n_slots=1, max_batch_rays=1 << 16, memory_budget=(1 << 16) * 82, instances_per_scene=1,
-                 max_wait=0.0)
+    per_ray = RAY_BYTES + HIT_BYTES + SCRATCH_BYTES_PER_RAY
+    srv = Server(ctx, scenes, n_slots=1, max_batch_rays=1 << 16, memory_budget=(1 << 16) * per_ray,
+                 instances_per_scene=1, max_wait=0.0)
     reqs = world.requests(40, rate=1e7, seed=11, resolutions=((200, 200),))
     tickets = srv.run(reqs)
     status = [t.status for t in tickets]
