@@ -1359,12 +1359,12 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   const int lane = threadIdx.x & 31;
   const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
   const unsigned long long warp = blockIdx.x + (unsigned long long)gridDim.x * (threadIdx.x >> 5);
-  // Four list entries per warp, one group of 8 lanes each (at most 8
-  // contenders per entry): FP64 issues at a few lanes per clock and a warp
-  // instruction holds the pipe whatever its active lanes, so packing entries
-  // cuts the pipe time per entry.  Entries without contenders are re-traced
-  // afterwards by the whole warp, one at a time.
-  static_assert(kContenders == 8, "8-lane groups");
+  // Four list entries per warp, one group of 8 lanes each (at most 16
+  // contenders per entry, two per lane): FP64 issues at a few lanes per clock
+  // and a warp instruction holds the pipe whatever its active lanes, so
+  // packing entries cuts the pipe time per entry.  Entries without contenders
+  // are re-traced afterwards by the whole warp, one at a time.
+  static_assert(kContenders <= 16, "8-lane groups, two contenders per lane at most");
   const int sub = lane >> 3, sl = lane & 7;
   for (unsigned long long i0 = 4 * warp; i0 < n; i0 += 4 * n_warps) {
     const unsigned long long i = i0 + (unsigned long long)sub;
@@ -1372,7 +1372,8 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
     const unsigned long long e = have ? L.fix_list[i] : 0ull;
     const int nc = (int)(e >> 48);
     {
-      // the FP32 pass narrowed the ray to nc contender leaves: one per lane of the group
+      // the FP32 pass narrowed the ray to nc contender leaves: lane q of the
+      // group takes contenders q and q + 8
       ExactState st;
       st.t = Num<double>::inf();
       st.part = kMissPart;
@@ -1382,11 +1383,14 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
       if (have && sl < nc) {
         const TraceItem &I = L.items[it];
         const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
-        const uint4 cv = L.fix_cand[L.fix_off[i] + sl];
-        const uint32_t p = cv.x;
-        const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
-        double tq;
-        if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
+        const uint32_t off = L.fix_off[i];
+        for (int q = sl; q < nc; q += 8) {
+          const uint4 cv = L.fix_cand[off + q];
+          const uint32_t p = cv.x;
+          const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
+          double tq;
+          if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
+        }
       }
       group_min8(st);
       if (have && nc > 0 && sl == 0)

@@ -15,7 +15,7 @@ constexpr int kMaxParts = SVO_MAX_PARTS;
 constexpr int kClusterSize = 8;                 // parts per sphere-hierarchy cluster
 constexpr int kMaxClusters = kMaxParts / kClusterSize;
 constexpr int kMaxBatchItems = 128;             // items per trace launch (kernel parameter space)
-constexpr int kContenders = 8;                  // contender leaves kept per flagged ray
+constexpr int kContenders = 16;                 // contender leaves kept per flagged ray
 constexpr unsigned long long kPoolPerRay = 3;   // FP64-pass leaf pool entries per ray of scratch capacity
 constexpr int kInlinePoseParts = 256;           // poses up to this many parts go by kernel parameter
 constexpr int kMaxSmemLevels = 4;               // top octree levels a trace block may stage in shared memory
