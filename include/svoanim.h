@@ -99,6 +99,15 @@ typedef int32_t svo_status;
                                 whose previous hit was a miss or on such a part, keeps its hit without a
                                 descent (ray flag SVO_RAY_REUSED).  Needs CULL | SORT | FP64_FIX, as the previous trace
                                 must have had; every trace of a scene restarts its change tracking. */
+#define SVO_TRACE_WAVEFRONT 1024u /* launch shape (results unchanged): the trace runs as two launches.  The
+                                     first runs every ray's first culling pass (Sec. IV-A/B), writes the
+                                     miss of each ray whose part spheres are all missed and queues the
+                                     others with their candidate parts; the second traces the queued rays
+                                     only, 32 to a warp, from those candidates on.  Pays where few rays
+                                     meet a part (incoherent rays in sparse scenes), so that a warp of the
+                                     fused launch descends with few lanes.  Needs CULL | SORT; not with
+                                     REUSE or GRID.  The queue (64 bytes per ray of the largest launch) is
+                                     per-stream scratch, grown like the FP64 list. */
 #define SVO_TRACE_DEFAULT (SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX)
 
 /* per-ray flags written when ray_flags != NULL */
@@ -354,9 +363,9 @@ svo_status trace_rays_host(svo_scene *scene, const float *rays_host, uint64_t n,
  * device, or a host application whose own allocator owns all device memory.
  * (The paper has no counterpart; this is a deployment variant.)  Same
  * arguments and results as trace_rays without `stats`; SVO_TRACE_STATS,
- * SVO_TRACE_DEFER_FIX and the ray-order flags SVO_TRACE_ORDER_DIR /
- * SVO_TRACE_ORDER_ORIGIN (which need per-ray scratch) are rejected
- * (SVO_ERR_ARG).  It never calls cudaMalloc
+ * SVO_TRACE_DEFER_FIX, the ray-order flags SVO_TRACE_ORDER_DIR /
+ * SVO_TRACE_ORDER_ORIGIN and SVO_TRACE_WAVEFRONT (which need per-ray scratch)
+ * are rejected (SVO_ERR_ARG).  It never calls cudaMalloc
  * or cudaFree: its scratch (about 15.7 MB) is a static device array inside the
  * library that every GPU loading the library holds until the process exits.
  * n above SVO_NOALLOC_MAX_RAYS returns SVO_ERR_LIMIT.  The first call on a

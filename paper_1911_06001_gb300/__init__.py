@@ -33,6 +33,7 @@ from ._lib import (  # noqa: F401
     TRACE_GRID,
     TRACE_IMAGE_TILES,
     TRACE_REUSE,
+    TRACE_WAVEFRONT,
     TRACE_SORT,
     TRACE_STATS,
     SvoError,

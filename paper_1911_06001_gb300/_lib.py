@@ -25,6 +25,7 @@ TRACE_ORDER_ORIGIN = 64
 TRACE_IMAGE_TILES = 128
 TRACE_REUSE = 256
 TRACE_GRID = 512
+TRACE_WAVEFRONT = 1024
 TRACE_DEFAULT = TRACE_CULL | TRACE_SORT | TRACE_FP64_FIX
 
 

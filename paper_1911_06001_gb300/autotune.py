@@ -6,8 +6,10 @@ Knobs that change only speed, never results: the trace kernel's block size
 for traces of one scene), the claim order of image tiles (row by row or
 centre-out), the ray order (as given, grouped by direction, grouped by origin cell
 then direction, or -- for rays that are the pixels of an image -- warp tiles
-of 8 x 4 pixels) and, for scenes of 64 parts or more, the culling structure
-(the cluster level or the scene grid).  ``tune`` times every combination on the caller's rays with
+of 8 x 4 pixels) and the culling structure: the cluster level in one launch,
+the cluster level as a culling launch plus a descent launch over the rays it
+queued (SVO_TRACE_WAVEFRONT), or -- for scenes of 64 parts or more -- the
+scene grid.  ``tune`` times every combination on the caller's rays with
 CUDA events (L2 flushed between repetitions), keeps the fastest, and can
 remember it in a JSON cache under a caller-chosen key (for example the scene
 and ray-batch shape).  ``tune_batch`` does the same for a batch of uneven
@@ -24,13 +26,14 @@ import os
 import numpy as np
 
 from . import (TRACE_CULL, TRACE_DEFAULT, TRACE_GRID, TRACE_IMAGE_TILES, TRACE_ORDER_DIR, TRACE_ORDER_ORIGIN,
-               TRACE_REUSE, TRACE_SORT, Context, trace_image)
+               TRACE_REUSE, TRACE_SORT, TRACE_WAVEFRONT, Context, trace_image)
 
 BLOCKS = (64, 128, 256)
 RAYS_PER_LANE = (1, 2, 4, 8)
 ORDERS = {"none": 0, "dir": TRACE_ORDER_DIR, "origin": TRACE_ORDER_ORIGIN, "image": TRACE_IMAGE_TILES}
 _ORDER_BITS = TRACE_ORDER_DIR | TRACE_ORDER_ORIGIN | TRACE_IMAGE_TILES | 0xFFFF0000
-CULLS = {"clusters": 0, "grid": TRACE_GRID}
+CULLS = {"clusters": 0, "grid": TRACE_GRID, "wavefront": TRACE_WAVEFRONT}
+_CULL_BITS = TRACE_GRID | TRACE_WAVEFRONT
 GRID_MIN_PARTS = 64  # scenes from this size on carry a grid
 
 
@@ -68,8 +71,9 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
         orders = tuple(o for o in ORDERS if o != "image" or image_width > 0)
     if culls is None:
         cs = TRACE_CULL | TRACE_SORT
-        grid_ok = getattr(scene, "n_parts", 0) >= GRID_MIN_PARTS and (flags & cs) == cs and not (flags & TRACE_REUSE)
-        culls = ("clusters", "grid") if grid_ok else ("clusters",)
+        two = (flags & cs) == cs and not (flags & TRACE_REUSE)
+        grid_ok = two and getattr(scene, "n_parts", 0) >= GRID_MIN_PARTS
+        culls = ("clusters", "wavefront") + (("grid",) if grid_ok else ()) if two else ("clusters",)
     hits = torch.empty((rays.shape[0], 2), dtype=torch.int64, device=rays.device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=rays.device)
     old = ctx.trace_config()
@@ -82,7 +86,7 @@ def tune(ctx: Context, scene, rays, flags: int = TRACE_DEFAULT, reps: int = 5, b
         ctx.set_trace_config(b, r)
         ctx.set_smem_levels(lv)
         ctx.set_tile_order(to)
-        f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | _flag(o, image_width) | CULLS[c]
+        f = (flags & ~(_ORDER_BITS | _CULL_BITS)) | _flag(o, image_width) | CULLS[c]
         table.append({"block": b, "rays_per_lane": r, "smem_levels": lv, "order": o, "cull": c, "tile_order": to,
                       "ms": _time(ctx, scene, rays, hits, f, reps, flush)})
     ctx.set_trace_config(*old)
@@ -161,7 +165,8 @@ def tune_batch(ctx: Context, items, flags: int = TRACE_DEFAULT, reps: int = 3, b
     if culls is None:
         cs = TRACE_CULL | TRACE_SORT
         big = any(getattr(it[0], "n_parts", 0) >= GRID_MIN_PARTS for it in items)
-        culls = ("clusters", "grid") if big and (flags & cs) == cs and not (flags & TRACE_REUSE) else ("clusters",)
+        two = (flags & cs) == cs and not (flags & TRACE_REUSE)
+        culls = ("clusters", "wavefront") + (("grid",) if big else ()) if two else ("clusters",)
     dev = items[0][1].device
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -169,7 +174,7 @@ def tune_batch(ctx: Context, items, flags: int = TRACE_DEFAULT, reps: int = 3, b
     table = []
     for b, r, o, c in itertools.product(blocks, rays_per_lane, orders, culls):
         ctx.set_trace_config(b, r)
-        f = (flags & ~(_ORDER_BITS | TRACE_GRID)) | ORDERS[o] | CULLS[c]
+        f = (flags & ~(_ORDER_BITS | _CULL_BITS)) | ORDERS[o] | CULLS[c]
         evs = []
         with torch.cuda.stream(st):
             for i in range(reps + 1):

@@ -69,6 +69,9 @@ struct TraceLaunchT {
   const int2 *top;       // one_scene: per part (first, count) of its top-level nodes staged in shared memory
   int32_t top_nodes;     // staged nodes per block (0: none)
   int32_t top_levels;    // levels staged of every part
+  QueueEntry *queue;                // SVO_TRACE_WAVEFRONT: the ray queue (item i from items[i].qbase)
+  unsigned int *queue_count;        // SVO_TRACE_WAVEFRONT: entries queued per item
+  unsigned long long *queue_tile;   // SVO_TRACE_WAVEFRONT: tile counter of the descent launch
 };
 
 namespace {
@@ -834,7 +837,51 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGri
   return ok;
 }
 
-template <bool STATS, int BLOCK, bool GRID>
+// One culling pass (Sec. IV-A/B): the ray against the cluster spheres, then
+// against the part spheres of the clusters it meets; the first kCap
+// candidates in order of sphere entry (entry t, descent reference parameter,
+// part) that come after (last_t, last_p), the last part an earlier pass
+// descended, and in over_t the smallest entry that did not fit the list.
+// Called by the whole warp (need: this lane's ray takes part); NC must be
+// the same on every lane.
+template <bool STATS>
+__device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, const PartHot *__restrict__ hot,
+                                          const Cluster *__restrict__ cl, const int32_t *__restrict__ order,
+                                          float last_t, int last_p, float (&ct)[kCap], float (&ce)[kCap],
+                                          int (&cp)[kCap], float &over_t, Counters &cnt) {
+  for (int c = 0; c < NC; ++c) {
+    const Cluster cc = cl[c];
+    const bool hc = need && cluster_cull(r, cc);
+    if (__ballot_sync(0xffffffffu, hc) == 0u) continue;  // no lane needs this cluster
+    if (hc) {
+      const uint32_t fc = __float_as_uint(cc.aux.w);
+      const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
+      for (int k = 0; k < count; ++k) {
+        const int p = order[first + k];
+        float tin, eta;
+        if (STATS) ++cnt.parts_tested;
+        if (!part_cull(r, hot[p], tin, eta)) continue;
+        if (tin < last_t || (tin == last_t && p <= last_p)) continue;  // visited in an earlier pass
+        float t = tin, e = eta;
+        int pp = p;
+        list_insert(ct, ce, cp, t, e, pp);
+        over_t = fminf(over_t, t);
+      }
+    }
+  }
+}
+
+// The candidates of a ray's first culling pass, as the culling launch of
+// SVO_TRACE_WAVEFRONT queued them.
+struct PreCull {
+  float4 ct, ce;
+  int4 cp;
+  float over_t;
+};
+
+// PRE: the first pass's candidates come from `pre` (the culling launch ran
+// that pass) instead of from the spheres.
+template <bool STATS, int BLOCK, bool GRID, bool PRE = false>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
@@ -842,7 +889,8 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
                               unsigned int &err,
                               Counters &cnt,
                               bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused,
-                              const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords) {
+                              const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords,
+                              const PreCull *pre = nullptr) {
   reused = false;
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
@@ -867,6 +915,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       if (STATS && need && walked) ++cnt.passes;
       need = need && !walked;
     }
+    bool first = true;
     while (__any_sync(0xffffffffu, need)) {
       float ct[kCap], ce[kCap];
       int cp[kCap];
@@ -877,27 +926,19 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
         cp[i] = 0x7fffffff;
       }
       float over_t = Num<float>::inf();  // smallest entry that did not fit the list
-      if (STATS && need) ++cnt.passes;
-      for (int c = 0; c < NC; ++c) {
-        const Cluster cc = cl[c];
-        const bool hc = need && cluster_cull(r, cc);
-        if (__ballot_sync(0xffffffffu, hc) == 0u) continue;  // no lane needs this cluster
-        if (hc) {
-          const uint32_t fc = __float_as_uint(cc.aux.w);
-          const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
-          for (int k = 0; k < count; ++k) {
-            const int p = order[first + k];
-            float tin, eta;
-            if (STATS) ++cnt.parts_tested;
-            if (!part_cull(r, hot[p], tin, eta)) continue;
-            if (tin < last_t || (tin == last_t && p <= last_p)) continue;  // visited in an earlier pass
-            float t = tin, e = eta;
-            int pp = p;
-            list_insert(ct, ce, cp, t, e, pp);
-            over_t = fminf(over_t, t);
-          }
+      if (PRE && first) {
+        static_assert(!PRE || kCap == 4, "a queued ray carries four candidates");
+        if (need) {
+          ct[0] = pre->ct.x, ct[1] = pre->ct.y, ct[2] = pre->ct.z, ct[3] = pre->ct.w;
+          ce[0] = pre->ce.x, ce[1] = pre->ce.y, ce[2] = pre->ce.z, ce[3] = pre->ce.w;
+          cp[0] = pre->cp.x, cp[1] = pre->cp.y, cp[2] = pre->cp.z, cp[3] = pre->cp.w;
+          over_t = pre->over_t;
         }
+      } else {
+        if (STATS && need) ++cnt.passes;
+        cull_pass<STATS>(r, need, NC, hot, cl, order, last_t, last_p, ct, ce, cp, over_t, cnt);
       }
+      first = false;
       // hit buffer reuse (Sec. IV-C, Fig. 5).  The paper reuses a pixel whose
       // ray meets one sphere, that of its unmoved previous part.  The same
       // holds whenever every part whose sphere the ray meets is unmoved and
@@ -994,15 +1035,210 @@ __device__ __forceinline__ void flush_stats(svo_trace_stats *st, const Counters 
   }
 }
 
+// The ray of `lane` in pass j of warp tile `tile` of item I: its index in the
+// item's ray buffer (through the item's visiting order, if any); in_range is
+// false past the item's end.  The tile of an image item is a block of
+// 8 x 4*rays_per_lane pixels, claimed in the item's tile order (row by row
+// without one).
+template <int NI>
+__device__ __forceinline__ unsigned long long tile_ray(const TraceLaunchT<NI> &L, const TraceItem &I,
+                                                       unsigned long long tile, int j, int lane, bool &in_range) {
+  const int rpl = L.rays_per_lane;
+  const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
+  unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
+  in_range = slot_i < I.n;
+  if (I.tiles_x) {
+    const uint32_t T = (uint32_t)(tile - I.tile_begin);
+    uint32_t ty, tx;
+    if (I.tile_order) {
+      const uint32_t v = __ldg(&I.tile_order[T]);
+      tx = v & 0xFFFFu;
+      ty = v >> 16;
+    } else {
+      ty = T / I.tiles_x;
+      tx = T - ty * I.tiles_x;
+    }
+    const uint32_t k = (uint32_t)(j * 32 + lane);
+    const uint32_t x = tx * 8u + (k & 7u);
+    const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);
+    slot_i = y * I.width + x;
+    in_range = x < I.width && slot_i < I.n;
+  }
+  return (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
+}
+
+// Ray `ray` of item I (in_range false: an empty ray).  Returns whether it
+// takes part: a ray needs a direction (Eq. 1) -- its largest component
+// magnitude must lie in [2^-60, 2^60], so that |d|^2 is a normal FP32 number
+// -- and origin, direction and bounds must be numbers, with tmin <= tmax;
+// anything else is a miss.  Exact comparisons: the rule does not depend on
+// rounding.
+__device__ __forceinline__ bool load_ray(const TraceItem &I, unsigned long long ray, bool in_range, RayW &r) {
+  bool active = in_range;
+  if (active) {
+    const float4 o = __ldcs(&I.rays[2 * ray]);
+    const float4 d = __ldcs(&I.rays[2 * ray + 1]);
+    r.ox = o.x;
+    r.oy = o.y;
+    r.oz = o.z;
+    r.tmin = o.w;
+    r.dx = d.x;
+    r.dy = d.y;
+    r.dz = d.z;
+    r.tmax = d.w;
+    const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
+    const float dm = fmaxf(fmaxf(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
+    const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
+                        isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dm >= 0x1p-60f && dm <= 0x1p60f;
+    r.inv_dd = __frcp_rn(dd);  // the correctly rounded 1 / dd
+    r.inv_len = rsqrtf(dd);
+    r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
+    active = finite && (o.w <= d.w);
+  } else {
+    r.ox = r.oy = r.oz = r.dx = r.dy = r.dz = 0.f;
+    r.tmin = 0.f;
+    r.tmax = -1.f;
+    r.inv_dd = 0.f;
+    r.inv_len = 0.f;
+    r.onorm = 0.f;
+  }
+  return active;
+}
+
+// The result of one ray, called by every lane of the warp (in_range false: a
+// lane without a ray): the hit and its flags, and -- with FP64_FIX -- the
+// ray's entry in the FP64 pass's list with the leaves that pass needs.
+template <int NI, bool STATS>
+__device__ __forceinline__ void finish_ray(const TraceLaunchT<NI> &L, const TraceItem &I, int it,
+                                           unsigned long long ray, bool in_range, bool reused, const RayW &r,
+                                           const PartAux *__restrict__ aux, const CertState &st,
+                                           const Contenders &con, int lane, unsigned int &err, Counters &cnt,
+                                           uint32_t &n_flag) {
+  bool flagged = false, ids_ok = true;
+  uint32_t tbound = 0;  // T_REFINED: the certified error exponent, biased (flag bits 8-15)
+  if (in_range && reused) {
+    if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
+    if (STATS) ++cnt.reused;
+  } else if (in_range) {
+    float t = Num<float>::inf();
+    uint32_t part = kMissPart;
+    unsigned long long vox = kMissVoxel;
+    if (st.part1 != kMissPart) {
+      // the reported t lies in [lo1, hi1]; its error is at most half the width
+      const float scale = fmaxf(st.lo1, aux[st.part1].hdiag * r.inv_len);
+      const bool w_ok = st.cert1 != 0u;
+      const bool o_ok = st.lo2 > st.hi1;
+      const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
+      ids_ok = w_ok && o_ok;
+      flagged = !(ids_ok && t_ok);
+      if (ids_ok && !t_ok && I.ray_flags) {
+        // the written t and the exact one both lie in [lo1, hi1]: their
+        // distance is at most 2^e scale with e = ceil(log2((hi1 - lo1) /
+        // scale)), both operations rounded up
+        const uint32_t bits = __float_as_uint(__fdiv_ru(__fsub_ru(st.hi1, st.lo1), scale));
+        const int e = (int)(bits >> 23) - 127 + ((bits & 0x7FFFFFu) != 0u ? 1 : 0);
+        tbound = (uint32_t)min(max(e + 128, 1), 255);
+      }
+      if (STATS) {
+        cnt.f_winner += w_ok ? 0u : 1u;
+        cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
+        cnt.f_width += (ids_ok && !t_ok) ? 1u : 0u;
+      }
+      t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
+      if (!st.cert1) t = st.te1;
+      part = st.part1;
+      vox = st.vox1;
+    }
+    uint4 hv;
+    hv.x = __float_as_uint(t);
+    hv.y = part;
+    hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
+    hv.w = (uint32_t)(vox >> 32);
+    __stcs(&I.hits[ray], hv);
+    if (I.ray_flags)
+      I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? (SVO_RAY_T_REFINED | (tbound << 8)) : 0u);
+    if (STATS && !ids_ok) ++n_flag;
+  }
+  // compact flagged rays for the FP64 pass: one list slot each and, from
+  // a pool, exactly the leaves the pass needs (one atomic per warp for
+  // each): the winner alone when only t needs FP64, the contenders still
+  // in play (lo <= hi_min) otherwise, or -- when the contender list
+  // overflowed -- one entry carrying hi_min, where the full re-trace may
+  // stop.  A ray the pool cannot hold is re-traced without that bound.
+  if (L.flags & SVO_TRACE_FP64_FIX) {
+    const unsigned int m = __ballot_sync(0xffffffffu, flagged);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned int ncon = 0;  // contenders in play
+      if (flagged && !ids_ok && !con.overflow)
+        for (int q = 0; q < con.n; ++q) ncon += (con.lo[q] <= st.hi_min) ? 1u : 0u;
+      const unsigned int need = !flagged ? 0u : (ids_ok || con.overflow || ncon == 0u) ? 1u : ncon;
+      unsigned int incl = need;  // inclusive scan of the lanes' pool entries
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned int basei = 0, basep = 0;
+      if (lane == leader) {
+        basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
+        basep = atomicAdd(L.cand_count, total);
+      }
+      basei = __shfl_sync(0xffffffffu, basei, leader);
+      basep = __shfl_sync(0xffffffffu, basep, leader);
+      if (flagged) {
+        const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
+        if (slot < L.fix_capacity) {
+          const unsigned long long off = (unsigned long long)basep + (incl - need);
+          const bool stored = off + need <= L.cand_capacity;
+          unsigned long long nc = 0;  // leaves listed; 0 = full FP64 re-trace
+          if (stored) {
+            if (ids_ok) {
+              // ids certified, only t needs FP64: the winner alone
+              L.fix_cand[off] = make_uint4(st.part1, (uint32_t)(st.vox1 & 0xFFFFFFFFull),
+                                           (uint32_t)(st.vox1 >> 32), __float_as_uint(st.lo1));
+              nc = 1;
+            } else if (!con.overflow && ncon > 0u) {
+              for (int q = 0; q < con.n; ++q) {
+                if (!(con.lo[q] <= st.hi_min)) continue;
+                L.fix_cand[off + nc] = make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull),
+                                                  (uint32_t)(con.vox[q] >> 32), __float_as_uint(con.lo[q]));
+                ++nc;
+              }
+            } else {
+              // the re-trace may stop at hi_min, an upper bound (rounded up) of the winner's t
+              L.fix_cand[off] = make_uint4(0u, 0u, 0u, __float_as_uint(st.hi_min));
+            }
+          }
+          L.fix_off[slot] = stored ? (uint32_t)off : kNoCand;
+          const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
+          L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
+        } else {
+          err |= kErrFixOverflow;
+        }
+      }
+    }
+  }
+
+}
+
 // REUSE: hit buffer reuse compiled in (a separate instantiation, so that the
 // common kernel carries none of its registers or tests).
 // GRID: the scene-level grid walk compiled in (likewise).
 // TOP: the top levels of every part staged in shared memory (a separate
 // instantiation: the staged-node base is one more live register, which the
 // common kernel does not carry).
-template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID, bool TOP = false>
-__global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+// QUEUE: the descent launch of SVO_TRACE_WAVEFRONT: a warp's tile is 32
+// consecutive entries of one item's region of the ray queue, each a ray with
+// the candidates of its first culling pass (k_cull ran that pass), and the
+// trace goes on from those candidates.  It keeps 16 warps per SM, as the
+// counting build does: at 24 the queued candidates would spill.
+template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID, bool TOP = false, bool QUEUE = false>
+__global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID || QUEUE ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // QUEUE: the first tile of each item's queue region, from the queue counts
+  __shared__ unsigned long long sQT[QUEUE ? NI + 1 : 1];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
   uint4 *sStack = reinterpret_cast<uint4 *>(smem + kTablesBytes) + threadIdx.x;
@@ -1038,17 +1274,40 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
       for (int k = threadIdx.x; k < t.y; k += BLOCK) sTop[t.x + k] = __ldg(&src[k]);
     }
   }
+  if (QUEUE && threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      sQT[i] = acc;
+      const unsigned long long q = min((unsigned long long)L.queue_count[i], L.items[i].n);
+      acc += (q + 31ull) / 32ull;
+    }
+    sQT[L.n_items] = acc;
+  }
   __syncthreads();  // the only block barrier: warps then take tiles independently
   unsigned int err = 0;
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   uint32_t n_rays = 0, n_flag = 0;
   const int lane = threadIdx.x & 31;
+  const unsigned long long n_tiles = QUEUE ? sQT[QUEUE ? L.n_items : 0] : L.n_tiles;
   for (;;) {
     unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
+    if (lane == 0) tile = atomicAdd(QUEUE ? L.queue_tile : L.tile_counter, 1ull);
     tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= L.n_tiles) break;
-    const int it = find_item(L, tile);
+    if (tile >= n_tiles) break;
+    int it = 0;
+    if (QUEUE) {
+      int lo = 0, hi = L.n_items - 1;  // the item whose tiles hold this one
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sQT[mid] <= tile)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      it = lo;
+    } else {
+      it = find_item(L, tile);
+    }
     const TraceItem &I = L.items[it];
     const int P = I.n_parts, NC = I.n_clusters;
     const bool staged = L.one_scene != 0;
@@ -1056,185 +1315,127 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
     const PartAux *aux = staged ? sAux : I.aux;
     const Cluster *cls = staged ? sCl : I.clusters;
     const int32_t *ord = staged ? sOrd : I.order;
-    const int rpl = L.rays_per_lane;
-    const unsigned long long base = (tile - I.tile_begin) * (unsigned long long)(32 * rpl);
+    const int rpl = QUEUE ? 1 : L.rays_per_lane;
 #pragma unroll 1
     for (int j = 0; j < rpl; ++j) {
-      unsigned long long slot_i = base + (unsigned long long)(j * 32 + lane);
-      bool in_range = slot_i < I.n;
-      if (I.tiles_x) {
-        // image layout: the tile is a block of 8 x 4*rpl pixels, claimed in
-        // the item's tile order (row by row without one)
-        const uint32_t T = (uint32_t)(tile - I.tile_begin);
-        uint32_t ty, tx;
-        if (I.tile_order) {
-          const uint32_t v = __ldg(&I.tile_order[T]);
-          tx = v & 0xFFFFu;
-          ty = v >> 16;
-        } else {
-          ty = T / I.tiles_x;
-          tx = T - ty * I.tiles_x;
+      bool in_range = false;
+      unsigned long long ray = 0;
+      PreCull pc;
+      if (QUEUE) {
+        const unsigned long long e = (tile - sQT[it]) * 32ull + (unsigned long long)lane;
+        in_range = e < min((unsigned long long)L.queue_count[it], I.n);
+        pc.ct = pc.ce = make_float4(0.f, 0.f, 0.f, 0.f);
+        pc.cp = make_int4(0, 0, 0, 0);
+        pc.over_t = 0.f;
+        if (in_range) {
+          const QueueEntry *q = L.queue + I.qbase + e;
+          const uint4 id = q->id;
+          ray = (unsigned long long)id.x | ((unsigned long long)id.y << 32);
+          pc.over_t = __uint_as_float(id.z);
+          pc.ct = q->ct;
+          pc.ce = q->ce;
+          pc.cp = q->cp;
         }
-        const uint32_t k = (uint32_t)(j * 32 + lane);
-        const uint32_t x = tx * 8u + (k & 7u);
-        const unsigned long long y = (unsigned long long)ty * (unsigned long long)(4 * rpl) + (k >> 3);
-        slot_i = y * I.width + x;
-        in_range = x < I.width && slot_i < I.n;
-      }
-      const unsigned long long ray = (in_range && I.perm) ? (unsigned long long)I.perm[slot_i] : slot_i;
-      bool active = in_range;
-      RayW r;
-      if (active) {
-        const float4 o = __ldcs(&I.rays[2 * ray]);
-        const float4 d = __ldcs(&I.rays[2 * ray + 1]);
-        r.ox = o.x;
-        r.oy = o.y;
-        r.oz = o.z;
-        r.tmin = o.w;
-        r.dx = d.x;
-        r.dy = d.y;
-        r.dz = d.z;
-        r.tmax = d.w;
-        const float dd = d.x * d.x + d.y * d.y + d.z * d.z;
-        // a ray needs a direction (Eq. 1): its largest component magnitude
-        // must lie in [2^-60, 2^60] (so |d|^2 is a normal FP32 number), and
-        // origin, direction and bounds must be numbers; anything else is a
-        // miss.  Exact comparisons: the rule does not depend on rounding.
-        const float dm = fmaxf(fmaxf(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
-        const bool finite = isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) &&
-                            isfinite(d.z) && !isnan(o.w) && !isnan(d.w) && dm >= 0x1p-60f && dm <= 0x1p60f;
-        r.inv_dd = __frcp_rn(dd);  // the correctly rounded 1 / dd
-        r.inv_len = rsqrtf(dd);
-        r.onorm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fabsf(o.z));
-        active = finite && (o.w <= d.w);
-        if (STATS) ++n_rays;
       } else {
-        r.ox = r.oy = r.oz = r.dx = r.dy = r.dz = 0.f;
-        r.tmin = 0.f;
-        r.tmax = -1.f;
-        r.inv_dd = 0.f;
-        r.inv_len = 0.f;
-        r.onorm = 0.f;
+        ray = tile_ray(L, I, tile, j, lane, in_range);
       }
+      RayW r;
+      const bool active = load_ray(I, ray, in_range, r);
+      if (STATS && in_range && !QUEUE) ++n_rays;  // the culling launch counted the queued rays
       CertState st;
       Contenders con;
       const bool reuse = REUSE && active;
       const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
-      trace_ray_f32<STATS, BLOCK, GRID>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sTopAddr,
-                                        (TOP && ntop_all > 0) ? L.top_levels : 0, sStack, st, con,
-                                        err, cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr, sMbox,
-                                        L.mbox_words);
-      bool flagged = false, ids_ok = true;
-      uint32_t tbound = 0;  // T_REFINED: the certified error exponent, biased (flag bits 8-15)
-      if (in_range && reused) {
-        if (I.ray_flags) I.ray_flags[ray] = SVO_RAY_REUSED;
-        if (STATS) ++cnt.reused;
-      } else if (in_range) {
-        float t = Num<float>::inf();
-        uint32_t part = kMissPart;
-        unsigned long long vox = kMissVoxel;
-        if (st.part1 != kMissPart) {
-          // the reported t lies in [lo1, hi1]; its error is at most half the width
-          const float scale = fmaxf(st.lo1, aux[st.part1].hdiag * r.inv_len);
-          const bool w_ok = st.cert1 != 0u;
-          const bool o_ok = st.lo2 > st.hi1;
-          const bool t_ok = 0.5f * (st.hi1 - st.lo1) <= kTau * scale;
-          ids_ok = w_ok && o_ok;
-          flagged = !(ids_ok && t_ok);
-          if (ids_ok && !t_ok && I.ray_flags) {
-            // the written t and the exact one both lie in [lo1, hi1]: their
-            // distance is at most 2^e scale with e = ceil(log2((hi1 - lo1) /
-            // scale)), both operations rounded up
-            const uint32_t bits = __float_as_uint(__fdiv_ru(__fsub_ru(st.hi1, st.lo1), scale));
-            const int e = (int)(bits >> 23) - 127 + ((bits & 0x7FFFFFu) != 0u ? 1 : 0);
-            tbound = (uint32_t)min(max(e + 128, 1), 255);
-          }
-          if (STATS) {
-            cnt.f_winner += w_ok ? 0u : 1u;
-            cnt.f_overlap += (w_ok && !o_ok) ? 1u : 0u;
-            cnt.f_width += (ids_ok && !t_ok) ? 1u : 0u;
-          }
-          t = fminf(fmaxf(st.te1, st.lo1), st.hi1);
-          if (!st.cert1) t = st.te1;
-          part = st.part1;
-          vox = st.vox1;
-        }
-        uint4 hv;
-        hv.x = __float_as_uint(t);
-        hv.y = part;
-        hv.z = (uint32_t)(vox & 0xFFFFFFFFull);
-        hv.w = (uint32_t)(vox >> 32);
-        __stcs(&I.hits[ray], hv);
-        if (I.ray_flags)
-          I.ray_flags[ray] = !ids_ok ? SVO_RAY_UNCERTAIN : (flagged ? (SVO_RAY_T_REFINED | (tbound << 8)) : 0u);
-        if (STATS && !ids_ok) ++n_flag;
-      }
-      // compact flagged rays for the FP64 pass: one list slot each and, from
-      // a pool, exactly the leaves the pass needs (one atomic per warp for
-      // each): the winner alone when only t needs FP64, the contenders still
-      // in play (lo <= hi_min) otherwise, or -- when the contender list
-      // overflowed -- one entry carrying hi_min, where the full re-trace may
-      // stop.  A ray the pool cannot hold is re-traced without that bound.
-      if (L.flags & SVO_TRACE_FP64_FIX) {
-        const unsigned int m = __ballot_sync(0xffffffffu, flagged);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          unsigned int ncon = 0;  // contenders in play
-          if (flagged && !ids_ok && !con.overflow)
-            for (int q = 0; q < con.n; ++q) ncon += (con.lo[q] <= st.hi_min) ? 1u : 0u;
-          const unsigned int need = !flagged ? 0u : (ids_ok || con.overflow || ncon == 0u) ? 1u : ncon;
-          unsigned int incl = need;  // inclusive scan of the lanes' pool entries
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-          }
-          const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-          unsigned int basei = 0, basep = 0;
-          if (lane == leader) {
-            basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
-            basep = atomicAdd(L.cand_count, total);
-          }
-          basei = __shfl_sync(0xffffffffu, basei, leader);
-          basep = __shfl_sync(0xffffffffu, basep, leader);
-          if (flagged) {
-            const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
-            if (slot < L.fix_capacity) {
-              const unsigned long long off = (unsigned long long)basep + (incl - need);
-              const bool stored = off + need <= L.cand_capacity;
-              unsigned long long nc = 0;  // leaves listed; 0 = full FP64 re-trace
-              if (stored) {
-                if (ids_ok) {
-                  // ids certified, only t needs FP64: the winner alone
-                  L.fix_cand[off] = make_uint4(st.part1, (uint32_t)(st.vox1 & 0xFFFFFFFFull),
-                                               (uint32_t)(st.vox1 >> 32), __float_as_uint(st.lo1));
-                  nc = 1;
-                } else if (!con.overflow && ncon > 0u) {
-                  for (int q = 0; q < con.n; ++q) {
-                    if (!(con.lo[q] <= st.hi_min)) continue;
-                    L.fix_cand[off + nc] = make_uint4(con.part[q], (uint32_t)(con.vox[q] & 0xFFFFFFFFull),
-                                                      (uint32_t)(con.vox[q] >> 32), __float_as_uint(con.lo[q]));
-                    ++nc;
-                  }
-                } else {
-                  // the re-trace may stop at hi_min, an upper bound (rounded up) of the winner's t
-                  L.fix_cand[off] = make_uint4(0u, 0u, 0u, __float_as_uint(st.hi_min));
-                }
-              }
-              L.fix_off[slot] = stored ? (uint32_t)off : kNoCand;
-              const unsigned long long t_only = ids_ok ? 1ull : 0ull;  // ids certain, t needs FP64
-              L.fix_list[slot] = (nc << 48) | (t_only << 47) | ((unsigned long long)it << kRayBits) | ray;
-            } else {
-              err |= kErrFixOverflow;
-            }
-          }
-        }
-      }
+      trace_ray_f32<STATS, BLOCK, GRID, QUEUE>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sTopAddr,
+                                               (TOP && ntop_all > 0) ? L.top_levels : 0, sStack, st, con,
+                                               err, cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr,
+                                               sMbox, L.mbox_words, QUEUE ? &pc : nullptr);
+      finish_ray<NI, STATS>(L, I, it, ray, in_range, reused, r, aux, st, con, lane, err, cnt, n_flag);
     }
   }
   if (STATS) flush_stats(L.stats, cnt, n_rays, n_flag);
   if (err) atomicOr(L.err, err);
+}
+
+// The culling launch of SVO_TRACE_WAVEFRONT.  Its warps take the trace's
+// tiles of rays statically (a warp's tiles are its index plus multiples of
+// the warp count: the work per ray varies little, and no counter is
+// contended), run each ray's first culling pass (Sec. IV-A/B) and either
+// write its miss -- no part sphere met: the result the trace would write --
+// or queue it with its candidates in its item's region of the queue (one
+// atomic per warp).  The descent launch traces the queued rays from there.
+template <int NI, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_cull(const __grid_constant__ TraceLaunchT<NI> L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // [staged part spheres and rows | clusters | part order] of a one-scene launch
+  const int sp = L.one_scene ? L.items[0].n_parts : 0;
+  const int sc = L.one_scene ? L.items[0].n_clusters : 0;
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem);
+  Cluster *sCl = reinterpret_cast<Cluster *>(sHot + sp);
+  int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
+  if (L.one_scene) {
+    const TraceItem &I0 = L.items[0];
+    for (int i = threadIdx.x; i < I0.n_parts; i += BLOCK) {
+      sHot[i] = I0.hot[i];
+      sOrd[i] = I0.order[i];
+    }
+    for (int i = threadIdx.x; i < I0.n_clusters; i += BLOCK) sCl[i] = I0.clusters[i];
+  }
+  __syncthreads();
+  Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t n_rays = 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n_warps = (unsigned long long)gridDim.x * (BLOCK / 32);
+  for (unsigned long long tile = (unsigned long long)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5);
+       tile < L.n_tiles; tile += n_warps) {
+    const int it = find_item(L, tile);
+    const TraceItem &I = L.items[it];
+    const bool staged = L.one_scene != 0;
+    const PartHot *hot = staged ? sHot : I.hot;
+    const Cluster *cls = staged ? sCl : I.clusters;
+    const int32_t *ord = staged ? sOrd : I.order;
+#pragma unroll 1
+    for (int j = 0; j < L.rays_per_lane; ++j) {
+      bool in_range;
+      const unsigned long long ray = tile_ray(L, I, tile, j, lane, in_range);
+      RayW r;
+      const bool active = load_ray(I, ray, in_range, r);
+      if (STATS && in_range) ++n_rays;
+      float ct[kCap], ce[kCap];
+      int cp[kCap];
+#pragma unroll
+      for (int i = 0; i < kCap; ++i) {
+        ct[i] = Num<float>::inf();
+        ce[i] = 0.f;
+        cp[i] = 0x7fffffff;
+      }
+      float over_t = Num<float>::inf();
+      if (STATS && active) ++cnt.passes;
+      cull_pass<STATS>(r, active, I.n_clusters, hot, cls, ord, -Num<float>::inf(), -1, ct, ce, cp, over_t, cnt);
+      // over_t is set only by a full list, so an empty list means no candidate at all
+      const bool queued = active && ct[0] != Num<float>::inf();
+      if (in_range && !queued) {
+        __stcs(&I.hits[ray], make_uint4(0x7f800000u, kMissPart, 0xFFFFFFFFu, 0xFFFFFFFFu));
+        if (I.ray_flags) I.ray_flags[ray] = 0u;
+      }
+      const unsigned int m = __ballot_sync(0xffffffffu, queued);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned int base = 0;
+        if (lane == leader) base = atomicAdd(&L.queue_count[it], (unsigned int)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (queued) {
+          QueueEntry *q = L.queue + I.qbase + base + (unsigned int)__popc(m & ((1u << lane) - 1u));
+          q->id = make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), __float_as_uint(over_t), 0u);
+          q->ct = make_float4(ct[0], ct[1], ct[2], ct[3]);
+          q->ce = make_float4(ce[0], ce[1], ce[2], ce[3]);
+          q->cp = make_int4(cp[0], cp[1], cp[2], cp[3]);
+        }
+      }
+    }
+  }
+  if (STATS) flush_stats(L.stats, cnt, n_rays, 0u);
 }
 
 // ------------------------------------------------------------- FP64 pass
@@ -1474,6 +1675,33 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
     for (int i = 0; i < L.n_items; ++i) any = any || L.items[i].grid != nullptr;
     walk = any;
   }
+  if (L.flags & SVO_TRACE_WAVEFRONT) {
+    // the culling launch, then the descent launch over the queued rays (the
+    // host has checked CULL | SORT without REUSE or GRID)
+    const int parts = L.one_scene ? L.items[0].n_parts : 0, clusters = L.one_scene ? L.items[0].n_clusters : 0;
+    const size_t csmem = (size_t)parts * (sizeof(PartHot) + sizeof(int32_t)) + (size_t)clusters * sizeof(Cluster);
+    auto ck = stats ? k_cull<NI, true, BLOCK> : k_cull<NI, false, BLOCK>;
+    int per_sm = 0;
+    cudaError_t e = blocks_per_sm(ck, BLOCK, csmem, per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned long long grid = (unsigned long long)n_sm * per_sm;
+    const unsigned long long need = (L.n_tiles + BLOCK / 32 - 1) / (BLOCK / 32);
+    if (grid > need) grid = need;
+    if (grid == 0) return cudaSuccess;
+    ck<<<(unsigned int)grid, BLOCK, csmem, stream>>>(L);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the number of queued rays is known on the device only: a full persistent grid
+    const size_t smem = trace_smem_bytes(L.stack_levels, parts, clusters, BLOCK, 0, 0);
+    auto kq = stats ? k_trace<NI, true, BLOCK, false, false, false, true>
+                    : k_trace<NI, false, BLOCK, false, false, false, true>;
+    e = blocks_per_sm(kq, BLOCK, smem, per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kq<<<(unsigned int)(n_sm * per_sm), BLOCK, smem, stream>>>(L);
+    return cudaGetLastError();
+  }
   // the staged top levels only in the common kernel (counting, reuse and grid traces give the same
   // results without them)
   const bool top = L.one_scene && L.top_nodes > 0 && !stats && !reuse && !walk;
@@ -1541,6 +1769,9 @@ void fill_launch(const TraceLaunch &src, TraceLaunchT<NI> &dst) {
   dst.top = src.top;
   dst.top_nodes = (dst.one_scene && src.top) ? src.top_nodes : 0;
   dst.top_levels = dst.top_nodes > 0 ? src.top_levels : 0;
+  dst.queue = src.queue;
+  dst.queue_count = src.queue_count;
+  dst.queue_tile = src.queue_tile;
 }
 
 }  // namespace

@@ -69,9 +69,13 @@ constexpr unsigned long long kZeroCopyMaxRays = 1ull << 18;
 // rounded so that the second half starts 256-byte aligned.
 inline size_t stage_half_bytes(unsigned long long n) { return ((size_t)n * (32 + 16 + 4) + 255) & ~(size_t)255; }
 
+constexpr size_t kCounterWords = kQueueCountWords + kMaxBatchItems / 2;
+
 // Scratch of one stream: launch counters and the FP64 re-intersection list.
 struct Slot {
-  unsigned long long *d_counters = nullptr;  // [0] tile counter, [1] fix count (low 32 bits)
+  // [0] tile counter, [1] fix count (low 32 bits), [2] pool count, [3] tile counter of the wavefront
+  // descent launch, then kMaxBatchItems 32-bit queue counts
+  unsigned long long *d_counters = nullptr;
   unsigned long long *d_fix = nullptr;
   unsigned long long cap = 0;
   uint4 *d_cand = nullptr;                   // pool of leaves stored for the FP64 pass
@@ -86,6 +90,8 @@ struct Slot {
   unsigned long long stage_rays = 0;                   // capacity of each half
   void *d_order = nullptr;                   // ray-ordering keys, histogram and permutations
   size_t order_cap = 0;
+  QueueEntry *d_queue = nullptr;             // SVO_TRACE_WAVEFRONT: the ray queue
+  unsigned long long queue_cap = 0;          // entries
 };
 
 }  // namespace
@@ -144,7 +150,7 @@ AssetRec *find_asset(svo_ctx *ctx, svo_handle h) {
 svo_status get_slot(svo_ctx *ctx, void *stream, unsigned long long need, Slot **out) {
   std::lock_guard<std::mutex> g(ctx->mu);
   Slot &s = ctx->slots[stream];
-  if (!s.d_counters) CK(cudaMalloc(&s.d_counters, 4 * sizeof(unsigned long long)));
+  if (!s.d_counters) CK(cudaMalloc(&s.d_counters, kCounterWords * sizeof(unsigned long long)));
   if (need > s.cap) {
     unsigned long long cap = need < 65536 ? 65536 : need;
     unsigned long long *p = nullptr;
@@ -214,6 +220,7 @@ TraceItem make_item(svo_scene *s, const float *rays, uint64_t n, svo_hit *hits, 
   it.tiles_x = 0;
   it.pad = 0;
   it.tile_order = nullptr;
+  it.qbase = 0;
   return it;
 }
 
@@ -284,6 +291,10 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   if ((L.flags & SVO_TRACE_GRID) &&
       ((L.flags & SVO_TRACE_REUSE) || (L.flags & (SVO_TRACE_CULL | SVO_TRACE_SORT)) != (SVO_TRACE_CULL | SVO_TRACE_SORT)))
     return fail(SVO_ERR_ARG, "SVO_TRACE_GRID needs CULL | SORT and excludes REUSE");
+  const bool wave = (L.flags & SVO_TRACE_WAVEFRONT) != 0;
+  if (wave && ((L.flags & (SVO_TRACE_REUSE | SVO_TRACE_GRID)) ||
+               (L.flags & (SVO_TRACE_CULL | SVO_TRACE_SORT)) != (SVO_TRACE_CULL | SVO_TRACE_SORT)))
+    return fail(SVO_ERR_ARG, "SVO_TRACE_WAVEFRONT needs CULL | SORT and excludes REUSE and GRID");
   cudaStream_t st = (cudaStream_t)stream;
   Slot *slot = nullptr;
   svo_status rc = get_slot(ctx, stream, total_rays, &slot);
@@ -334,6 +345,29 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
                                      (uint32_t)band, it.width, rows, &it.tile_order);
     if (rc != SVO_OK) return rc;
   }
+  L.queue = nullptr;
+  L.queue_count = reinterpret_cast<unsigned int *>(slot->d_counters + kQueueCountWords);
+  L.queue_tile = slot->d_counters + 3;
+  if (wave) {
+    if (total_rays > slot->queue_cap) {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      if (slot->d_queue) {
+        CK(cudaStreamSynchronize(st));  // queued work on this stream may still read the old queue
+        CK(cudaFree(slot->d_queue));
+        slot->d_queue = nullptr;
+        slot->queue_cap = 0;
+      }
+      cudaError_t e = cudaMalloc(&slot->d_queue, total_rays * sizeof(QueueEntry));
+      if (e != cudaSuccess) return fail(SVO_ERR_OOM, "ray queue: %s", cudaGetErrorString(e));
+      slot->queue_cap = total_rays;
+    }
+    L.queue = slot->d_queue;
+    unsigned long long q = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      L.items[i].qbase = q;
+      q += L.items[i].n;
+    }
+  }
   L.tile_counter = slot->d_counters;
   L.fix_count = reinterpret_cast<unsigned int *>(slot->d_counters + 1);
   L.fix_list = slot->d_fix;
@@ -346,7 +380,10 @@ svo_status run_trace(svo_ctx *ctx, TraceLaunch &L, unsigned long long total_rays
   L.block = ctx->block;
   L.rays_per_lane = ctx->rays_per_lane;
   set_top_levels(ctx, only, L);
-  CK(cudaMemsetAsync(slot->d_counters, 0, 3 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(slot->d_counters, 0,
+                     wave ? kQueueCountWords * sizeof(unsigned long long) + (size_t)L.n_items * sizeof(unsigned int)
+                          : 3 * sizeof(unsigned long long),
+                     st));
   if (L.flags & SVO_TRACE_GRID) {
     GridLaunch gl;
     if (grid_jobs(L.items, L.n_items, gl) > 0) CK(launch_grid(gl, st));
@@ -450,6 +487,7 @@ svo_status svo_ctx_destroy(svo_ctx *ctx) {
     if (kv.second.d_off) cudaFree(kv.second.d_off);
     if (kv.second.d_stage) cudaFree(kv.second.d_stage);
     if (kv.second.d_order) cudaFree(kv.second.d_order);
+    if (kv.second.d_queue) cudaFree(kv.second.d_queue);
     for (cudaStream_t ps : kv.second.pipe)
       if (ps) cudaStreamDestroy(ps);
     for (cudaEvent_t e : kv.second.pipe_ev) cudaEventDestroy(e);

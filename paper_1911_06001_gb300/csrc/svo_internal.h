@@ -113,7 +113,20 @@ struct TraceItem {
   uint32_t tiles_x;   // tiles per image row band (width > 0)
   int32_t pad;
   const uint32_t *tile_order;  // image tiles: claim order, entry tx | ty << 16 (nullptr: row by row)
+  unsigned long long qbase;    // SVO_TRACE_WAVEFRONT: the item's first entry in the ray queue
 };
+
+// SVO_TRACE_WAVEFRONT: a ray whose first culling pass found candidate parts,
+// queued by the culling launch for the descent launch (64 B).
+struct QueueEntry {
+  uint4 id;   // .x | .y << 32: the ray's index in its item; .z: bits of the smallest sphere entry that
+              // did not fit the list (infinity: none); .w: unused
+  float4 ct;  // sphere entry t of up to four candidates, increasing (infinity: no candidate)
+  float4 ce;  // the reference parameter of each candidate's descent
+  int4 cp;    // the candidates' part ids
+};
+static_assert(sizeof(QueueEntry) == 64, "QueueEntry is 64 bytes");
+constexpr int kQueueCountWords = 4;  // per-stream counters before the per-item queue counts (64-bit words)
 
 // Warp tiles of every item, laid out one item after another: sets each
 // item's tile_begin (and tiles_x) and returns the total.  A tile is
@@ -162,6 +175,9 @@ struct TraceLaunch {
   const int2 *top;        // per part (first, count) of its staged top-level nodes, or nullptr
   int32_t top_nodes;      // nodes staged in shared memory per block (0: none)
   int32_t top_levels;     // the top levels of every part that are staged
+  QueueEntry *queue;                  // SVO_TRACE_WAVEFRONT: entries of every item, item i from items[i].qbase
+  unsigned int *queue_count;          // SVO_TRACE_WAVEFRONT: per item, entries queued; zeroed before the launch
+  unsigned long long *queue_tile;     // SVO_TRACE_WAVEFRONT: tile counter of the descent launch; zeroed
 };
 
 // Kernel launchers (k_trace.cu, k_refit.cu).

@@ -22,8 +22,9 @@
 // device's primary context) while the library is loaded would leave that
 // address stale, so it is not supported.
 //
-// Ray ordering (SVO_TRACE_ORDER_DIR / _ORIGIN) needs per-ray scratch of its
-// own and is rejected here, as are STATS and DEFER_FIX.  The launch record
+// Ray ordering (SVO_TRACE_ORDER_DIR / _ORIGIN) and the two-launch wavefront
+// shape (SVO_TRACE_WAVEFRONT) need per-ray scratch of their own and are
+// rejected here, as are STATS and DEFER_FIX.  The launch record
 // lives in static storage under a lock of its own, so the call puts nothing
 // large on the caller's stack.
 #include <cuda_runtime.h>
@@ -94,9 +95,10 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   }
   if ((reinterpret_cast<uintptr_t>(rays) & 15) || (reinterpret_cast<uintptr_t>(hits) & 15))
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: rays and hits must be 16-byte aligned");
-  if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX | SVO_TRACE_ORDER_DIR | SVO_TRACE_ORDER_ORIGIN))
+  if (flags & (SVO_TRACE_STATS | SVO_TRACE_DEFER_FIX | SVO_TRACE_ORDER_DIR | SVO_TRACE_ORDER_ORIGIN |
+               SVO_TRACE_WAVEFRONT))
     return set_last_error(SVO_ERR_ARG,
-                          "trace_rays_noalloc: STATS, DEFER_FIX and the ORDER flags are not supported");
+                          "trace_rays_noalloc: STATS, DEFER_FIX, the ORDER flags and WAVEFRONT are not supported");
   constexpr uint32_t kReuseNeeds = SVO_TRACE_CULL | SVO_TRACE_SORT | SVO_TRACE_FP64_FIX;
   if ((flags & SVO_TRACE_REUSE) && (flags & kReuseNeeds) != kReuseNeeds)
     return set_last_error(SVO_ERR_ARG, "trace_rays_noalloc: SVO_TRACE_REUSE needs CULL | SORT | FP64_FIX");
@@ -139,6 +141,9 @@ extern "C" svo_status trace_rays_noalloc(svo_scene *s, const float *rays, uint64
   L->top = nullptr;  // no shared-memory top levels on this path
   L->top_nodes = 0;
   L->top_levels = 0;
+  L->queue = nullptr;  // no wavefront shape on this path
+  L->queue_count = nullptr;
+  L->queue_tile = nullptr;
   // clear what the kernels expect at zero: the tile counter, the list count and the pool count
   e = cudaMemsetAsync(base, 0, 3 * sizeof(unsigned long long), st);
   if (e == cudaSuccess && (flags & SVO_TRACE_GRID)) {
