@@ -511,19 +511,22 @@ def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
     t_given = timed(lambda: ctx.trace_batch(items, flags=flags))
     t_origin = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_ORDER_ORIGIN))
     t_each = timed(lambda: [sc.trace(r, h, flags=flags) for sc, r, h, _ in items])
-    # roofline of the trace kernel on the batch: algorithmic bytes from a
-    # counting pass, over the launch with the FP64 pass deferred (the call
-    # then issues two counter memsets and the trace kernel only)
-    st = g.new_stats(dev)
-    ctx.trace_batch(items, flags=flags | g.TRACE_STATS, stats=st)
-    torch.cuda.synchronize()
-    counts = g.read_stats(st)
-    t_kernel = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_DEFER_FIX))
-    ctx.fix_pending()
+    t_wave = timed(lambda: ctx.trace_batch(items, flags=flags | g.TRACE_WAVEFRONT))
     # the launch shape tuned on this batch, then the graph-captured frame in that shape
     tuned = autotune.tune_batch(ctx, items, flags=flags, reps=2, blocks=(64, 128, 256), rays_per_lane=(1, 2, 4))
     tflags = flags | autotune.order_flag(tuned)
     t_tuned = timed(lambda: ctx.trace_batch(items, flags=tflags))
+    # roofline of the trace in the tuned shape: algorithmic bytes from a
+    # counting pass, over the call with the FP64 pass deferred (counter
+    # memsets, any ordering launches, and the trace launch -- or, in the
+    # wavefront shape, the culling and descent launches)
+    st = g.new_stats(dev)
+    ctx.trace_batch(items, flags=tflags | g.TRACE_STATS, stats=st)
+    torch.cuda.synchronize()
+    counts = g.read_stats(st)
+    t_kernel = timed(lambda: ctx.trace_batch(items, flags=tflags | g.TRACE_DEFER_FIX))
+    ctx.fix_pending()
+    wave = bool(tflags & g.TRACE_WAVEFRONT)
     bg = BatchGraph(ctx, items, [s.local for s in bat.scenes], flags=tflags)
     t_graph = timed(lambda: bg.replay(), st=bg.stream)
     ctx.set_trace_config(*old_cfg)
@@ -542,14 +545,18 @@ def batched_section(g, ctx, bat, pool_handles, dev, reps: int, flush) -> dict:
                                 "ordering, the persistent trace and the FP64 pass, in the tuned shape"},
             "batched_given_order": {"value": mr(t_given), "unit": "Mrays/s", "ms": t_given,
                                     "launch": "block 128, 1 ray per lane, rays in their given order"},
+            "wavefront_given_order": {"value": mr(t_wave), "unit": "Mrays/s", "ms": t_wave,
+                                      "launch": "block 128, 1 ray per lane, given order, culling launch + "
+                                                "descent launch over the queued rays"},
             "batched_origin_order": {"value": mr(t_origin), "unit": "Mrays/s", "ms": t_origin},
             "per_scene_calls": {"value": mr(t_each), "unit": "Mrays/s", "ms": t_each},
             "tuned": {k: tuned[k] for k in ("block", "rays_per_lane", "order", "cull", "ms", "default_ms", "key")},
             "nodes_per_ray": counts["nodes_visited"] / n, "parts_entered_per_ray": counts["parts_entered"] / n,
             "roofline": {**roofline_of(alg_bytes(counts), t_kernel,
-                                       "trace_batch with the FP64 pass deferred: two 16-byte memsets and the "
-                                       "trace kernel (block 128, 1 ray per lane, given order)"),
-                         "kernel": "k_trace"}}
+                                       "trace_batch in the tuned shape with the FP64 pass deferred: counter "
+                                       "memsets, ordering launches if any, and "
+                                       + ("the culling and descent launches" if wave else "the trace launch")),
+                         "kernel": "k_cull + k_trace (queue)" if wave else "k_trace"}}
 
 
 def serving_section(g, ctx, srv, pool_handles, n_requests: int, warm: int, rate: float,
