@@ -675,7 +675,8 @@ def run_many_parts_only() -> None:
 def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -> dict:
     """A scene of 1024 parts (the largest a scene holds) traced by a
     1920x1080 camera outside the part cube and by 1 M rays inside it, with
-    the cluster level and with the scene grid (Sec. V-E); refit included."""
+    the cluster level in one launch, the cluster level as culling and descent
+    launches (wavefront), and the scene grid (Sec. V-E); refit included."""
     import torch
 
     scene, cam_np, inner_np = many
@@ -718,7 +719,7 @@ def many_parts_section(g, ctx, many, pool_handles, dev, flush, reps: int = 10) -
         n = int(rays.shape[0])
         hits = torch.empty((n, 2), dtype=torch.int64, device=dev)
         row = {}
-        for label, cull in (("clusters", 0), ("grid", g.TRACE_GRID)):
+        for label, cull in (("clusters", 0), ("wavefront", g.TRACE_WAVEFRONT), ("grid", g.TRACE_GRID)):
             f = g.TRACE_DEFAULT | extra | cull
             ms = timed(lambda: sc.trace(rays, hits, flags=f))
             trace_ms, fix_ms = timed_split(f)

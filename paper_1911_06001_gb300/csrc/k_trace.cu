@@ -844,18 +844,86 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGri
 // descended, and in over_t the smallest entry that did not fit the list.
 // Called by the whole warp (need: this lane's ray takes part); NC must be
 // the same on every lane.
-template <bool STATS>
+//
+// The list holds the kCap smallest (t, part) keys and over_t the smallest t
+// of the others whatever the order of insertion, so the member tests may be
+// dealt out in any order.  SPREAD: when few lanes meet a cluster (incoherent
+// rays), its (lane, member) pairs are dealt over the warp's lanes -- each
+// lane tests one member against the ray of the lane that met the cluster,
+// read by shuffles -- and every hit is handed back to its ray's lane;
+// otherwise every lane that met the cluster tests all its members, and the
+// others idle through them.
+// Position of the n-th (from 0) set bit of m; n < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned int m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const int c = __popc(m & ((1u << w) - 1u));  // set bits among the low w
+    if (c <= n) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+template <bool STATS, bool SPREAD = false>
 __device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, const PartHot *__restrict__ hot,
                                           const Cluster *__restrict__ cl, const int32_t *__restrict__ order,
                                           float last_t, int last_p, float (&ct)[kCap], float (&ce)[kCap],
                                           int (&cp)[kCap], float &over_t, Counters &cnt) {
+  const int lane = threadIdx.x & 31;
   for (int c = 0; c < NC; ++c) {
     const Cluster cc = cl[c];
     const bool hc = need && cluster_cull(r, cc);
-    if (__ballot_sync(0xffffffffu, hc) == 0u) continue;  // no lane needs this cluster
+    const unsigned int m = __ballot_sync(0xffffffffu, hc);
+    if (m == 0u) continue;  // no lane needs this cluster
+    const uint32_t fc = __float_as_uint(cc.aux.w);
+    const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
+    const int nl = __popc(m);
+    static_assert(kClusterSize == 8, "pairs are dealt eight members to a lane that met the cluster");
+    if (SPREAD && nl <= 12) {
+      // pair q = (n-th lane of m, member q & 7): up to three rounds of 32 pairs
+      for (int q0 = 0; q0 < 8 * nl; q0 += 32) {
+        const int q = q0 + lane, n = q >> 3, k = q & 7;
+        const bool valid = n < nl && k < count;
+        const int owner = valid ? nth_set_bit(m, n) : lane;
+        RayW ro;
+        ro.ox = __shfl_sync(0xffffffffu, r.ox, owner);
+        ro.oy = __shfl_sync(0xffffffffu, r.oy, owner);
+        ro.oz = __shfl_sync(0xffffffffu, r.oz, owner);
+        ro.dx = __shfl_sync(0xffffffffu, r.dx, owner);
+        ro.dy = __shfl_sync(0xffffffffu, r.dy, owner);
+        ro.dz = __shfl_sync(0xffffffffu, r.dz, owner);
+        ro.tmin = __shfl_sync(0xffffffffu, r.tmin, owner);
+        ro.tmax = __shfl_sync(0xffffffffu, r.tmax, owner);
+        ro.inv_dd = __shfl_sync(0xffffffffu, r.inv_dd, owner);
+        const float lt = __shfl_sync(0xffffffffu, last_t, owner);
+        const int lp = __shfl_sync(0xffffffffu, last_p, owner);
+        float tin = 0.f, tref = 0.f;
+        int p = 0;
+        bool hit = false;
+        if (valid) {
+          p = order[first + k];
+          if (STATS) ++cnt.parts_tested;
+          hit = part_cull(ro, hot[p], tin, tref) && !(tin < lt || (tin == lt && p <= lp));
+        }
+        // hand each hit to its ray's lane (hits are rare: one round each)
+        for (unsigned int hm = __ballot_sync(0xffffffffu, hit); hm != 0u; hm &= hm - 1u) {
+          const int src = __ffs(hm) - 1;
+          const int o = __shfl_sync(0xffffffffu, owner, src);
+          float t = __shfl_sync(0xffffffffu, tin, src), e = __shfl_sync(0xffffffffu, tref, src);
+          int pp = __shfl_sync(0xffffffffu, p, src);
+          if (lane == o) {
+            list_insert(ct, ce, cp, t, e, pp);
+            over_t = fminf(over_t, t);
+          }
+        }
+      }
+      continue;
+    }
     if (hc) {
-      const uint32_t fc = __float_as_uint(cc.aux.w);
-      const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
       for (int k = 0; k < count; ++k) {
         const int p = order[first + k];
         float tin, eta;
@@ -1412,7 +1480,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_cull(const __grid_const
       }
       float over_t = Num<float>::inf();
       if (STATS && active) ++cnt.passes;
-      cull_pass<STATS>(r, active, I.n_clusters, hot, cls, ord, -Num<float>::inf(), -1, ct, ce, cp, over_t, cnt);
+      cull_pass<STATS, true>(r, active, I.n_clusters, hot, cls, ord, -Num<float>::inf(), -1, ct, ce, cp, over_t,
+                             cnt);
       // over_t is set only by a full list, so an empty list means no candidate at all
       const bool queued = active && ct[0] != Num<float>::inf();
       if (in_range && !queued) {

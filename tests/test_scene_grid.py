@@ -242,15 +242,16 @@ def test_autotune_tries_the_grid(ctx):
     rays = torch.from_numpy(rays_np).cuda()
     old = ctx.trace_config()
     cfg = autotune.tune(ctx, gs.sc, rays, reps=2, blocks=(128,), rays_per_lane=(1,), orders=("none",))
-    assert sorted(x["cull"] for x in cfg["table"]) == ["clusters", "grid"]
+    assert sorted(x["cull"] for x in cfg["table"]) == ["clusters", "grid", "wavefront"]
     extra = autotune.order_flag(cfg)
     assert bool(extra & g.TRACE_GRID) == (cfg["cull"] == "grid")
+    assert bool(extra & g.TRACE_WAVEFRONT) == (cfg["cull"] == "wavefront")
     res = gs.trace(rays_np, DEFAULT | extra)
     compare(scene, scene.local, rays_np, res, oracle.SceneOracle(scene).trace(rays_np))
-    # no grid knob for small scenes or with hit buffer reuse
+    # no grid knob for small scenes; neither grid nor wavefront with hit buffer reuse
     small = GpuScene(ctx, _affine_scene(rng, 20, 8.0))
     c2 = autotune.tune(ctx, small.sc, rays, reps=1, blocks=(128,), rays_per_lane=(1,), orders=("none",))
-    assert [x["cull"] for x in c2["table"]] == ["clusters"]
+    assert [x["cull"] for x in c2["table"]] == ["clusters", "wavefront"]
     c3 = autotune.tune(ctx, gs.sc, rays, flags=DEFAULT | g.TRACE_REUSE, reps=1, blocks=(128,), rays_per_lane=(1,),
                        orders=("none",))
     assert [x["cull"] for x in c3["table"]] == ["clusters"]
