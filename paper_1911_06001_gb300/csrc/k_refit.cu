@@ -59,13 +59,19 @@ __device__ __forceinline__ unsigned int spread10(unsigned int v) {
   return v;
 }
 
-// Thread of the j-th item (part) of a pass: item j -> warp j % 8, lane group
-// j / 8, so that even a handful of parts lands on every warp.  Returns the
-// item handled by thread t and the lane r (0..3) inside its group of four.
+// Thread of the j-th item (part) of a pass.  A warp's FP64 instruction holds
+// its sub-partition's FP64 pipe for the same time however few of its lanes
+// are busy, so items fill one warp per sub-partition first (warps 0-3, one
+// per sub-partition), eight lane groups deep, before warps 4-7 take items 32
+// to 63: item j -> warp (j & 3) + 4 (j >> 5), lane group (j >> 2) & 7.  A
+// 16-part scene then costs each sub-partition one warp's instructions, not
+// two half-empty warps'.  Returns the item handled by thread t and the lane
+// r (0..3) inside its group of four.
 __device__ __forceinline__ int quad_item(int t, int &r) {
+  static_assert(kRefitWarps == 8, "two warps per sub-partition");
   const int w = t >> 5, l = t & 31;
   r = l & 3;
-  return (l >> 2) * kRefitWarps + w;
+  return 32 * (w >> 2) + 4 * (l >> 2) + (w & 3);
 }
 
 // Shared-memory layout of one refit: every per-part intermediate stays on
@@ -161,16 +167,18 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
         out[2] = p0 * Li[2] + p1 * Li[6] + p2 * Li[10];
         out[3] = p0 * Li[3] + p1 * Li[7] + p2 * Li[11] + p3;
       }
-      bool changed = false;  // against the pose of the previous refit (bitwise; NaN-filled at creation)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        changed |= __double_as_longlong(a.world[12 * i + 4 * r + c]) != __double_as_longlong(out[c]);
-        sm.world[12 * i + 4 * r + c] = out[c];
-        a.world[12 * i + 4 * r + c] = out[c];
-      }
-      if (changed) a.dirty[i] = 1;
+      for (int c = 0; c < 4; ++c) sm.world[12 * i + 4 * r + c] = out[c];
     }
     __syncthreads();
+  }
+  // change flags against the poses of the previous refit (bitwise; NaN-filled
+  // at creation) and the device copy of the world poses, in one pass: one
+  // global round trip for the whole scene instead of one per tree level
+  for (int k = tid; k < 12 * P; k += kRefitThreads) {
+    const double w = sm.world[k];
+    if (__double_as_longlong(a.world[k]) != __double_as_longlong(w)) a.dirty[k / 12] = 1;
+    a.world[k] = w;
   }
 
   // 2-4. per part: lane r < 3 inverts row r in FP64; all four lanes share the
@@ -283,26 +291,33 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
       mx[2] = fmaxf(mx[2], cfz);
     }
   }
-  // bounding box of the sphere centres (block reduction)
+  // bounding box of the sphere centres: warp shuffles, then the eight warp
+  // results through shared memory (min and max are exact in any order)
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    sm.red[k * kRefitThreads + tid] = mn[k];
-    sm.red[(3 + k) * kRefitThreads + tid] = mx[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+      mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sm.red[k * kRefitWarps + (tid >> 5)] = mn[k];
+      sm.red[(3 + k) * kRefitWarps + (tid >> 5)] = mx[k];
+    }
   }
   __syncthreads();
-  for (int w = kRefitThreads / 2; w > 0; w >>= 1) {
-    if (tid < w) {
+  float bb[6];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float *lo = sm.red + k * kRefitThreads, *hi = sm.red + (3 + k) * kRefitThreads;
-        lo[tid] = fminf(lo[tid], lo[tid + w]);
-        hi[tid] = fmaxf(hi[tid], hi[tid + w]);
-      }
-    }
-    __syncthreads();
+  for (int k = 0; k < 6; ++k) {
+    float v = sm.red[k * kRefitWarps];
+    for (int w = 1; w < kRefitWarps; ++w) v = k < 3 ? fminf(v, sm.red[k * kRefitWarps + w]) : fmaxf(v, sm.red[k * kRefitWarps + w]);
+    bb[k] = v;
   }
-  const float bx0 = sm.red[0], by0 = sm.red[kRefitThreads], bz0 = sm.red[2 * kRefitThreads];
-  const float bx1 = sm.red[3 * kRefitThreads], by1 = sm.red[4 * kRefitThreads], bz1 = sm.red[5 * kRefitThreads];
+  const float bx0 = bb[0], by0 = bb[1], bz0 = bb[2];
+  const float bx1 = bb[3], by1 = bb[4], bz1 = bb[5];
   const float ex = fmaxf(bx1 - bx0, 1e-30f), ey = fmaxf(by1 - by0, 1e-30f), ez = fmaxf(bz1 - bz0, 1e-30f);
   // 5. Morton keys and a rank sort (P <= kMaxParts)
   for (int i = tid; i < P; i += kRefitThreads) {
