@@ -292,6 +292,19 @@ svo_status scene_set_transforms_trs(svo_scene *scene, const double *rts_15, void
  * Sec. IV-A) and rebuild the cluster level of the sphere hierarchy.  A
  * singular pose sets the device error word (svo_check_device). */
 svo_status scene_refit(svo_scene *scene, void *stream);
+/* scene_refit of n scenes of one context in one launch, a thread block per
+ * scene (async; Sec. III, Eq. 3, Sec. IV-A as scene_refit).  Each scene's
+ * refit is the same as scene_refit's, so the results are identical; the
+ * batch runs the scenes side by side on the GPU instead of one launch after
+ * another, for a frame that poses many scenes (a server's batch of
+ * requests, a batched trace).  scenes: n distinct scene handles.  local_dev:
+ * NULL, or n pointers, each NULL or a device array of that scene's
+ * n_parts*12 local poses (as scene_set_transforms_device, read by the
+ * launch, which also keeps the scene's own copy); a scene without one uses
+ * the poses its last scene_set_transforms / _device call set (host poses of
+ * a scene of at most 256 parts are read by the launch from the scene's
+ * page-locked staging buffer).  Launches of up to 64 scenes each. */
+svo_status scene_refit_batch(svo_scene *const *scenes, const double *const *local_dev, int32_t n, void *stream);
 /* Copy the last refit's per-part data to host arrays (any may be NULL) and
  * synchronise `stream`: world and inverse poses (n_parts*12 doubles each,
  * [A | b] rows), the FP32 rows used by tracing (n_parts*12 floats: the

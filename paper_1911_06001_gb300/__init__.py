@@ -151,6 +151,26 @@ class Context:
                                        0 if rf is None else rf.data_ptr(), width)
         _lib.check(self.lib.trace_batch(self.h, arr, len(items), int(flags), _ptr(stats), _stream_ptr(stream)))
 
+    def refit_batch(self, scenes, local_dev=None, stream=None) -> None:
+        """scene_refit of several scenes in one launch (a block per scene).
+        local_dev: None, or one entry per scene, each None or a CUDA float64
+        tensor of that scene's [P, 12] local poses."""
+        n = len(scenes)
+        if n == 0:
+            return
+        hs = (C.c_void_p * n)(*[sc.h.value for sc in scenes])
+        if local_dev is None:
+            ptrs = None
+        else:
+            if len(local_dev) != n:
+                raise ValueError("local_dev needs one entry per scene")
+            for sc, t in zip(scenes, local_dev):
+                if t is not None and (t.dtype.itemsize != 8 or not t.is_cuda or not t.is_contiguous()
+                                      or t.numel() != 12 * sc.n_parts):
+                    raise ValueError("local_dev entries: contiguous CUDA float64 tensors of n_parts*12")
+            ptrs = (C.c_void_p * n)(*[None if t is None else t.data_ptr() for t in local_dev])
+        _lib.check(self.lib.scene_refit_batch(hs, ptrs, n, _stream_ptr(stream)))
+
     def raygen(self, eye, target, width: int, height: int, fov_y_deg: float = 60.0, up=(0.0, 1.0, 0.0),
                tmin: float = 0.0, tmax: float = float("inf"), rays=None, stream=None):
         """Pinhole primary rays generated on the device: returns a CUDA float32 tensor [W*H, 8]."""

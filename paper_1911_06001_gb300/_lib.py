@@ -62,7 +62,7 @@ EXPORTS = [
     "svo_set_tile_order", "svo_get_tile_order",
     "svo_build_host", "svo_upload", "svo_release", "svo_asset_info", "svo_read_asset",
     "scene_create", "scene_destroy", "scene_set_transforms", "scene_set_transforms_device",
-    "scene_set_transforms_trs", "scene_refit",
+    "scene_set_transforms_trs", "scene_refit", "scene_refit_batch",
     "scene_read_poses", "scene_read_clusters", "trace_rays", "trace_batch", "trace_fix_pending",
     "trace_rays_host", "trace_rays_noalloc", "svo_raygen_pinhole", "trace_hit_colors",
     "trace_shade",
@@ -132,6 +132,7 @@ def load(path: str | None = None):
         "scene_set_transforms_device": ([vp, vp, vp], i32),
         "scene_set_transforms_trs": ([vp, vp, vp], i32),
         "scene_refit": ([vp, vp], i32),
+        "scene_refit_batch": ([C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), i32, vp], i32),
         "scene_read_poses": ([vp, vp, vp, vp, vp, vp], i32),
         "scene_read_clusters": ([vp, C.POINTER(i32), vp, vp, vp], i32),
         "trace_rays": ([vp, vp, u64, vp, vp, u32, vp, vp], i32),

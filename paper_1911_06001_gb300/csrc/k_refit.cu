@@ -122,18 +122,21 @@ __device__ __forceinline__ float norm_up(float x, float y, float z) {
   return __fsqrt_ru(__fmaf_ru(x, x, __fmaf_ru(y, y, __fmul_ru(z, z))));
 }
 
-template <bool INLINE, int CAP>
-__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses<CAP> poses) {
+// The pose pipeline of one scene, run by one block.  local: where the local
+// poses are read from; keep != nullptr: they are first copied to keep (the
+// scene's device copy, kept in step with what is composed), and with
+// read_keep the block then reads them back from there (a source in host
+// memory is read once).
+__device__ __forceinline__ void refit_scene(const RefitArgs &a, const double *local, double *keep, bool read_keep,
+                                            unsigned char *refit_smem) {
   const int P = a.n_parts;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  extern __shared__ __align__(16) unsigned char refit_smem[];
   const RefitSmem sm = carve(refit_smem, P, a.n_clusters, a.n_levels);
-  if (INLINE) {
-    // keep the device copy of the local poses in step with what is composed
-    for (int k = tid; k < P * 12; k += kRefitThreads) const_cast<double *>(a.local)[k] = poses.local[k];
+  if (keep) {
+    for (int k = tid; k < P * 12; k += kRefitThreads) keep[k] = local[k];
+    if (read_keep) local = keep;  // visible to the block after the barrier below
   }
-  const double *local = INLINE ? poses.local : a.local;
   // tree topology to shared memory (independent loads, one round trip)
   for (int i = tid; i < P; i += kRefitThreads) {
     sm.parent[i] = a.stat[i].parent;
@@ -393,6 +396,31 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __gr
 }
 
 template <bool INLINE, int CAP>
+__global__ void __launch_bounds__(kRefitThreads) k_refit(RefitArgs a, const __grid_constant__ InlinePoses<CAP> poses) {
+  extern __shared__ __align__(16) unsigned char refit_smem[];
+  // inline poses: composed from the parameter block, and copied to the
+  // scene's device copy on the way
+  refit_scene(a, INLINE ? poses.local : a.local, INLINE ? const_cast<double *>(a.local) : nullptr, false, refit_smem);
+}
+
+// Many scenes in one launch, one block each (scene_refit_batch): block b
+// refits B.a[b], reading its local poses from B.src[b] (device or mapped
+// host memory) when that is set.
+struct RefitBatch {
+  RefitArgs a[kRefitBatch];
+  const double *src[kRefitBatch];
+  int32_t n;
+};
+
+__global__ void __launch_bounds__(kRefitThreads) k_refit_batch(const __grid_constant__ RefitBatch B) {
+  extern __shared__ __align__(16) unsigned char refit_smem[];
+  const int b = blockIdx.x;
+  const RefitArgs &a = B.a[b];
+  const double *src = B.src[b];
+  refit_scene(a, src ? src : a.local, src ? const_cast<double *>(a.local) : nullptr, true, refit_smem);
+}
+
+template <bool INLINE, int CAP>
 cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, size_t smem, cudaStream_t stream) {
   InlinePoses<CAP> p;
   if (INLINE)
@@ -404,6 +432,27 @@ cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, size_t 
 }
 
 }  // namespace
+
+cudaError_t launch_refit_batch(const RefitArgs *args, const double *const *src, int n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kRefitBatch) return cudaErrorInvalidValue;
+  RefitBatch *B = new RefitBatch();  // about 9 KB: off the host stack
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    B->a[i] = args[i];
+    B->src[i] = src[i];
+    const size_t m = refit_smem_bytes(args[i].n_parts, args[i].n_clusters, args[i].n_levels, kRefitThreads);
+    smem = m > smem ? m : smem;
+  }
+  B->n = n;
+  cudaError_t e = cudaFuncSetAttribute(k_refit_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    k_refit_batch<<<n, kRefitThreads, smem, stream>>>(*B);
+    e = cudaGetLastError();
+  }
+  delete B;
+  return e;
+}
 
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
   static_assert(kInlinePoseParts == 256, "size classes below");

@@ -424,6 +424,29 @@ void scene_trace_config(const svo_scene *s, int *block, int *rays_per_lane) {
 svo_status set_last_error(svo_status code, const char *msg) { return fail(code, "%s", msg); }
 }  // namespace svo
 
+// Kernel arguments of one scene's refit.
+static RefitArgs refit_args(const svo_scene *s) {
+  RefitArgs a;
+  a.n_parts = s->P;
+  a.n_levels = s->L;
+  a.level_order = s->d_level_order;
+  a.level_start = s->d_level_start;
+  a.stat = s->d_stat;
+  a.local = s->d_local;
+  a.world = s->d_world;
+  a.inv64 = s->d_inv64;
+  a.hot = s->d_hot;
+  a.aux = s->d_aux;
+  a.clusters = s->d_cl;
+  a.order = s->d_order;
+  a.n_clusters = s->NC;
+  a.bound = s->d_bound;
+  a.dirty = s->d_dirty;
+  a.grid = s->grid_G > 0 ? s->d_grid : nullptr;
+  a.err = s->ctx->d_err;
+  return a;
+}
+
 extern "C" {
 
 const char *svo_last_error(void) { return g_last_error.c_str(); }
@@ -883,27 +906,55 @@ svo_status scene_set_transforms_device(svo_scene *s, const double *local_dev, vo
   return ok();
 }
 
+
+svo_status scene_refit_batch(svo_scene *const *scenes, const double *const *local_dev, int32_t n, void *stream) {
+  if (n < 0 || (n > 0 && !scenes)) return fail(SVO_ERR_ARG, "scene_refit_batch: bad scene list");
+  if (n == 0) return ok();
+  for (int i = 0; i < n; ++i) {
+    if (!scenes[i]) return fail(SVO_ERR_ARG, "scene_refit_batch: scene %d is NULL", i);
+    if (scenes[i]->ctx != scenes[0]->ctx) return fail(SVO_ERR_ARG, "scene_refit_batch: scene %d belongs to another context", i);
+    for (int j = 0; j < i; ++j)
+      if (scenes[j] == scenes[i]) return fail(SVO_ERR_ARG, "scene_refit_batch: scene %d appears twice", i);
+  }
+  CK(cudaSetDevice(scenes[0]->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int b = 0; b < n; b += kRefitBatch) {
+    const int cnt = (n - b) < kRefitBatch ? (n - b) : kRefitBatch;
+    RefitArgs args[kRefitBatch];
+    const double *src[kRefitBatch];
+    for (int k = 0; k < cnt; ++k) {
+      svo_scene *s = scenes[b + k];
+      args[k] = refit_args(s);
+      src[k] = local_dev ? local_dev[b + k] : nullptr;
+      if (src[k]) {
+        s->host_pending = false;  // the given device poses replace any set from the host
+      } else if (s->host_pending) {
+        // poses set from the host (small scenes): the kernel reads them from
+        // the scene's page-locked staging buffer through its device mapping
+        if (s->stage_pending) CK(cudaEventSynchronize(s->ev_stage));
+        memcpy(s->h_stage, s->h_local.data(), s->h_local.size() * sizeof(double));
+        void *mapped = nullptr;
+        CK(cudaHostGetDevicePointer(&mapped, s->h_stage, 0));
+        src[k] = static_cast<const double *>(mapped);
+        s->host_pending = false;
+      }
+    }
+    CK(launch_refit_batch(args, src, cnt, st));
+    for (int k = 0; k < cnt; ++k) {  // the staging buffers read by this launch stay untouched until it is done
+      svo_scene *s = scenes[b + k];
+      if (!local_dev || !local_dev[b + k]) {
+        CK(cudaEventRecord(s->ev_stage, st));
+        s->stage_pending = true;
+      }
+    }
+  }
+  return ok();
+}
+
 svo_status scene_refit(svo_scene *s, void *stream) {
   if (!s) return fail(SVO_ERR_ARG, "scene_refit: scene is NULL");
   CK(cudaSetDevice(s->ctx->device));
-  RefitArgs a;
-  a.n_parts = s->P;
-  a.n_levels = s->L;
-  a.level_order = s->d_level_order;
-  a.level_start = s->d_level_start;
-  a.stat = s->d_stat;
-  a.local = s->d_local;
-  a.world = s->d_world;
-  a.inv64 = s->d_inv64;
-  a.hot = s->d_hot;
-  a.aux = s->d_aux;
-  a.clusters = s->d_cl;
-  a.order = s->d_order;
-  a.n_clusters = s->NC;
-  a.bound = s->d_bound;
-  a.dirty = s->d_dirty;
-  a.grid = s->grid_G > 0 ? s->d_grid : nullptr;
-  a.err = s->ctx->d_err;
+  const RefitArgs a = refit_args(s);
   CK(launch_refit(a, s->host_pending ? s->h_local.data() : nullptr, (cudaStream_t)stream));
   s->host_pending = false;
   return ok();

@@ -244,6 +244,12 @@ struct RefitArgs {
 // host_local: when not NULL and n_parts <= kInlinePoseParts, the local poses
 // travel in the kernel parameters instead of through a device copy.
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream);
+// Scenes per launch of scene_refit_batch (kernel parameter space).
+constexpr int kRefitBatch = 64;
+// n <= kRefitBatch scenes in one launch, one block each; src[i]: where scene
+// i's local poses are read from (device or mapped host memory), or nullptr
+// for args[i].local.
+cudaError_t launch_refit_batch(const RefitArgs *args, const double *const *src, int n, cudaStream_t stream);
 
 // Grid (re)builds before a trace with SVO_TRACE_GRID: one block per distinct
 // scene, each a no-op unless the scene's grid is stale.

@@ -61,10 +61,10 @@ class BatchGraph:
     One replay copies every scene's local poses from a pinned host buffer to
     the device, composes / inverts / refits every scene, and runs
     ``trace_batch`` over all items (its ray-ordering launches, the persistent
-    trace kernel and the FP64 pass included).  The per-scene refits are
-    one-block kernels, so the graph fans them out over ``branches`` parallel
-    branches (side streams joined by events at capture) and they run side by
-    side on the device instead of one after another.
+    trace kernel and the FP64 pass included).  The refits are one launch
+    (``Context.refit_batch``: a thread block per scene, each reading its
+    poses straight from the copied buffer), so they run side by side on the
+    device instead of one after another.
 
     ``items``: (scene, rays, hits, ray_flags-or-None[, image_width]) as for
     ``Context.trace_batch``; ``local``: one [P, 12] FP64 pose array per
@@ -72,7 +72,7 @@ class BatchGraph:
     happens once, after an eager warm-up on the same streams has grown the
     library's per-stream scratch."""
 
-    def __init__(self, ctx: Context, items, local, flags: int = TRACE_DEFAULT, branches: int = 8):
+    def __init__(self, ctx: Context, items, local, flags: int = TRACE_DEFAULT):
         import torch
 
         self.ctx = ctx
@@ -89,9 +89,7 @@ class BatchGraph:
         self.host = torch.empty(n, dtype=torch.float64).pin_memory()
         self.dev = torch.empty(n, dtype=torch.float64, device=dev)
         self.stream = torch.cuda.Stream(device=dev)
-        self.side = [torch.cuda.Stream(device=dev) for _ in range(max(1, min(branches, len(self.scenes))))]
-        self.fork = torch.cuda.Event()
-        self.joins = [torch.cuda.Event() for _ in self.side]
+        self.pose_views = [self.dev[int(self.offsets[k]):int(self.offsets[k + 1])] for k in range(len(self.scenes))]
         self.done = torch.cuda.Event()
         self.set_poses(local)
         torch.cuda.synchronize()
@@ -112,23 +110,17 @@ class BatchGraph:
     def _frame(self) -> None:
         s = self.stream
         self.dev.copy_(self.host, non_blocking=True)
-        self.fork.record(s)
-        nb = len(self.side)
-        for b, side in enumerate(self.side):
-            side.wait_event(self.fork)
-            for k in range(b, len(self.scenes), nb):
-                sc = self.scenes[k]
-                sc.set_transforms_device(self.dev[self.offsets[k]:self.offsets[k + 1]], stream=side)
-                sc.refit(stream=side)
-            self.joins[b].record(side)
-        for e in self.joins:
-            s.wait_event(e)
+        self.ctx.refit_batch(self.scenes, self.pose_views, stream=s)
         self.ctx.trace_batch(self.items, flags=self.flags, stream=s)
 
     def replay(self, local=None) -> None:
-        """Run one batched frame on ``self.stream``; ``local`` (per scene [P, 12]
-        poses) replaces the poses first."""
+        """Run one batched frame on ``self.stream`` (asynchronously: the caller
+        orders its own stream after it, e.g. ``wait_stream``); ``local`` (per
+        scene [P, 12] poses) replaces the poses first."""
+        import torch
+
         if local is not None:
             self.set_poses(local)
-        self.graph.replay()
+        with torch.cuda.stream(self.stream):  # a graph launches on the current stream
+            self.graph.replay()
         self.done.record(self.stream)

@@ -256,11 +256,14 @@ class Server:
         now = time.perf_counter()
         s.start = torch.cuda.Event(enable_timing=True)
         s.start.record(s.stream)
+        # every request's scene instance is posed, then all are refitted by one
+        # launch (a block per instance; a batch leases distinct instances)
+        for t in batch:
+            t.instance.set_transforms(t.request.local, stream=s.stream)
+        self.ctx.refit_batch([t.instance for t in batch], stream=s.stream)
         for t in batch:
             r = t.request
             inst = t.instance
-            inst.set_transforms(r.local, stream=s.stream)
-            inst.refit(stream=s.stream)
             rays = s.rays[t.offset:t.offset + t.n_rays]
             hits = s.hits[t.offset:t.offset + t.n_rays]
             self.ctx.raygen(tuple(float(v) for v in r.eye), tuple(float(v) for v in r.target), int(r.width),

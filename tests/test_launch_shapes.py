@@ -313,8 +313,8 @@ def _small_batch(ctx):
 
 
 def test_batch_graph_replays_match_eager_batches(ctx):
-    """A batched frame (per-scene pose copies, refits fanned out over graph
-    branches, ordering, the persistent trace and the FP64 pass) replayed from
+    """A batched frame (one pose copy, every scene refitted by one batched
+    launch, ordering, the persistent trace and the FP64 pass) replayed from
     one CUDA graph gives bit-identical hits and flags to the eager
     trace_batch of the same poses, over several pose sets."""
     import torch
@@ -326,7 +326,7 @@ def test_batch_graph_replays_match_eager_batches(ctx):
     rng = np.random.default_rng(3)
     flags = g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN
     graph_items = [(sc, r, torch.empty_like(h), torch.zeros_like(f)) for sc, r, h, f in items]
-    bg = BatchGraph(ctx, graph_items, [s.local for s in bat.scenes], flags=flags, branches=4)
+    bg = BatchGraph(ctx, graph_items, [s.local for s in bat.scenes], flags=flags)
     for rep in range(3):
         local = []
         for s in bat.scenes:  # every root re-posed: a small rigid motion of each scene
@@ -337,6 +337,7 @@ def test_batch_graph_replays_match_eager_batches(ctx):
                 L[i] = np.hstack([A @ M[:, :3], (A @ M[:, 3] + rng.uniform(-0.3, 0.3, 3))[:, None]]).ravel()
             local.append(L)
         bg.replay(local)
+        torch.cuda.current_stream().wait_stream(bg.stream)  # the eager frame below re-poses the same scenes
         for (sc, _, _, _), L in zip(items, local):
             sc.set_transforms(L)
             sc.refit()
