@@ -1636,6 +1636,73 @@ __global__ void __launch_bounds__(kBlock) k_fix(const __grid_constant__ TraceLau
   // are re-traced afterwards by the whole warp, one at a time.
   static_assert(kContenders <= 16, "8-lane groups, two contenders per lane at most");
   const int sub = lane >> 3, sl = lane & 7;
+  if (n > 8ull * n_warps) {
+    // A long list (more than two rounds of four entries per warp): runs of 32
+    // entries per warp.  An entry with one stored leaf (every t refinement)
+    // takes one lane, so 32 of them share each FP64 instruction; entries with
+    // a contender list go four at a time in 8-lane groups; entries without
+    // one get the whole warp.  A short list keeps four entries per warp
+    // (below), which spreads it over more warps.
+    for (unsigned long long i0 = 32 * warp; i0 < n; i0 += 32 * n_warps) {
+      const unsigned long long i = i0 + (unsigned long long)lane;
+      const bool have = i < n;
+      const unsigned long long e = have ? L.fix_list[i] : 0ull;
+      const int nc = (int)(e >> 48);
+      if (have && nc == 1) {
+        const int it = (int)((e >> kRayBits) & 0x7Fu);
+        const unsigned long long ray = e & ((1ull << kRayBits) - 1ull);
+        const TraceItem &I = L.items[it];
+        const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
+        const uint4 cv = L.fix_cand[L.fix_off[i]];
+        const uint32_t p = cv.x;
+        const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
+        ExactState st;
+        st.t = Num<double>::inf();
+        st.part = kMissPart;
+        st.vox = kMissVoxel;
+        double tq;
+        if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
+        write_fixed(I, ray, st, ((e >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN);
+      }
+      for (unsigned int multi = __ballot_sync(0xffffffffu, have && nc >= 2); multi != 0u;) {
+        // the next four such entries, one 8-lane group each
+        int src = -1;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int s = multi ? __ffs(multi) - 1 : -1;
+          if (g == sub) src = s;
+          if (multi) multi &= multi - 1u;
+        }
+        const unsigned long long ee = __shfl_sync(0xffffffffu, e, src < 0 ? 0 : src);
+        const int ncg = src >= 0 ? (int)(ee >> 48) : 0;
+        const int it = (int)((ee >> kRayBits) & 0x7Fu);
+        const unsigned long long ray = ee & ((1ull << kRayBits) - 1ull);
+        ExactState st;
+        st.t = Num<double>::inf();
+        st.part = kMissPart;
+        st.vox = kMissVoxel;
+        if (sl < ncg) {
+          const TraceItem &I = L.items[it];
+          const float4 o = I.rays[2 * ray], d = I.rays[2 * ray + 1];
+          const uint32_t off = L.fix_off[i0 + (unsigned long long)src];
+          for (int q = sl; q < ncg; q += 8) {
+            const uint4 cv = L.fix_cand[off + q];
+            const uint32_t p = cv.x;
+            const unsigned long long vox = (unsigned long long)cv.y | ((unsigned long long)cv.z << 32);
+            double tq;
+            if (leaf_entry64(I.inv64 + 12 * p, I.aux[p].depth, vox, o, d, tq)) offer(st, tq, p, vox);
+          }
+        }
+        group_min8(st);
+        if (ncg > 0 && sl == 0)
+          write_fixed(L.items[it], ray, st, ((ee >> 47) & 1ull) ? SVO_RAY_T_REFINED : SVO_RAY_UNCERTAIN);
+      }
+      for (unsigned int pending = __ballot_sync(0xffffffffu, have && nc == 0); pending != 0u; pending &= pending - 1u) {
+        const int src = __ffs(pending) - 1;
+        overflow_retrace(L, i0 + (unsigned long long)src, __shfl_sync(0xffffffffu, e, src), tab, err, cnt);
+      }
+    }
+  } else
   for (unsigned long long i0 = 4 * warp; i0 < n; i0 += 4 * n_warps) {
     const unsigned long long i = i0 + (unsigned long long)sub;
     const bool have = i < n;
