@@ -312,7 +312,8 @@ def _small_batch(ctx):
     return bat, items
 
 
-def test_batch_graph_replays_match_eager_batches(ctx):
+@pytest.mark.parametrize("wavefront", [False, True])
+def test_batch_graph_replays_match_eager_batches(ctx, wavefront):
     """A batched frame (one pose copy, every scene refitted by one batched
     launch, ordering, the persistent trace and the FP64 pass) replayed from
     one CUDA graph gives bit-identical hits and flags to the eager
@@ -324,7 +325,7 @@ def test_batch_graph_replays_match_eager_batches(ctx):
 
     bat, items = _small_batch(ctx)
     rng = np.random.default_rng(3)
-    flags = g.TRACE_DEFAULT | g.TRACE_ORDER_ORIGIN
+    flags = g.TRACE_DEFAULT | (g.TRACE_WAVEFRONT if wavefront else g.TRACE_ORDER_ORIGIN)
     graph_items = [(sc, r, torch.empty_like(h), torch.zeros_like(f)) for sc, r, h, f in items]
     bg = BatchGraph(ctx, graph_items, [s.local for s in bat.scenes], flags=flags)
     for rep in range(3):

@@ -171,4 +171,14 @@ def test_wavefront_flag_combinations(ctx):
             gs.sc.trace(r, flags=bad)
     gs.sc.trace(r, flags=g.TRACE_DEFAULT | g.TRACE_WAVEFRONT)
     torch.cuda.synchronize()
+    # the entry point that allocates nothing has no queue: it refuses the shape
+    import ctypes as C
+
+    import paper_1911_06001_gb300._lib as L
+
+    lib = L.load()
+    h = torch.empty((r.shape[0], 2), dtype=torch.int64, device="cuda")
+    rc = lib.trace_rays_noalloc(gs.sc.h, C.c_void_p(r.data_ptr()), r.shape[0], C.c_void_p(h.data_ptr()), None,
+                                g.TRACE_DEFAULT | g.TRACE_WAVEFRONT, None)
+    assert rc == -1 and b"WAVEFRONT" in lib.svo_last_error()
     ctx.check_device()
