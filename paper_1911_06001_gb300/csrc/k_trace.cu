@@ -356,17 +356,27 @@ __device__ __forceinline__ uint2 node_at(const uint2 *__restrict__ nodes, uint32
   return __ldg(&nodes[idx]);
 }
 
-template <typename R, typename S, bool STATS, int STRIDE>
-__device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint2 *__restrict__ nodes, uint32_t n_nodes,
-                                             uint32_t top, int top_levels, int D, R ox, R oy,
-                                             R oz, R dx, R dy, R dz, R tmin, R tmax, R eta, R tshift, uint32_t part,
-                                             const Tables *__restrict__ tab, S &st, Contenders *con,
-                                             unsigned int &err, Counters &cnt) {
+// One part's front-to-back descent in progress: what the descent keeps
+// between node visits (its stack lives in shared memory).  The local ray
+// has every direction component made non-negative by mirroring (mir: the
+// mirrored axes), with reciprocals (ix, iy, iz) and b = -o * (1/d).
+template <typename R>
+struct Descent {
+  R ox, oy, oz, ix, iy, iz, bx, by, bz, tmin, tmax, eta, tshift;
+  const uint2 *nodes;
+  uint32_t n_nodes, part, top, mir;
+  int D, top_levels, level;
+  uint32_t px, py, pz;
+  uint32_t live;  // bit l: the stack entry of level l still has a child that may hold the closest hit
+  uint2 desc;     // the descriptor of the node visited next
+};
+
+// Starts a descent at the part's root (the caller has checked n_nodes > 0).
+template <typename R, bool STATS>
+__device__ __forceinline__ void descent_start(Descent<R> &s, const uint2 *__restrict__ nodes, uint32_t n_nodes,
+                                              uint32_t top, int top_levels, int D, R ox, R oy, R oz, R dx, R dy,
+                                              R dz, R tmin, R tmax, R eta, R tshift, uint32_t part, Counters &cnt) {
   static_assert(std::is_same<R, float>::value, "the stack stores FP32 entry parameters");
-  if (n_nodes == 0) return;
-  constexpr bool CERT = std::is_same<S, CertState>::value;
-  constexpr bool HYBRID = std::is_same<S, HybridState>::value;
-  constexpr bool INFLATE = sizeof(R) == 4;  // FP32 descents inflate boxes by eta
   uint32_t mir = 0;
   if (dx < R(0)) {
     ox = R(1) - ox;
@@ -386,8 +396,52 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
   dx = dx > Num<R>::tiny() ? dx : Num<R>::tiny();
   dy = dy > Num<R>::tiny() ? dy : Num<R>::tiny();
   dz = dz > Num<R>::tiny() ? dz : Num<R>::tiny();
-  const R ix = Num<R>::rcp(dx), iy = Num<R>::rcp(dy), iz = Num<R>::rcp(dz);
-  const R bx = -(ox * ix), by = -(oy * iy), bz = -(oz * iz);
+  s.ix = Num<R>::rcp(dx);
+  s.iy = Num<R>::rcp(dy);
+  s.iz = Num<R>::rcp(dz);
+  s.bx = -(ox * s.ix);
+  s.by = -(oy * s.iy);
+  s.bz = -(oz * s.iz);
+  s.ox = ox;
+  s.oy = oy;
+  s.oz = oz;
+  s.tmin = tmin;
+  s.tmax = tmax;
+  s.eta = eta;
+  s.tshift = tshift;
+  s.nodes = nodes;
+  s.n_nodes = n_nodes;
+  s.part = part;
+  s.top = top;
+  s.mir = mir;
+  s.D = D;
+  s.top_levels = top_levels;
+  s.level = 0;
+  s.px = s.py = s.pz = 0;
+  s.live = 0;
+  s.desc = node_at(nodes, top, top_levels, 0, 0u);
+  if (STATS) ++cnt.nodes;
+}
+
+// One node of a descent, in FP32 with boxes inflated by eta; (o, d) is the
+// local ray whose parameter is t - tshift, tmin / tmax in that parameter.
+// State S is CertState (the certified search: leaves give entry bounds) or
+// HybridState (the FP64 pass's re-trace: every leaf reached is decided by
+// leaf_entry64).  The node's child mask comes first, then a push and a step
+// down, its leaves, or a pop: a pop goes straight to the deepest level that
+// still has a child to visit, so levels with nothing left cost no step, and
+// a lane that pops is at its next node in the same step as lanes that
+// descend.  Returns false once the part is done.
+template <typename R, typename S, bool STATS, int STRIDE>
+__device__ __forceinline__ bool descent_step(Descent<R> &s, uint4 *__restrict__ stk, const Tables *__restrict__ tab,
+                                             S &st, Contenders *con, unsigned int &err, Counters &cnt) {
+  constexpr bool CERT = std::is_same<S, CertState>::value;
+  constexpr bool HYBRID = std::is_same<S, HybridState>::value;
+  constexpr bool INFLATE = sizeof(R) == 4;  // FP32 descents inflate boxes by eta
+  const R ox = s.ox, oy = s.oy, oz = s.oz, ix = s.ix, iy = s.iy, iz = s.iz, bx = s.bx, by = s.by, bz = s.bz;
+  const R tmin = s.tmin, tmax = s.tmax, eta = s.eta, tshift = s.tshift;
+  const uint32_t mir = s.mir, part = s.part;
+  const int D = s.D;
   // masks (true octant space) of the children lying in the far half along
   // each mirrored axis
   const uint32_t HX = (mir & 1u) ? 0x55u : 0xAAu;
@@ -395,19 +449,11 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
   const uint32_t HZ = (mir & 4u) ? 0x0Fu : 0xF0u;
   const uint8_t *__restrict__ qt = &tab->q[mir][0][0];
   const uint8_t *__restrict__ kt = &tab->k[mir][0][0];
-
-  int level = 0;
-  uint32_t px = 0, py = 0, pz = 0;
-  uint32_t live = 0;  // bit l: the stack entry of level l still has a child that may hold the closest hit
-  uint2 desc = node_at(nodes, top, top_levels, 0, 0u);
-  if (STATS) ++cnt.nodes;
-  // One loop, one node per iteration: every lane of the warp computes the
-  // child mask of its current node, then pushes and goes down, tests the
-  // leaves, or pops.  A pop goes straight to the deepest level that still has
-  // a child to visit, so levels with nothing left cost no iteration, and a
-  // lane that pops is at its next node in the same iteration as the lanes
-  // that descend (no lane waits for the others to finish a run of descents).
-  for (;;) {  // one node per iteration: its child mask, then a push, its leaves or a pop
+  int level = s.level;
+  uint32_t px = s.px, py = s.py, pz = s.pz;
+  uint32_t live = s.live;
+  const uint2 desc = s.desc;
+  {
     const R sz = Num<R>::pow2neg(level), h = sz * R(0.5);
     const R lx = R(px) * sz, ly = R(py) * sz, lz = R(pz) * sz;
     const R tl = rel_bound(st, tmax, tshift);
@@ -474,7 +520,7 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
             double tq;
             if (leaf_entry64(st.inv64, D, vox, st.o, st.d, tq)) offer(st.ex, tq, part, vox);
           } else {
-            static_assert(CERT || HYBRID, "descend_part: CertState or HybridState");
+            static_assert(CERT || HYBRID, "descent_step: CertState or HybridState");
           }
         }
       } else {
@@ -492,23 +538,25 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
         live = rest ? (live | (1u << level)) : (live & ~(1u << level));
         const uint32_t k = kt[p * 8 + q];
         const uint32_t idx = desc.x + __popc(cmask & ((1u << k) - 1u));
-        if (idx >= n_nodes) {
+        if (idx >= s.n_nodes) {
           err |= kErrNodeIndex;
-          return;
+          return false;
         }
-        desc = node_at(nodes, top, top_levels, level + 1, idx);
+        s.desc = node_at(s.nodes, s.top, s.top_levels, level + 1, idx);
         if (STATS) ++cnt.nodes;
         const uint32_t m = k ^ mir;
-        px = 2u * px + (m & 1u);
-        py = 2u * py + ((m >> 1) & 1u);
-        pz = 2u * pz + ((m >> 2) & 1u);
-        ++level;
-        continue;
+        s.px = 2u * px + (m & 1u);
+        s.py = 2u * py + ((m >> 1) & 1u);
+        s.pz = 2u * pz + ((m >> 2) & 1u);
+        s.level = level + 1;
+        s.live = live;
+        return true;
       }
     }
+  }
   for (;;) {  // pop to the deepest level above that still has a child to visit
     const uint32_t cand = live & ((1u << level) - 1u);
-    if (cand == 0u) return;
+    if (cand == 0u) return false;
     const int up = level - (31 - __clz(cand));
     level -= up;
     px >>= up;
@@ -540,19 +588,19 @@ __device__ __forceinline__ void descend_part(uint4 *__restrict__ stk, const uint
     const uint32_t k = kt[p * 8 + q];
     const uint32_t cmask = e.y & 0xFFu;
     const uint32_t idx = e.x + __popc(cmask & ((1u << k) - 1u));
-    if (idx >= n_nodes) {
+    if (idx >= s.n_nodes) {
       err |= kErrNodeIndex;
-      return;
+      return false;
     }
-    desc = node_at(nodes, top, top_levels, level + 1, idx);
+    s.desc = node_at(s.nodes, s.top, s.top_levels, level + 1, idx);
     if (STATS) ++cnt.nodes;
     const uint32_t m = k ^ mir;
-    px = 2u * px + (m & 1u);
-    py = 2u * py + ((m >> 1) & 1u);
-    pz = 2u * pz + ((m >> 2) & 1u);
-    ++level;
-    break;
-  }
+    s.px = 2u * px + (m & 1u);
+    s.py = 2u * py + ((m >> 1) & 1u);
+    s.pz = 2u * pz + ((m >> 2) & 1u);
+    s.level = level + 1;
+    s.live = live;
+    return true;
   }
 }
 
@@ -620,11 +668,13 @@ __device__ __forceinline__ bool cluster_cull(const RayW &r, const Cluster &c) {
 // stop: shared-memory address of the block's staged top-level nodes, of
 // which each part has its top `top_levels` levels (pa.spare0 carries, as
 // bits, the part's first staged node; 0 levels when nothing is staged).
-template <bool STATS, typename S = CertState, int STRIDE = kBlock>
-__device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
-                                               uint32_t part, const Tables *tab, uint32_t stop, int top_levels,
-                                               uint4 *stk, S &st, Contenders *con, unsigned int &err,
-                                               Counters &cnt) {
+// part_start sets up the descent (returns false when the part's box is
+// missed, starts beyond the bound, or the part is empty); trace_part_f32
+// runs it to the end.
+template <bool STATS, typename S>
+__device__ __forceinline__ bool part_start(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
+                                           uint32_t part, uint32_t stop, int top_levels, const S &st,
+                                           Descent<float> &ds, Counters &cnt) {
   const float4 a = ph.r0, b = ph.r1, c = ph.r2;
   const float4 s = ph.sphere;
   const float qx = fmaf(tref, r.dx, r.ox), qy = fmaf(tref, r.dy, r.oy), qz = fmaf(tref, r.dz, r.oz);
@@ -671,11 +721,23 @@ __device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph,
   }
   // nothing to do either when the box starts beyond the best certain hit so
   // far (the descent's own bound)
-  if (!(tmin_rel <= tmax_rel) || tmin_rel > rel_bound(st, tmax_rel, tref)) return;
+  if (!(tmin_rel <= tmax_rel) || tmin_rel > rel_bound(st, tmax_rel, tref)) return false;
   if (STATS) ++cnt.parts_entered;
-  descend_part<float, S, STATS, STRIDE>(stk, pa.nodes, pa.n_nodes, stop + 8u * __float_as_uint(pa.spare0), top_levels,
-                                        pa.depth, ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel, eta, tref, part, tab,
-                                        st, con, err, cnt);
+  if (pa.n_nodes == 0) return false;
+  descent_start<float, STATS>(ds, pa.nodes, pa.n_nodes, stop + 8u * __float_as_uint(pa.spare0), top_levels, pa.depth,
+                              ox, oy, oz, dx, dy, dz, tmin_rel, tmax_rel, eta, tref, part, cnt);
+  return true;
+}
+
+template <bool STATS, typename S = CertState, int STRIDE = kBlock>
+__device__ __forceinline__ void trace_part_f32(const RayW &r, const PartHot &ph, const PartAux &pa, float tref,
+                                               uint32_t part, const Tables *tab, uint32_t stop, int top_levels,
+                                               uint4 *stk, S &st, Contenders *con, unsigned int &err,
+                                               Counters &cnt) {
+  Descent<float> ds;
+  if (part_start<STATS, S>(r, ph, pa, tref, part, stop, top_levels, st, ds, cnt))
+    while (descent_step<float, S, STATS, STRIDE>(ds, stk, tab, st, con, err, cnt)) {
+    }
 }
 
 // Insert (t, p) into the sorted register list (ct, cp); the displaced largest
@@ -868,17 +930,23 @@ __device__ __forceinline__ int nth_set_bit(unsigned int m, int n) {
   return pos;
 }
 
-template <bool STATS, bool SPREAD = false>
+// VOTE false: a lane alone (no warp vote; its warp's lanes may hold rays of
+// different items), as the refilling descent launch calls it.
+template <bool STATS, bool SPREAD = false, bool VOTE = true>
 __device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, const PartHot *__restrict__ hot,
                                           const Cluster *__restrict__ cl, const int32_t *__restrict__ order,
                                           float last_t, int last_p, float (&ct)[kCap], float (&ce)[kCap],
                                           int (&cp)[kCap], float &over_t, Counters &cnt) {
+  static_assert(VOTE || !SPREAD, "spreading the member tests needs the warp vote");
   const int lane = threadIdx.x & 31;
   for (int c = 0; c < NC; ++c) {
     const Cluster cc = cl[c];
     const bool hc = need && cluster_cull(r, cc);
-    const unsigned int m = __ballot_sync(0xffffffffu, hc);
-    if (m == 0u) continue;  // no lane needs this cluster
+    unsigned int m = 0u;
+    if (VOTE) {
+      m = __ballot_sync(0xffffffffu, hc);
+      if (m == 0u) continue;  // no lane needs this cluster
+    }
     const uint32_t fc = __float_as_uint(cc.aux.w);
     const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
     const int nl = __popc(m);
@@ -939,17 +1007,7 @@ __device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, cons
   }
 }
 
-// The candidates of a ray's first culling pass, as the culling launch of
-// SVO_TRACE_WAVEFRONT queued them.
-struct PreCull {
-  float4 ct, ce;
-  int4 cp;
-  float over_t;
-};
-
-// PRE: the first pass's candidates come from `pre` (the culling launch ran
-// that pass) instead of from the spheres.
-template <bool STATS, int BLOCK, bool GRID, bool PRE = false>
+template <bool STATS, int BLOCK, bool GRID>
 __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P, int NC,
                               const PartHot *__restrict__ hot, const PartAux *__restrict__ aux,
                               const Cluster *__restrict__ cl, const int32_t *__restrict__ order, const Tables *tab,
@@ -957,8 +1015,7 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
                               unsigned int &err,
                               Counters &cnt,
                               bool reuse, uint32_t prev_part, const uint8_t *__restrict__ dirty, bool &reused,
-                              const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords,
-                              const PreCull *pre = nullptr) {
+                              const SceneGrid *__restrict__ grid, uint32_t *mbox, int mwords) {
   reused = false;
   st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
   st.part1 = kMissPart;
@@ -983,7 +1040,6 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
       if (STATS && need && walked) ++cnt.passes;
       need = need && !walked;
     }
-    bool first = true;
     while (__any_sync(0xffffffffu, need)) {
       float ct[kCap], ce[kCap];
       int cp[kCap];
@@ -994,19 +1050,8 @@ __device__ void trace_ray_f32(const RayW &r, bool active, uint32_t flags, int P,
         cp[i] = 0x7fffffff;
       }
       float over_t = Num<float>::inf();  // smallest entry that did not fit the list
-      if (PRE && first) {
-        static_assert(!PRE || kCap == 4, "a queued ray carries four candidates");
-        if (need) {
-          ct[0] = pre->ct.x, ct[1] = pre->ct.y, ct[2] = pre->ct.z, ct[3] = pre->ct.w;
-          ce[0] = pre->ce.x, ce[1] = pre->ce.y, ce[2] = pre->ce.z, ce[3] = pre->ce.w;
-          cp[0] = pre->cp.x, cp[1] = pre->cp.y, cp[2] = pre->cp.z, cp[3] = pre->cp.w;
-          over_t = pre->over_t;
-        }
-      } else {
-        if (STATS && need) ++cnt.passes;
-        cull_pass<STATS>(r, need, NC, hot, cl, order, last_t, last_p, ct, ce, cp, over_t, cnt);
-      }
-      first = false;
+      if (STATS && need) ++cnt.passes;
+      cull_pass<STATS>(r, need, NC, hot, cl, order, last_t, last_p, ct, ce, cp, over_t, cnt);
       // hit buffer reuse (Sec. IV-C, Fig. 5).  The paper reuses a pixel whose
       // ray meets one sphere, that of its unmoved previous part.  The same
       // holds whenever every part whose sphere the ray meets is unmoved and
@@ -1176,7 +1221,10 @@ __device__ __forceinline__ bool load_ray(const TraceItem &I, unsigned long long 
 // The result of one ray, called by every lane of the warp (in_range false: a
 // lane without a ray): the hit and its flags, and -- with FP64_FIX -- the
 // ray's entry in the FP64 pass's list with the leaves that pass needs.
-template <int NI, bool STATS>
+// LANE: a lane alone (its warp's other lanes are elsewhere in their work):
+// its list slot and pool entries come from atomics of its own instead of
+// one atomic per warp.
+template <int NI, bool STATS, bool LANE = false>
 __device__ __forceinline__ void finish_ray(const TraceLaunchT<NI> &L, const TraceItem &I, int it,
                                            unsigned long long ray, bool in_range, bool reused, const RayW &r,
                                            const PartAux *__restrict__ aux, const CertState &st,
@@ -1234,31 +1282,37 @@ __device__ __forceinline__ void finish_ray(const TraceLaunchT<NI> &L, const Trac
   // overflowed -- one entry carrying hi_min, where the full re-trace may
   // stop.  A ray the pool cannot hold is re-traced without that bound.
   if (L.flags & SVO_TRACE_FP64_FIX) {
-    const unsigned int m = __ballot_sync(0xffffffffu, flagged);
+    const unsigned int m = LANE ? (flagged ? 1u : 0u) : __ballot_sync(0xffffffffu, flagged);
     if (m) {
-      const int leader = __ffs(m) - 1;
       unsigned int ncon = 0;  // contenders in play
       if (flagged && !ids_ok && !con.overflow)
         for (int q = 0; q < con.n; ++q) ncon += (con.lo[q] <= st.hi_min) ? 1u : 0u;
       const unsigned int need = !flagged ? 0u : (ids_ok || con.overflow || ncon == 0u) ? 1u : ncon;
-      unsigned int incl = need;  // inclusive scan of the lanes' pool entries
+      unsigned long long slot = 0, off = 0;
+      if (LANE) {
+        slot = atomicAdd(L.fix_count, 1u);
+        off = atomicAdd(L.cand_count, need);
+      } else {
+        const int leader = __ffs(m) - 1;
+        unsigned int incl = need;  // inclusive scan of the lanes' pool entries
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned int basei = 0, basep = 0;
+        if (lane == leader) {
+          basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
+          basep = atomicAdd(L.cand_count, total);
+        }
+        basei = __shfl_sync(0xffffffffu, basei, leader);
+        basep = __shfl_sync(0xffffffffu, basep, leader);
+        slot = basei + __popc(m & ((1u << lane) - 1u));
+        off = (unsigned long long)basep + (incl - need);
       }
-      const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned int basei = 0, basep = 0;
-      if (lane == leader) {
-        basei = atomicAdd(L.fix_count, (unsigned int)__popc(m));
-        basep = atomicAdd(L.cand_count, total);
-      }
-      basei = __shfl_sync(0xffffffffu, basei, leader);
-      basep = __shfl_sync(0xffffffffu, basep, leader);
       if (flagged) {
-        const unsigned long long slot = basei + __popc(m & ((1u << lane) - 1u));
         if (slot < L.fix_capacity) {
-          const unsigned long long off = (unsigned long long)basep + (incl - need);
           const bool stored = off + need <= L.cand_capacity;
           unsigned long long nc = 0;  // leaves listed; 0 = full FP64 re-trace
           if (stored) {
@@ -1297,16 +1351,9 @@ __device__ __forceinline__ void finish_ray(const TraceLaunchT<NI> &L, const Trac
 // TOP: the top levels of every part staged in shared memory (a separate
 // instantiation: the staged-node base is one more live register, which the
 // common kernel does not carry).
-// QUEUE: the descent launch of SVO_TRACE_WAVEFRONT: a warp's tile is 32
-// consecutive entries of one item's region of the ray queue, each a ray with
-// the candidates of its first culling pass (k_cull ran that pass), and the
-// trace goes on from those candidates.  It keeps 16 warps per SM, as the
-// counting build does: at 24 the queued candidates would spill.
-template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID, bool TOP = false, bool QUEUE = false>
-__global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID || QUEUE ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
+template <int NI, bool STATS, int BLOCK, bool REUSE, bool GRID, bool TOP = false>
+__global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceThreadsPerSM) / BLOCK) k_trace(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // QUEUE: the first tile of each item's queue region, from the queue counts
-  __shared__ unsigned long long sQT[QUEUE ? NI + 1 : 1];
   // [tables | traversal stacks, level-major | staged part tables]
   Tables *tab = reinterpret_cast<Tables *>(smem);
   uint4 *sStack = reinterpret_cast<uint4 *>(smem + kTablesBytes) + threadIdx.x;
@@ -1342,40 +1389,17 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID || QUEUE ? 512 
       for (int k = threadIdx.x; k < t.y; k += BLOCK) sTop[t.x + k] = __ldg(&src[k]);
     }
   }
-  if (QUEUE && threadIdx.x == 0) {
-    unsigned long long acc = 0;
-    for (int i = 0; i < L.n_items; ++i) {
-      sQT[i] = acc;
-      const unsigned long long q = min((unsigned long long)L.queue_count[i], L.items[i].n);
-      acc += (q + 31ull) / 32ull;
-    }
-    sQT[L.n_items] = acc;
-  }
   __syncthreads();  // the only block barrier: warps then take tiles independently
   unsigned int err = 0;
   Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   uint32_t n_rays = 0, n_flag = 0;
   const int lane = threadIdx.x & 31;
-  const unsigned long long n_tiles = QUEUE ? sQT[QUEUE ? L.n_items : 0] : L.n_tiles;
   for (;;) {
     unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(QUEUE ? L.queue_tile : L.tile_counter, 1ull);
+    if (lane == 0) tile = atomicAdd(L.tile_counter, 1ull);
     tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= n_tiles) break;
-    int it = 0;
-    if (QUEUE) {
-      int lo = 0, hi = L.n_items - 1;  // the item whose tiles hold this one
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sQT[mid] <= tile)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      it = lo;
-    } else {
-      it = find_item(L, tile);
-    }
+    if (tile >= L.n_tiles) break;
+    const int it = find_item(L, tile);
     const TraceItem &I = L.items[it];
     const int P = I.n_parts, NC = I.n_clusters;
     const bool staged = L.one_scene != 0;
@@ -1383,42 +1407,23 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID || QUEUE ? 512 
     const PartAux *aux = staged ? sAux : I.aux;
     const Cluster *cls = staged ? sCl : I.clusters;
     const int32_t *ord = staged ? sOrd : I.order;
-    const int rpl = QUEUE ? 1 : L.rays_per_lane;
+    const int rpl = L.rays_per_lane;
 #pragma unroll 1
     for (int j = 0; j < rpl; ++j) {
       bool in_range = false;
-      unsigned long long ray = 0;
-      PreCull pc;
-      if (QUEUE) {
-        const unsigned long long e = (tile - sQT[it]) * 32ull + (unsigned long long)lane;
-        in_range = e < min((unsigned long long)L.queue_count[it], I.n);
-        pc.ct = pc.ce = make_float4(0.f, 0.f, 0.f, 0.f);
-        pc.cp = make_int4(0, 0, 0, 0);
-        pc.over_t = 0.f;
-        if (in_range) {
-          const QueueEntry *q = L.queue + I.qbase + e;
-          const uint4 id = q->id;
-          ray = (unsigned long long)id.x | ((unsigned long long)id.y << 32);
-          pc.over_t = __uint_as_float(id.z);
-          pc.ct = q->ct;
-          pc.ce = q->ce;
-          pc.cp = q->cp;
-        }
-      } else {
-        ray = tile_ray(L, I, tile, j, lane, in_range);
-      }
+      const unsigned long long ray = tile_ray(L, I, tile, j, lane, in_range);
       RayW r;
       const bool active = load_ray(I, ray, in_range, r);
-      if (STATS && in_range && !QUEUE) ++n_rays;  // the culling launch counted the queued rays
+      if (STATS && in_range) ++n_rays;
       CertState st;
       Contenders con;
       const bool reuse = REUSE && active;
       const uint32_t prev_part = reuse ? reinterpret_cast<const uint32_t *>(&I.hits[ray])[1] : kMissPart;
       bool reused;
-      trace_ray_f32<STATS, BLOCK, GRID, QUEUE>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sTopAddr,
-                                               (TOP && ntop_all > 0) ? L.top_levels : 0, sStack, st, con,
-                                               err, cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr,
-                                               sMbox, L.mbox_words, QUEUE ? &pc : nullptr);
+      trace_ray_f32<STATS, BLOCK, GRID>(r, active, L.flags, P, NC, hot, aux, cls, ord, tab, sTopAddr,
+                                        (TOP && ntop_all > 0) ? L.top_levels : 0, sStack, st, con,
+                                        err, cnt, reuse, prev_part, I.dirty, reused, GRID ? I.grid : nullptr,
+                                        sMbox, L.mbox_words);
       finish_ray<NI, STATS>(L, I, it, ray, in_range, reused, r, aux, st, con, lane, err, cnt, n_flag);
     }
   }
@@ -1505,6 +1510,188 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_cull(const __grid_const
     }
   }
   if (STATS) flush_stats(L.stats, cnt, n_rays, 0u);
+}
+
+// The descent launch of SVO_TRACE_WAVEFRONT.  Every lane works through the
+// queued rays on its own: when its part's descent ends it goes on to the
+// ray's next candidate, a further culling pass, or the ray's result and the
+// next queued ray, while the other lanes of its warp carry on with their
+// own descents.  A warp thus stays full until the queue runs dry, instead
+// of waiting for the longest of a tile's 32 descents (incoherent rays into
+// assets of different depths descend for very different lengths).  Each
+// step of the loop: lanes that need a ray take the next entries of the
+// warp's claimed run (32 entries claimed with one atomic), lanes between
+// parts set up their next part, and every lane in a descent takes one node.
+// The arithmetic is that of the fused kernel: part_start, descent_step,
+// cull_pass and finish_ray, so results are the same bit for bit.
+constexpr int kRefillLanes = 16;  // lanes that wait before the warp serves them
+
+template <int NI, bool STATS, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_descend(const __grid_constant__ TraceLaunchT<NI> L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long sQE[NI + 1];  // first entry of each item in the flat order of all queued rays
+  // [tables | traversal stacks, level-major | staged part tables]
+  Tables *tab = reinterpret_cast<Tables *>(smem);
+  uint4 *sStack = reinterpret_cast<uint4 *>(smem + kTablesBytes) + threadIdx.x;
+  const int sp = L.one_scene ? L.items[0].n_parts : 0;
+  const int sc = L.one_scene ? L.items[0].n_clusters : 0;
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem + kTablesBytes + (size_t)L.stack_levels * BLOCK * sizeof(uint4));
+  PartAux *sAux = reinterpret_cast<PartAux *>(sHot + sp);
+  Cluster *sCl = reinterpret_cast<Cluster *>(sAux + sp);
+  int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
+  load_tables(tab);
+  if (L.one_scene) {
+    const TraceItem &I0 = L.items[0];
+    for (int i = threadIdx.x; i < I0.n_parts; i += BLOCK) {
+      sHot[i] = I0.hot[i];
+      sAux[i] = I0.aux[i];
+      sOrd[i] = I0.order[i];
+    }
+    for (int i = threadIdx.x; i < I0.n_clusters; i += BLOCK) sCl[i] = I0.clusters[i];
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int i = 0; i < L.n_items; ++i) {
+      sQE[i] = acc;
+      acc += min((unsigned long long)L.queue_count[i], L.items[i].n);
+    }
+    sQE[L.n_items] = acc;
+  }
+  __syncthreads();  // the only block barrier
+  const unsigned long long total = sQE[L.n_items];
+  const bool staged = L.one_scene != 0;
+  unsigned int err = 0;
+  Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t n_flag = 0;
+  const int lane = threadIdx.x & 31;
+  enum { kNeedRay = 0, kBetween = 1, kDescending = 2, kDone = 3 };
+  int state = kNeedRay;
+  int it = 0;
+  unsigned long long ray = 0;
+  RayW r;
+  CertState st;
+  Contenders con;
+  float ct[kCap], ce[kCap];
+  int cp[kCap];
+  float over_t = 0.f, last_t = 0.f;
+  int last_p = -1;
+  bool stopped = false;
+  Descent<float> ds;
+  unsigned long long wnext = 0, wend = 0;  // the warp's claimed run of entries (warp-uniform)
+  for (;;) {
+    // lanes waiting for work are served together, once enough of them wait
+    // (or no lane is descending): the set-up of a part and the result of a
+    // ray then run for many lanes at a time
+    const unsigned int waiting = __ballot_sync(0xffffffffu, state == kNeedRay || state == kBetween);
+    const bool serve = __popc(waiting) >= kRefillLanes || !__any_sync(0xffffffffu, state == kDescending);
+    // lanes that need a ray take the next entries of the warp's run
+    unsigned int want = serve ? __ballot_sync(0xffffffffu, state == kNeedRay) : 0u;
+    while (want) {
+      if (wnext >= wend) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(L.queue_tile, 32ull);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        wnext = b;
+        wend = b + 32ull < total ? b + 32ull : total;
+        if (wnext >= total) {
+          if (want & (1u << lane)) state = kDone;  // the queue is empty
+          break;
+        }
+      }
+      const unsigned int take = min((unsigned int)__popc(want), (unsigned int)(wend - wnext));
+      const unsigned int rank = __popc(want & ((1u << lane) - 1u));
+      if ((want & (1u << lane)) && rank < take) {
+        const unsigned long long g = wnext + rank;
+        int lo = 0, hi = L.n_items - 1;  // the item holding flat entry g
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sQE[mid] <= g)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        it = lo;
+        const TraceItem &I = L.items[it];
+        const QueueEntry *q = L.queue + I.qbase + (g - sQE[it]);
+        const uint4 id = q->id;
+        ray = (unsigned long long)id.x | ((unsigned long long)id.y << 32);
+        over_t = __uint_as_float(id.z);
+        const float4 a = q->ct, b = q->ce;
+        const int4 c = q->cp;
+        static_assert(kCap == 4, "a queued ray carries four candidates");
+        ct[0] = a.x, ct[1] = a.y, ct[2] = a.z, ct[3] = a.w;
+        ce[0] = b.x, ce[1] = b.y, ce[2] = b.z, ce[3] = b.w;
+        cp[0] = c.x, cp[1] = c.y, cp[2] = c.z, cp[3] = c.w;
+        load_ray(I, ray, true, r);  // a queued ray is a ray: the culling launch checked it
+        st.lo1 = st.hi1 = st.te1 = st.lo2 = st.hi_min = Num<float>::inf();
+        st.part1 = kMissPart;
+        st.cert1 = 0;
+        st.vox1 = kMissVoxel;
+        con.n = 0;
+        con.overflow = false;
+        last_t = -Num<float>::inf();
+        last_p = -1;
+        stopped = false;
+        state = kBetween;
+      }
+      // warp-uniform bookkeeping of the run and of the lanes still waiting
+      unsigned int served = 0u, w = want;
+      for (unsigned int k = 0; k < take; ++k) {
+        served |= w & (0u - w);  // lowest waiting lane
+        w &= w - 1u;
+      }
+      want &= ~served;
+      wnext += take;
+    }
+    // lanes between parts: the next candidate, a further culling pass, or the ray's result
+    while (serve && state == kBetween) {
+      const TraceItem &I = L.items[it];
+      const PartHot *hot = staged ? sHot : I.hot;
+      const PartAux *aux = staged ? sAux : I.aux;
+      if (ct[0] != Num<float>::inf()) {
+        const float tin = ct[0], tref = ce[0];
+        const int p = cp[0];
+#pragma unroll
+        for (int i = 0; i < kCap - 1; ++i) {
+          ct[i] = ct[i + 1];
+          ce[i] = ce[i + 1];
+          cp[i] = cp[i + 1];
+        }
+        ct[kCap - 1] = Num<float>::inf();
+        if (tin > prune_bound(st, r.tmax)) {  // this and every later candidate start beyond the best hit
+          stopped = true;
+#pragma unroll
+          for (int i = 0; i < kCap; ++i) ct[i] = Num<float>::inf();
+          continue;
+        }
+        last_t = tin;
+        last_p = p;
+        if (part_start<STATS, CertState>(r, hot[p], aux[p], tref, (uint32_t)p, 0u, 0, st, ds, cnt)) state = kDescending;
+        continue;
+      }
+      if (!stopped && over_t < Num<float>::inf() && over_t <= prune_bound(st, r.tmax)) {
+        // some candidate did not fit the list and may still matter: another pass
+#pragma unroll
+        for (int i = 0; i < kCap; ++i) {
+          ct[i] = Num<float>::inf();
+          ce[i] = 0.f;
+          cp[i] = 0x7fffffff;
+        }
+        over_t = Num<float>::inf();
+        if (STATS) ++cnt.passes;
+        cull_pass<STATS, false, false>(r, true, I.n_clusters, hot, staged ? sCl : I.clusters, staged ? sOrd : I.order,
+                                       last_t, last_p, ct, ce, cp, over_t, cnt);
+        continue;
+      }
+      finish_ray<NI, STATS, true>(L, I, it, ray, true, false, r, aux, st, con, lane, err, cnt, n_flag);
+      state = kNeedRay;
+    }
+    if (__all_sync(0xffffffffu, state == kDone)) break;
+    if (state == kDescending && !descent_step<float, CertState, STATS, BLOCK>(ds, sStack, tab, st, &con, err, cnt))
+      state = kBetween;
+  }
+  if (STATS) flush_stats(L.stats, cnt, 0u, n_flag);
+  if (err) atomicOr(L.err, err);
 }
 
 // ------------------------------------------------------------- FP64 pass
@@ -1830,8 +2017,7 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
     if (e != cudaSuccess) return e;
     // the number of queued rays is known on the device only: a full persistent grid
     const size_t smem = trace_smem_bytes(L.stack_levels, parts, clusters, BLOCK, 0, 0);
-    auto kq = stats ? k_trace<NI, true, BLOCK, false, false, false, true>
-                    : k_trace<NI, false, BLOCK, false, false, false, true>;
+    auto kq = stats ? k_descend<NI, true, BLOCK> : k_descend<NI, false, BLOCK>;
     e = blocks_per_sm(kq, BLOCK, smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
