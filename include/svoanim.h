@@ -339,7 +339,10 @@ svo_status trace_rays(svo_scene *scene, const float *rays, uint64_t n, svo_hit *
  * FP64 list; hits still land at each ray's own index.) */
 /* Batched trace: every item's rays against its own scene, in one persistent
  * launch whose thread blocks take fixed-size tiles of rays from a device work
- * counter (async).  Items may reference different scenes of the context. */
+ * counter (async), or -- with SVO_TRACE_WAVEFRONT -- in a culling launch and a
+ * descent launch over all items' queued rays.  Items may reference different
+ * scenes of the context; flags and per-stream scratch are those of
+ * trace_rays, sized to the batch's total ray count. */
 svo_status trace_batch(svo_ctx *ctx, const svo_batch_item *items, int32_t n_items, uint32_t flags,
                        svo_trace_stats *stats, void *stream);
 
