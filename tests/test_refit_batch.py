@@ -147,3 +147,31 @@ def test_refit_batch_rejects_bad_lists(ctx):
     ctx.refit_batch([sc])
     ctx.check_device()
     sc.close()
+
+
+def test_refit_batch_more_scenes_than_one_launch_takes(ctx):
+    """70 scenes: two launches (64 + 6), each scene as scene_refit leaves it."""
+    import torch
+
+    rng = np.random.default_rng(7)
+    pool = synthetic.asset_pool(range(4, 6), 2, seed=9)
+    handles = [ctx.upload(p.asset.depth, p.asset.leaf_ids, p.asset.rgb) for p in pool]
+    single, batched = [], []
+    for k in range(70):
+        P = int(rng.integers(1, 12))
+        parent = np.array([-1] + [int(rng.integers(0, i)) for i in range(1, P)], dtype=np.int32)
+        assets = [handles[int(a)] for a in rng.integers(0, len(handles), P)]
+        L = _poses(rng, parent)
+        a = ctx.scene(assets, parent)
+        b = ctx.scene(assets, parent)
+        a.set_transforms(L)
+        a.refit()
+        b.set_transforms(L)
+        single.append(a)
+        batched.append(b)
+    ctx.refit_batch(batched)
+    torch.cuda.synchronize()
+    for a, b in zip(single, batched):
+        _equal(_state(a), _state(b))
+    for sc in single + batched:
+        sc.close()
