@@ -906,7 +906,6 @@ svo_status scene_set_transforms_device(svo_scene *s, const double *local_dev, vo
   return ok();
 }
 
-
 svo_status scene_refit_batch(svo_scene *const *scenes, const double *const *local_dev, int32_t n, void *stream) {
   if (n < 0 || (n > 0 && !scenes)) return fail(SVO_ERR_ARG, "scene_refit_batch: bad scene list");
   if (n == 0) return ok();
