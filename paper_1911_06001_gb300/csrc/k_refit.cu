@@ -30,6 +30,8 @@
 
 #include <cfloat>
 #include <cmath>
+#include <memory>
+#include <mutex>
 
 #include "svo_internal.h"
 
@@ -436,22 +438,38 @@ cudaError_t launch_refit_t(const RefitArgs &a, const double *host_local, size_t 
 cudaError_t launch_refit_batch(const RefitArgs *args, const double *const *src, int n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   if (n > kRefitBatch) return cudaErrorInvalidValue;
-  RefitBatch *B = new RefitBatch();  // about 9 KB: off the host stack
+  // the parameter block (about 9 KB): one per host thread, allocated on its
+  // first batched refit, so it stays off the caller's stack and no call
+  // allocates it afresh
+  thread_local std::unique_ptr<RefitBatch> block;
+  if (!block) block.reset(new RefitBatch());
+  RefitBatch &B = *block;
   size_t smem = 0;
   for (int i = 0; i < n; ++i) {
-    B->a[i] = args[i];
-    B->src[i] = src[i];
+    B.a[i] = args[i];
+    B.src[i] = src[i];
     const size_t m = refit_smem_bytes(args[i].n_parts, args[i].n_clusters, args[i].n_levels, kRefitThreads);
     smem = m > smem ? m : smem;
   }
-  B->n = n;
-  cudaError_t e = cudaFuncSetAttribute(k_refit_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
-    k_refit_batch<<<n, kRefitThreads, smem, stream>>>(*B);
-    e = cudaGetLastError();
+  B.n = n;
+  // the shared-memory attribute only ever grows: set it when this launch needs more (per device)
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static size_t admitted[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (smem > admitted[dev]) {
+      e = cudaFuncSetAttribute(k_refit_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      admitted[dev] = smem;
+    }
   }
-  delete B;
-  return e;
+  k_refit_batch<<<n, kRefitThreads, smem, stream>>>(B);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_refit(const RefitArgs &a, const double *host_local, cudaStream_t stream) {
