@@ -13,7 +13,10 @@ Per request, on its slot's stream: the request's pose goes to a leased
 pose tables, so concurrent requests of one scene can carry different poses),
 the instance is refitted, and the camera's primary rays are generated on the
 device.  Latency is measured from the request's arrival to the host observing
-its batch's completion event.
+its batch's completion event.  The serving loops run with Python's cyclic
+garbage collector paused (reference counting still frees what they drop): a
+full collection in a process holding many objects stops the host for tens to
+hundreds of milliseconds, and every request in flight would wait it out.
 
 Host-side scheduling only; every per-ray and per-frame step runs in the
 library's kernels.
@@ -22,6 +25,8 @@ library's kernels.
 from __future__ import annotations
 
 import collections
+import contextlib
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -154,10 +159,11 @@ class Server:
 
     def __init__(self, ctx: Context, scenes, n_slots: int = 3, max_batch_rays: int = 8 << 20,
                  memory_budget: int | None = None, instances_per_scene: int = 3, flags: int = TRACE_DEFAULT,
-                 max_wait: float | None = None):
+                 max_wait: float | None = None, pause_gc: bool = True):
         import torch
 
         self.ctx = ctx
+        self.pause_gc = bool(pause_gc)
         self.flags = int(flags)
         self.dev = torch.device("cuda", ctx.device)
         self.instances = []
@@ -290,18 +296,19 @@ class Server:
         the tickets in completion order.  ``on_done(ticket)`` runs for every
         completed ticket while its hits are still valid."""
         self.on_done = on_done
-        t0 = time.perf_counter()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         tickets = []
-        while pending or not self.idle():
-            now = time.perf_counter()
-            while pending and t0 + pending[0].arrival <= now:
-                r = pending.popleft()
-                tickets.append(self.submit(r, arrival=t0 + r.arrival))
-            before = len(self.completed)
-            launched = self.step()
-            if not launched and len(self.completed) == before:
-                time.sleep(20e-6)
+        with gc_paused(self.pause_gc):
+            t0 = time.perf_counter()
+            while pending or not self.idle():
+                now = time.perf_counter()
+                while pending and t0 + pending[0].arrival <= now:
+                    r = pending.popleft()
+                    tickets.append(self.submit(r, arrival=t0 + r.arrival))
+                before = len(self.completed)
+                launched = self.step()
+                if not launched and len(self.completed) == before:
+                    time.sleep(20e-6)
         self.on_done = None
         return tickets
 
@@ -317,25 +324,43 @@ def render_alone(ctx: Context, scene_handle, request, flags: int = TRACE_DEFAULT
     return rays, hits
 
 
-def run_unbatched(ctx: Context, scene_handles, requests, flags: int = TRACE_DEFAULT) -> list:
+def run_unbatched(ctx: Context, scene_handles, requests, flags: int = TRACE_DEFAULT, pause_gc: bool = True) -> list:
     """The baseline: the same request stream served one request at a time, each
     traced alone as soon as it has arrived and the previous one has finished.
     Returns (arrival, done, n_rays, device ms) per request."""
     import torch
 
-    t0 = time.perf_counter()
     out = []
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for r in sorted(requests, key=lambda q: q.arrival):
-        while time.perf_counter() < t0 + r.arrival:
-            pass
-        ev[0].record(stream)
-        render_alone(ctx, scene_handles[r.scene], r, flags=flags, stream=stream)
-        ev[1].record(stream)
-        stream.synchronize()
-        out.append((t0 + r.arrival, time.perf_counter(), int(r.width) * int(r.height), ev[0].elapsed_time(ev[1])))
+    order = sorted(requests, key=lambda q: q.arrival)
+    with gc_paused(pause_gc):
+        t0 = time.perf_counter()
+        for r in order:
+            while time.perf_counter() < t0 + r.arrival:
+                pass
+            ev[0].record(stream)
+            render_alone(ctx, scene_handles[r.scene], r, flags=flags, stream=stream)
+            ev[1].record(stream)
+            stream.synchronize()
+            out.append((t0 + r.arrival, time.perf_counter(), int(r.width) * int(r.height),
+                        ev[0].elapsed_time(ev[1])))
     return out
+
+
+@contextlib.contextmanager
+def gc_paused(pause: bool = True):
+    """Pause Python's cyclic garbage collector for the duration (when it is on
+    and ``pause`` is set), and put it back as it was afterwards, also on an
+    exception."""
+    was = gc.isenabled()
+    if pause and was:
+        gc.disable()
+    try:
+        yield
+    finally:
+        if pause and was:
+            gc.enable()
 
 
 def latency_stats(pairs) -> dict:

@@ -6,11 +6,12 @@ reach the GPU)."""
 
 from __future__ import annotations
 
+import gc
 from dataclasses import dataclass
 
 import pytest
 
-from paper_1911_06001_gb300.serving import AdmissionError, RequestQueue, Ticket
+from paper_1911_06001_gb300.serving import AdmissionError, RequestQueue, Ticket, gc_paused
 
 
 @dataclass
@@ -82,3 +83,24 @@ def test_expiry_and_cancellation():
     q2.submit(_t(5, arrival=-1e9))
     assert q2.expire(now=0.0) == [] and len(q2) == 1
 
+
+
+def test_gc_paused_restores_the_collector_state():
+    was = gc.isenabled()
+    try:
+        gc.enable()
+        with gc_paused():
+            assert not gc.isenabled()
+        assert gc.isenabled()
+        with pytest.raises(RuntimeError):
+            with gc_paused():
+                raise RuntimeError("a failing serving loop")
+        assert gc.isenabled()
+        with gc_paused(False):
+            assert gc.isenabled()
+        gc.disable()
+        with gc_paused():
+            assert not gc.isenabled()
+        assert not gc.isenabled()  # a collector that was off stays off
+    finally:
+        (gc.enable if was else gc.disable)()
