@@ -905,93 +905,23 @@ __device__ __forceinline__ bool grid_walk(const RayW &r, bool go, const SceneGri
 // part) that come after (last_t, last_p), the last part an earlier pass
 // descended, and in over_t the smallest entry that did not fit the list.
 // Called by the whole warp (need: this lane's ray takes part); NC must be
-// the same on every lane.
-//
-// The list holds the kCap smallest (t, part) keys and over_t the smallest t
-// of the others whatever the order of insertion, so the member tests may be
-// dealt out in any order.  SPREAD: when few lanes meet a cluster (incoherent
-// rays), its (lane, member) pairs are dealt over the warp's lanes -- each
-// lane tests one member against the ray of the lane that met the cluster,
-// read by shuffles -- and every hit is handed back to its ray's lane;
-// otherwise every lane that met the cluster tests all its members, and the
-// others idle through them.
-// Position of the n-th (from 0) set bit of m; n < popc(m).
-__device__ __forceinline__ int nth_set_bit(unsigned int m, int n) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    const int c = __popc(m & ((1u << w) - 1u));  // set bits among the low w
-    if (c <= n) {
-      n -= c;
-      m >>= w;
-      pos += w;
-    }
-  }
-  return pos;
-}
-
-// VOTE false: a lane alone (no warp vote; its warp's lanes may hold rays of
-// different items), as the refilling descent launch calls it.
-template <bool STATS, bool SPREAD = false, bool VOTE = true>
+// the same on every lane.  Every lane that met a cluster tests all its
+// members; with VOTE the others idle through them, and a cluster no lane
+// met is skipped.  VOTE false: a lane alone (no warp vote; its warp's lanes
+// may hold rays of different items), as the refilling descent launch calls
+// it.
+template <bool STATS, bool VOTE = true>
 __device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, const PartHot *__restrict__ hot,
                                           const Cluster *__restrict__ cl, const int32_t *__restrict__ order,
                                           float last_t, int last_p, float (&ct)[kCap], float (&ce)[kCap],
                                           int (&cp)[kCap], float &over_t, Counters &cnt) {
-  static_assert(VOTE || !SPREAD, "spreading the member tests needs the warp vote");
-  const int lane = threadIdx.x & 31;
   for (int c = 0; c < NC; ++c) {
     const Cluster cc = cl[c];
     const bool hc = need && cluster_cull(r, cc);
-    unsigned int m = 0u;
-    if (VOTE) {
-      m = __ballot_sync(0xffffffffu, hc);
-      if (m == 0u) continue;  // no lane needs this cluster
-    }
-    const uint32_t fc = __float_as_uint(cc.aux.w);
-    const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
-    const int nl = __popc(m);
-    static_assert(kClusterSize == 8, "pairs are dealt eight members to a lane that met the cluster");
-    if (SPREAD && nl <= 12) {
-      // pair q = (n-th lane of m, member q & 7): up to three rounds of 32 pairs
-      for (int q0 = 0; q0 < 8 * nl; q0 += 32) {
-        const int q = q0 + lane, n = q >> 3, k = q & 7;
-        const bool valid = n < nl && k < count;
-        const int owner = valid ? nth_set_bit(m, n) : lane;
-        RayW ro;
-        ro.ox = __shfl_sync(0xffffffffu, r.ox, owner);
-        ro.oy = __shfl_sync(0xffffffffu, r.oy, owner);
-        ro.oz = __shfl_sync(0xffffffffu, r.oz, owner);
-        ro.dx = __shfl_sync(0xffffffffu, r.dx, owner);
-        ro.dy = __shfl_sync(0xffffffffu, r.dy, owner);
-        ro.dz = __shfl_sync(0xffffffffu, r.dz, owner);
-        ro.tmin = __shfl_sync(0xffffffffu, r.tmin, owner);
-        ro.tmax = __shfl_sync(0xffffffffu, r.tmax, owner);
-        ro.inv_dd = __shfl_sync(0xffffffffu, r.inv_dd, owner);
-        const float lt = __shfl_sync(0xffffffffu, last_t, owner);
-        const int lp = __shfl_sync(0xffffffffu, last_p, owner);
-        float tin = 0.f, tref = 0.f;
-        int p = 0;
-        bool hit = false;
-        if (valid) {
-          p = order[first + k];
-          if (STATS) ++cnt.parts_tested;
-          hit = part_cull(ro, hot[p], tin, tref) && !(tin < lt || (tin == lt && p <= lp));
-        }
-        // hand each hit to its ray's lane (hits are rare: one round each)
-        for (unsigned int hm = __ballot_sync(0xffffffffu, hit); hm != 0u; hm &= hm - 1u) {
-          const int src = __ffs(hm) - 1;
-          const int o = __shfl_sync(0xffffffffu, owner, src);
-          float t = __shfl_sync(0xffffffffu, tin, src), e = __shfl_sync(0xffffffffu, tref, src);
-          int pp = __shfl_sync(0xffffffffu, p, src);
-          if (lane == o) {
-            list_insert(ct, ce, cp, t, e, pp);
-            over_t = fminf(over_t, t);
-          }
-        }
-      }
-      continue;
-    }
+    if (VOTE && __ballot_sync(0xffffffffu, hc) == 0u) continue;  // no lane needs this cluster
     if (hc) {
+      const uint32_t fc = __float_as_uint(cc.aux.w);
+      const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
       for (int k = 0; k < count; ++k) {
         const int p = order[first + k];
         float tin, eta;
@@ -1005,6 +935,116 @@ __device__ __forceinline__ void cull_pass(const RayW &r, bool need, int NC, cons
       }
     }
   }
+}
+
+// The first culling pass of the culling launch (the same candidates as
+// cull_pass with nothing descended before), with the member tests packed
+// over the warp's lanes across clusters.  Incoherent rays meet a cluster a
+// few lanes at a time, and testing its members in place would leave most
+// lanes idle.  So every (lane, cluster) pair of a cluster met by at most
+// kInPlaceLanes lanes goes into the warp's ring in shared memory (owner
+// lane, first | count << 16). Whenever four pairs wait, one round tests
+// their 32 (pair, member) combinations: lane q takes member q & 7 of pair
+// q >> 3 against its owner's ray (read by shuffles), and every hit goes back
+// to the owner's list.  A cluster met by more lanes has its members tested
+// in place.  The list keeps the kCap smallest (t, part) keys, and over_t the
+// smallest t of the others, whatever the order of insertion, so the result
+// is that of cull_pass.
+constexpr int kPackRing = 64;      // ring slots per warp: a power of two above 3 + kInPlaceLanes
+constexpr int kInPlaceLanes = 16;  // lanes above which a cluster's members are tested in place
+static_assert(kClusterSize == 8 && kInPlaceLanes + 3 < kPackRing, "four pairs of eight members fill a round");
+
+// One round: pairs ring[head .. head + n_pairs) (n_pairs <= 4), member
+// lane & 7 of pair lane >> 3 on every lane.
+template <bool STATS>
+__device__ __forceinline__ void member_round(const RayW &r, const int2 *ring, int head, int n_pairs,
+                                             const PartHot *__restrict__ hot, const int32_t *__restrict__ order,
+                                             float (&ct)[kCap], float (&ce)[kCap], int (&cp)[kCap],
+                                             float &over_t, Counters &cnt) {
+  const int lane = threadIdx.x & 31;
+  const int e = lane >> 3, k = lane & 7;
+  int owner = lane;
+  uint32_t fc = 0u;  // no pair: count 0
+  if (e < n_pairs) {
+    const int2 q = ring[(head + e) & (kPackRing - 1)];
+    owner = q.x;
+    fc = (uint32_t)q.y;
+  }
+  const bool valid = k < (int)(fc >> 16);
+  RayW ro;
+  ro.ox = __shfl_sync(0xffffffffu, r.ox, owner);
+  ro.oy = __shfl_sync(0xffffffffu, r.oy, owner);
+  ro.oz = __shfl_sync(0xffffffffu, r.oz, owner);
+  ro.dx = __shfl_sync(0xffffffffu, r.dx, owner);
+  ro.dy = __shfl_sync(0xffffffffu, r.dy, owner);
+  ro.dz = __shfl_sync(0xffffffffu, r.dz, owner);
+  ro.tmin = __shfl_sync(0xffffffffu, r.tmin, owner);
+  ro.tmax = __shfl_sync(0xffffffffu, r.tmax, owner);
+  ro.inv_dd = __shfl_sync(0xffffffffu, r.inv_dd, owner);
+  ro.inv_len = 0.f;
+  ro.onorm = 0.f;
+  float tin = 0.f, tref = 0.f;
+  int p = 0;
+  bool hit = false;
+  if (valid) {
+    p = order[(int)(fc & 0xFFFFu) + k];
+    if (STATS) ++cnt.parts_tested;
+    hit = part_cull(ro, hot[p], tin, tref);
+  }
+  // hand each hit to its ray's lane (hits are rare: one round each)
+  for (unsigned int hm = __ballot_sync(0xffffffffu, hit); hm != 0u; hm &= hm - 1u) {
+    const int src = __ffs(hm) - 1;
+    const int o = __shfl_sync(0xffffffffu, owner, src);
+    float t = __shfl_sync(0xffffffffu, tin, src), te = __shfl_sync(0xffffffffu, tref, src);
+    int pp = __shfl_sync(0xffffffffu, p, src);
+    if (lane == o) {
+      list_insert(ct, ce, cp, t, te, pp);
+      over_t = fminf(over_t, t);
+    }
+  }
+}
+
+// ring: the warp's kPackRing slots.  Called by the whole warp.
+template <bool STATS>
+__device__ __forceinline__ void cull_first_packed(const RayW &r, bool need, int NC, const PartHot *__restrict__ hot,
+                                                  const Cluster *__restrict__ cl,
+                                                  const int32_t *__restrict__ order, int2 *ring, float (&ct)[kCap],
+                                                  float (&ce)[kCap], int (&cp)[kCap], float &over_t,
+                                                  Counters &cnt) {
+  const int lane = threadIdx.x & 31;
+  int head = 0, pending = 0;  // warp-uniform: the ring's first waiting pair and the number waiting
+  for (int c = 0; c < NC; ++c) {
+    const Cluster cc = cl[c];
+    const bool hc = need && cluster_cull(r, cc);
+    const unsigned int m = __ballot_sync(0xffffffffu, hc);
+    if (m == 0u) continue;  // no lane needs this cluster
+    const uint32_t fc = __float_as_uint(cc.aux.w);
+    const int nl = __popc(m);
+    if (nl > kInPlaceLanes) {
+      if (hc) {
+        const int first = (int)(fc & 0xFFFFu), count = (int)(fc >> 16);
+        for (int k = 0; k < count; ++k) {
+          const int p = order[first + k];
+          float tin, eta;
+          if (STATS) ++cnt.parts_tested;
+          if (!part_cull(r, hot[p], tin, eta)) continue;
+          float t = tin, e = eta;
+          int pp = p;
+          list_insert(ct, ce, cp, t, e, pp);
+          over_t = fminf(over_t, t);
+        }
+      }
+      continue;
+    }
+    __syncwarp();  // the last round's reads of the ring are done
+    if (hc) ring[(head + pending + __popc(m & ((1u << lane) - 1u))) & (kPackRing - 1)] = make_int2(lane, (int)fc);
+    __syncwarp();
+    pending += nl;
+    for (; pending >= 4; pending -= 4, head = (head + 4) & (kPackRing - 1))
+      member_round<STATS>(r, ring, head, 4, hot, order, ct, ce, cp, over_t, cnt);
+  }
+  for (; pending > 0; pending -= 4, head = (head + 4) & (kPackRing - 1))  // the last pairs
+    member_round<STATS>(r, ring, head, min(pending, 4), hot, order, ct, ce, cp, over_t, cnt);
 }
 
 template <bool STATS, int BLOCK, bool GRID>
@@ -1441,10 +1481,11 @@ __global__ void __launch_bounds__(BLOCK, (STATS || REUSE || GRID ? 512 : kTraceT
 template <int NI, bool STATS, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_cull(const __grid_constant__ TraceLaunchT<NI> L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // [staged part spheres and rows | clusters | part order] of a one-scene launch
+  // [per-warp rings of member-test pairs | staged part spheres | clusters | part order of a one-scene launch]
   const int sp = L.one_scene ? L.items[0].n_parts : 0;
   const int sc = L.one_scene ? L.items[0].n_clusters : 0;
-  PartHot *sHot = reinterpret_cast<PartHot *>(smem);
+  int2 *ring = reinterpret_cast<int2 *>(smem) + (threadIdx.x >> 5) * kPackRing;
+  PartHot *sHot = reinterpret_cast<PartHot *>(smem + (BLOCK / 32) * kPackRing * sizeof(int2));
   Cluster *sCl = reinterpret_cast<Cluster *>(sHot + sp);
   int32_t *sOrd = reinterpret_cast<int32_t *>(sCl + sc);
   if (L.one_scene) {
@@ -1485,8 +1526,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_cull(const __grid_const
       }
       float over_t = Num<float>::inf();
       if (STATS && active) ++cnt.passes;
-      cull_pass<STATS, true>(r, active, I.n_clusters, hot, cls, ord, -Num<float>::inf(), -1, ct, ce, cp, over_t,
-                             cnt);
+      cull_first_packed<STATS>(r, active, I.n_clusters, hot, cls, ord, ring, ct, ce, cp, over_t, cnt);
       // over_t is set only by a full list, so an empty list means no candidate at all
       const bool queued = active && ct[0] != Num<float>::inf();
       if (in_range && !queued) {
@@ -1679,7 +1719,7 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_descend(const __grid_con
         }
         over_t = Num<float>::inf();
         if (STATS) ++cnt.passes;
-        cull_pass<STATS, false, false>(r, true, I.n_clusters, hot, staged ? sCl : I.clusters, staged ? sOrd : I.order,
+        cull_pass<STATS, false>(r, true, I.n_clusters, hot, staged ? sCl : I.clusters, staged ? sOrd : I.order,
                                        last_t, last_p, ct, ce, cp, over_t, cnt);
         continue;
       }
@@ -2002,7 +2042,8 @@ cudaError_t launch_trace_b(const TraceLaunchT<NI> &L, int n_sm, cudaStream_t str
     // the culling launch, then the descent launch over the queued rays (the
     // host has checked CULL | SORT without REUSE or GRID)
     const int parts = L.one_scene ? L.items[0].n_parts : 0, clusters = L.one_scene ? L.items[0].n_clusters : 0;
-    const size_t csmem = (size_t)parts * (sizeof(PartHot) + sizeof(int32_t)) + (size_t)clusters * sizeof(Cluster);
+    const size_t csmem = (size_t)(BLOCK / 32) * kPackRing * sizeof(int2) +
+                         (size_t)parts * (sizeof(PartHot) + sizeof(int32_t)) + (size_t)clusters * sizeof(Cluster);
     auto ck = stats ? k_cull<NI, true, BLOCK> : k_cull<NI, false, BLOCK>;
     int per_sm = 0;
     cudaError_t e = blocks_per_sm(ck, BLOCK, csmem, per_sm);
